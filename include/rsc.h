@@ -1,0 +1,155 @@
+/*
+ * rsc.h -- C ABI of librsc, GPU rotational sparse coding (rotational OMP) for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: McCann, Andrearczyk, Unser, Depeursinge, "Fast Rotational Sparse
+ * Coding".  Each patch x is coded by K (atom m, angle index r, weight a)
+ * triples chosen greedily by orthogonal matching pursuit (Sec. II-C, the OMP
+ * call of the R-K-SVD pseudocode in Fig. "code") over the augmented
+ * dictionary [S_0 D, ..., S_{R-1} D] of all atoms rotated to the angles
+ * 2*pi*r/R (Eq. (rot-SC)).  Patches and atoms are given in the steerable
+ * circular-harmonic basis of Sec. II-D, in which a rotation is the diagonal
+ * steering matrix of Eq. (Sr): harmonic k is multiplied by exp(-i k theta).
+ *
+ * Coefficient layout (patches and atoms alike): half spectra of real
+ * signals, float32, [k][j][re,im] with harmonics k = 0..kmax and rings
+ * j = 0..J-1, i.e. (kmax+1)*J*2 floats per vector, row-major, contiguous.
+ * The negative harmonics are implicit (c[j,-k] = conj(c[j,k])); the Im slot
+ * of k = 0 is ignored.  The inner product is the full-spectrum one,
+ * <u,v> = sum_j u_j0 v_j0 + 2 sum_{k>=1} sum_j Re(conj(u_jk) v_jk).
+ *
+ * Conventions: every call returns an int status (RSC_OK = 0, negative on
+ * error); no call throws.  Device pointers must be 16-byte aligned and
+ * belong to the current CUDA device.  Calls taking a `stream` enqueue work on
+ * that cudaStream_t (NULL = legacy default stream) and return after launch;
+ * the caller synchronises the stream before reading outputs.  The caller owns
+ * every buffer it passes; the library owns only the rsc_dict handle and the
+ * device memory behind it.  There is no CPU fallback: without a usable CUDA
+ * device the calls return RSC_ERR_CUDA.
+ */
+#ifndef RSC_H
+#define RSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define RSC_OK 0
+#define RSC_ERR_INVALID (-1)     /* bad argument (null pointer, size, alignment, norm) */
+#define RSC_ERR_OOM (-2)         /* device or host allocation failed */
+#define RSC_ERR_CUDA (-3)        /* a CUDA runtime call failed (message via rsc_last_cuda_error) */
+#define RSC_ERR_TIMEOUT (-4)     /* a device-side bounded wait gave up (see rsc_dict_check) */
+#define RSC_ERR_UNSUPPORTED (-5) /* valid but outside the sizes this build handles */
+
+/* Arithmetic of the scoring pass (step (a)-(c) below).  Every path re-scores
+ * its candidates in double-float arithmetic and solves the least-squares
+ * problem in FP64, so all paths return the same selections wherever the
+ * top-two margin of the exact scores exceeds their error bound. */
+#define RSC_FP32 0         /* FP32 CUDA-core contraction + angle DFT */
+#define RSC_BF16_RESCORE 2 /* BF16 tcgen05 tensor-core scores, candidates re-scored */
+
+typedef struct {
+  int32_t M;    /* atoms, >= 1 */
+  int32_t J;    /* radial rings, >= 1 */
+  int32_t kmax; /* highest angular harmonic, >= 0 */
+  int32_t R;    /* rotation angles 2*pi*r/R, r = 0..R-1, >= 1 */
+} rsc_dims;
+
+typedef struct rsc_dict rsc_dict; /* opaque, device-resident, immutable */
+
+/*
+ * rsc_dict_create -- upload a dictionary D-hat (Sec. II-D, step 2 of the
+ * proposed algorithm: atoms in steerable-basis coordinates) and precompute
+ * its per-angle tables (the steering factors exp(-i k 2 pi r / R) of
+ * Eq. (Sr), a transposed copy for the contraction, and, for the tensor-core
+ * path, the steered dictionary S_r d_m in bf16).
+ *   coef   : device pointer, M x (kmax+1) x J x 2 floats, atoms of unit
+ *            norm (|<d,d> - 1| <= 1e-4, else RSC_ERR_INVALID); read once,
+ *            the caller keeps ownership.
+ *   dims   : sizes; this build supports J*(kmax+1) <= 512, kmax <= 16,
+ *            R <= 128 (RSC_ERR_UNSUPPORTED otherwise).
+ *   stream : stream for the uploads; the call synchronises it before return.
+ *   out    : receives the handle; free it with rsc_dict_destroy.
+ */
+int rsc_dict_create(const float *coef, rsc_dims dims, void *stream, rsc_dict **out);
+
+/* Free a dictionary handle (NULL is accepted).  The caller must make sure no
+ * rsc_encode using it is still running. */
+int rsc_dict_destroy(rsc_dict *dict);
+
+/* Sizes of a dictionary handle. */
+int rsc_dict_dims(const rsc_dict *dict, rsc_dims *dims);
+
+/*
+ * rsc_encode -- rotational OMP (Sec. II-C; Eq. (rot-SC) with the steering
+ * of Eq. (Sr)) of P patches, K greedy steps each.  Every step of every patch:
+ *   (a) per-harmonic contraction G_k(m) = sum_j conj(d_m[j,k]) r[j,k];
+ *   (b) angle transform score(m,r) = G_0 + 2 Re sum_{k>=1} e^{ik 2 pi r/R} G_k
+ *       (= <S_r d_m, residual>);
+ *   (c) argmax over (m, r) of |score| (ties: smallest m*R + r), certified by
+ *       double-float re-scoring of every candidate within the scoring pass's
+ *       error bound of the best;
+ *   (e) least squares over the selected steered atoms by an incremental FP64
+ *       Cholesky factor of their Gram matrix;
+ *   (d) residual x - sum_i a_i S_{r_i} d_{m_i}.
+ * A patch stops early (remaining outputs atom = angle_idx = -1, angle = 0,
+ * coef = 0) when max |score| <= 1e-10 ||x|| or when the new pivot^2 of the
+ * Cholesky factor is <= 1e-12 times its Gram diagonal entry.
+ *   dict      : dictionary handle.
+ *   x         : device, P x (kmax+1) x J x 2 floats.
+ *   P         : patches, >= 0 (0 is a no-op).
+ *   K         : greedy steps, 1 <= K <= 16.
+ *   prec      : RSC_FP32 or RSC_BF16_RESCORE.
+ *   atom      : device int32 [P x K], atom index m per step, -1 if none.
+ *   angle_idx : device int32 [P x K], angle index r in [0, R), -1 if none.
+ *   angle     : device float [P x K] or NULL, the angle 2*pi*r/R in radians.
+ *   coef      : device double [P x K], least-squares weights a_i (FP64).
+ *   resid_norm2 : device float [P] or NULL, ||x - sum_i a_i S_{r_i} d_{m_i}||^2.
+ *   stream    : cudaStream_t (NULL = default stream).
+ * Outputs are in selection order.  Returns after launch.
+ */
+int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
+               int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
+               float *resid_norm2, void *stream);
+
+/*
+ * rsc_encode_host -- rsc_encode on HOST buffers (same shapes and meaning as
+ * above, all pointers host memory; pinned memory gives the fastest copies).
+ * Copies the patches to the device in chunks, codes them and copies the
+ * results back, overlapping the copies of one chunk with the coding of the
+ * next on two internal streams.  Blocks until every output is written.
+ * Device memory for the chunks is allocated and freed inside the call.
+ */
+int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
+                    int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
+                    float *resid_norm2);
+
+/*
+ * rsc_dict_check -- synchronise `stream` and report the first device-side
+ * error recorded by kernels that used `dict` since the last check
+ * (RSC_ERR_TIMEOUT when a bounded wait gave up), then clear it.
+ */
+int rsc_dict_check(const rsc_dict *dict, void *stream);
+
+/* Count of patch-steps, since the last call, in which the scoring pass left
+ * more candidates within its error bound than it keeps, so that the step was
+ * decided by an exact re-scan of all M*R candidates (diagnostic; resets). */
+int rsc_dict_fallback_count(const rsc_dict *dict, int64_t *count);
+
+/* Human-readable text of a status code (static storage). */
+const char *rsc_status_string(int status);
+
+/* Text of the last CUDA error seen by this thread inside librsc. */
+const char *rsc_last_cuda_error(void);
+
+/* ABI version, (major << 16) | minor. */
+int rsc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSC_H */

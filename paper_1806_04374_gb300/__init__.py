@@ -1,0 +1,219 @@
+"""GPU rotational sparse coding (rotational OMP, McCann et al., "Fast
+Rotational Sparse Coding") for NVIDIA GB300.
+
+The compute lives in librsc.so (CUDA, sm_103a) behind the C ABI of
+include/rsc.h.  This module is a thin ctypes binding with the same names: it
+marshals pointers, sizes and CUDA streams, and never computes anything
+itself.  PyTorch is used only to own device memory and streams.  There is no
+CPU fallback: if the library is missing the import of the binding fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librsc.so")
+
+RSC_OK = 0
+RSC_ERR_INVALID = -1
+RSC_ERR_OOM = -2
+RSC_ERR_CUDA = -3
+RSC_ERR_TIMEOUT = -4
+RSC_ERR_UNSUPPORTED = -5
+
+RSC_FP32 = 0
+RSC_BF16_RESCORE = 2
+PRECISIONS = {"fp32": RSC_FP32, "bf16": RSC_BF16_RESCORE}
+
+# every symbol include/rsc.h declares
+EXPORTS = (
+    "rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode", "rsc_encode_host",
+    "rsc_dict_check", "rsc_dict_fallback_count", "rsc_status_string", "rsc_last_cuda_error",
+    "rsc_version",
+)
+
+
+class rsc_dims(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("J", ctypes.c_int32), ("kmax", ctypes.c_int32),
+                ("R", ctypes.c_int32)]
+
+
+class RscError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = f"{what}: {rsc_status_string(status)} ({status})"
+        if status == RSC_ERR_CUDA:
+            msg += f" [{rsc_last_cuda_error()}]"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads librsc.so (built by ``build.build()``); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"librsc.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.rsc_dict_create.argtypes = [vp, rsc_dims, vp, ctypes.POINTER(vp)]
+    lib.rsc_dict_destroy.argtypes = [vp]
+    lib.rsc_dict_dims.argtypes = [vp, ctypes.POINTER(rsc_dims)]
+    lib.rsc_encode.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.rsc_encode_host.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
+    lib.rsc_dict_check.argtypes = [vp, vp]
+    lib.rsc_dict_fallback_count.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.rsc_status_string.argtypes = [ctypes.c_int]
+    lib.rsc_status_string.restype = ctypes.c_char_p
+    lib.rsc_last_cuda_error.argtypes = []
+    lib.rsc_last_cuda_error.restype = ctypes.c_char_p
+    lib.rsc_version.argtypes = []
+    for name in ("rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode",
+                 "rsc_encode_host", "rsc_dict_check", "rsc_dict_fallback_count", "rsc_version"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------- raw C-ABI calls
+
+def rsc_status_string(status: int) -> str:
+    return load_library().rsc_status_string(int(status)).decode()
+
+
+def rsc_last_cuda_error() -> str:
+    return load_library().rsc_last_cuda_error().decode()
+
+
+def rsc_version() -> int:
+    return load_library().rsc_version()
+
+
+def rsc_dict_create(coef_ptr: int, M: int, J: int, kmax: int, R: int, stream: int = 0) -> int:
+    """Returns the handle (int) or raises RscError."""
+    h = ctypes.c_void_p()
+    st = load_library().rsc_dict_create(ctypes.c_void_p(coef_ptr), rsc_dims(M, J, kmax, R),
+                                        ctypes.c_void_p(stream), ctypes.byref(h))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_dict_create")
+    return h.value
+
+
+def rsc_dict_destroy(handle: int) -> int:
+    return load_library().rsc_dict_destroy(ctypes.c_void_p(handle))
+
+
+def rsc_encode(handle: int, x_ptr: int, P: int, K: int, prec: int, atom_ptr: int, angle_idx_ptr: int,
+               angle_ptr: int, coef_ptr: int, resid_norm2_ptr: int, stream: int = 0) -> int:
+    """Raw call; returns the status code."""
+    vp = ctypes.c_void_p
+    return load_library().rsc_encode(vp(handle), vp(x_ptr), int(P), int(K), int(prec), vp(atom_ptr),
+                                     vp(angle_idx_ptr), vp(angle_ptr or None), vp(coef_ptr),
+                                     vp(resid_norm2_ptr or None), vp(stream))
+
+
+def rsc_encode_host(handle: int, x_ptr: int, P: int, K: int, prec: int, atom_ptr: int,
+                    angle_idx_ptr: int, angle_ptr: int, coef_ptr: int, resid_norm2_ptr: int) -> int:
+    vp = ctypes.c_void_p
+    return load_library().rsc_encode_host(vp(handle), vp(x_ptr), int(P), int(K), int(prec),
+                                          vp(atom_ptr), vp(angle_idx_ptr), vp(angle_ptr or None),
+                                          vp(coef_ptr), vp(resid_norm2_ptr or None))
+
+
+def rsc_dict_check(handle: int, stream: int = 0) -> int:
+    return load_library().rsc_dict_check(ctypes.c_void_p(handle), ctypes.c_void_p(stream))
+
+
+def rsc_dict_fallback_count(handle: int) -> int:
+    v = ctypes.c_int64()
+    st = load_library().rsc_dict_fallback_count(ctypes.c_void_p(handle), ctypes.byref(v))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_dict_fallback_count")
+    return v.value
+
+
+# ----------------------------------------------------------- torch helpers
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Dictionary:
+    """Owns an rsc_dict handle built from a CUDA float32 tensor [M, kmax+1, J, 2]."""
+
+    def __init__(self, d, R: int, stream=None):
+        import torch
+        if not (isinstance(d, torch.Tensor) and d.is_cuda and d.dtype == torch.float32):
+            raise TypeError("dictionary must be a CUDA float32 tensor [M, kmax+1, J, 2]")
+        d = d.contiguous()
+        M, H, J, two = d.shape
+        if two != 2:
+            raise ValueError("last dimension must be (re, im)")
+        self.M, self.J, self.kmax, self.R, self.H = M, J, H - 1, int(R), H
+        self.handle = rsc_dict_create(d.data_ptr(), M, J, H - 1, int(R), _stream_handle(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rsc_dict_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def encode(dic: Dictionary, x, K: int, precision: str = "fp32", stream=None, out=None):
+    """rsc_encode on CUDA tensors.  x: float32 [P, kmax+1, J, 2] on the
+    dictionary's device.  Returns a dict of output tensors (atom, angle_idx,
+    angle, coef, resid_norm2); ``out`` may hold preallocated ones."""
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise TypeError("x must be a contiguous CUDA float32 tensor")
+    P = x.shape[0]
+    dev = x.device
+    if out is None:
+        out = {
+            "atom": torch.empty((P, K), dtype=torch.int32, device=dev),
+            "angle_idx": torch.empty((P, K), dtype=torch.int32, device=dev),
+            "angle": torch.empty((P, K), dtype=torch.float32, device=dev),
+            "coef": torch.empty((P, K), dtype=torch.float64, device=dev),
+            "resid_norm2": torch.empty((P,), dtype=torch.float32, device=dev),
+        }
+    st = rsc_encode(dic.handle, x.data_ptr(), P, K, PRECISIONS[precision], out["atom"].data_ptr(),
+                    out["angle_idx"].data_ptr(), out["angle"].data_ptr(), out["coef"].data_ptr(),
+                    out["resid_norm2"].data_ptr(), _stream_handle(stream))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_encode")
+    return out
+
+
+def encode_host(dic: Dictionary, x, K: int, precision: str = "fp32", out=None):
+    """rsc_encode_host on host (ideally pinned) CPU tensors; blocks."""
+    import torch
+    if x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+        raise TypeError("x must be a contiguous CPU float32 tensor")
+    P = x.shape[0]
+    if out is None:
+        out = {
+            "atom": torch.empty((P, K), dtype=torch.int32),
+            "angle_idx": torch.empty((P, K), dtype=torch.int32),
+            "angle": torch.empty((P, K), dtype=torch.float32),
+            "coef": torch.empty((P, K), dtype=torch.float64),
+            "resid_norm2": torch.empty((P,), dtype=torch.float32),
+        }
+    st = rsc_encode_host(dic.handle, x.data_ptr(), P, K, PRECISIONS[precision],
+                         out["atom"].data_ptr(), out["angle_idx"].data_ptr(),
+                         out["angle"].data_ptr(), out["coef"].data_ptr(),
+                         out["resid_norm2"].data_ptr())
+    if st != RSC_OK:
+        raise RscError(st, "rsc_encode_host")
+    return out

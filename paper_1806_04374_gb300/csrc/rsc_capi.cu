@@ -1,0 +1,302 @@
+// rsc_capi.cu -- host side of the librsc C ABI (declared in include/rsc.h):
+// argument checks, dictionary set-up (the once-per-dictionary tables of the
+// steering matrix of Eq. (Sr)) and dispatch of the coding kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "rsc_internal.h"
+
+namespace {
+
+thread_local char g_cuda_msg[256] = "no error";
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <class T>
+bool aligned_as(const void *p) {
+  return (reinterpret_cast<uintptr_t>(p) % alignof(T)) == 0;
+}
+
+void free_dict(rsc_dict *d) {
+  if (!d) return;
+  cudaFree(d->d);
+  cudaFree(d->dT);
+  cudaFree(d->tw);
+  cudaFree(d->err);
+  cudaFree(d->fallbacks);
+  cudaFree(d->steered_bf16);
+  delete d;
+}
+
+int check_device(const rsc_dict *d) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  return dev == d->device ? RSC_OK : RSC_ERR_INVALID;
+}
+
+}  // namespace
+
+int rsc_cuda_fail(cudaError_t e) {
+  snprintf(g_cuda_msg, sizeof g_cuda_msg, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return RSC_ERR_CUDA;
+}
+
+extern "C" {
+
+const char *rsc_last_cuda_error(void) { return g_cuda_msg; }
+
+int rsc_version(void) { return (1 << 16) | 0; }
+
+const char *rsc_status_string(int s) {
+  switch (s) {
+    case RSC_OK: return "ok";
+    case RSC_ERR_INVALID: return "invalid argument";
+    case RSC_ERR_OOM: return "out of memory";
+    case RSC_ERR_CUDA: return "CUDA error";
+    case RSC_ERR_TIMEOUT: return "device-side wait timed out";
+    case RSC_ERR_UNSUPPORTED: return "unsupported size or option";
+    default: return "unknown status";
+  }
+}
+
+int rsc_dict_create(const float *coef, rsc_dims dims, void *stream, rsc_dict **out) {
+  if (!out) return RSC_ERR_INVALID;
+  *out = nullptr;
+  if (!coef || !aligned16(coef)) return RSC_ERR_INVALID;
+  if (dims.M < 1 || dims.J < 1 || dims.kmax < 0 || dims.R < 1) return RSC_ERR_INVALID;
+  const int H = dims.kmax + 1;
+  if (dims.kmax > kMaxKmax || dims.R > kMaxR || (int64_t)H * dims.J > kMaxEntries)
+    return RSC_ERR_UNSUPPORTED;
+  if ((int64_t)dims.M * dims.R >= (int64_t)1 << 30) return RSC_ERR_UNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int M = dims.M, J = dims.J, R = dims.R, HJ = H * J;
+  const size_t nd = (size_t)M * HJ * 2;
+
+  std::vector<float> h(nd);
+  cudaError_t e = cudaMemcpyAsync(h.data(), coef, nd * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+
+  // Im of k = 0 is ignored: store it as 0.  Atoms must have unit norm.
+  for (int m = 0; m < M; ++m) {
+    double n2 = 0.0;
+    for (int k = 0; k < H; ++k)
+      for (int j = 0; j < J; ++j) {
+        float *c = &h[((size_t)m * HJ + k * J + j) * 2];
+        if (k == 0) c[1] = 0.0f;
+        if (!isfinite(c[0]) || !isfinite(c[1])) return RSC_ERR_INVALID;
+        double w = k ? 2.0 : 1.0;
+        n2 += w * ((double)c[0] * c[0] + (double)c[1] * c[1]);
+      }
+    if (fabs(n2 - 1.0) > 1e-4) return RSC_ERR_INVALID;
+  }
+  std::vector<float> hT((size_t)2 * HJ * M);
+  for (int m = 0; m < M; ++m)
+    for (int q = 0; q < HJ; ++q) {
+      hT[(size_t)q * M + m] = h[((size_t)m * HJ + q) * 2];
+      hT[(size_t)(HJ + q) * M + m] = h[((size_t)m * HJ + q) * 2 + 1];
+    }
+  // steering factors exp(-i k 2 pi r / R) of Eq. (Sr) as cos/sin in
+  // double-float (hi + lo) from FP64, argument reduced exactly: k r mod R
+  std::vector<float> tw((size_t)4 * H * R);
+  for (int k = 0; k < H; ++k)
+    for (int r = 0; r < R; ++r) {
+      const double th = 2.0 * M_PI * (double)(((int64_t)k * r) % R) / (double)R;
+      const double c = cos(th), s = sin(th);
+      const float ch = (float)c, sh = (float)s;
+      tw[(size_t)(0 * H + k) * R + r] = ch;
+      tw[(size_t)(1 * H + k) * R + r] = (float)(c - (double)ch);
+      tw[(size_t)(2 * H + k) * R + r] = sh;
+      tw[(size_t)(3 * H + k) * R + r] = (float)(s - (double)sh);
+    }
+
+  rsc_dict *d = new rsc_dict();
+  memset(d, 0, sizeof *d);
+  d->M = M;
+  d->J = J;
+  d->kmax = dims.kmax;
+  d->R = R;
+  d->H = H;
+  e = cudaGetDevice(&d->device);
+  if (e == cudaSuccess) e = cudaMalloc(&d->d, nd * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d->dT, hT.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d->tw, tw.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d->fallbacks, sizeof(unsigned long long));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    free_dict(d);
+    return RSC_ERR_OOM;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->d, h.data(), nd * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->dT, hT.data(), hT.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->tw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->fallbacks, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    free_dict(d);
+    return rsc_cuda_fail(e);
+  }
+  *out = d;
+  return RSC_OK;
+}
+
+int rsc_dict_destroy(rsc_dict *dict) {
+  free_dict(dict);
+  return RSC_OK;
+}
+
+int rsc_dict_dims(const rsc_dict *dict, rsc_dims *dims) {
+  if (!dict || !dims) return RSC_ERR_INVALID;
+  dims->M = dict->M;
+  dims->J = dict->J;
+  dims->kmax = dict->kmax;
+  dims->R = dict->R;
+  return RSC_OK;
+}
+
+int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
+               int32_t *atom, int32_t *angle_idx, float *angle, double *coef, float *resid_norm2,
+               void *stream) {
+  if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_BF16_RESCORE) return RSC_ERR_INVALID;
+  if (P == 0) return RSC_OK;
+  if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
+  if (!aligned16(x) || !aligned_as<int32_t>(atom) || !aligned_as<int32_t>(angle_idx) ||
+      !aligned_as<double>(coef) || (angle && !aligned_as<float>(angle)) ||
+      (resid_norm2 && !aligned_as<float>(resid_norm2)))
+    return RSC_ERR_INVALID;
+  int rc = check_device(dict);
+  if (rc != RSC_OK) return rc;
+  RompArgs a;
+  a.x = x;
+  a.P = P;
+  a.K = K;
+  a.M = dict->M;
+  a.J = dict->J;
+  a.kmax = dict->kmax;
+  a.R = dict->R;
+  a.H = dict->H;
+  a.d = dict->d;
+  a.dT = dict->dT;
+  a.tw = dict->tw;
+  a.atom = atom;
+  a.angle_idx = angle_idx;
+  a.angle = angle;
+  a.coef = coef;
+  a.resid_norm2 = resid_norm2;
+  a.err = dict->err;
+  a.fallbacks = dict->fallbacks;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (prec == RSC_FP32) return rsc_launch_f32(a, st);
+  return RSC_ERR_UNSUPPORTED;
+}
+
+int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
+                    int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
+                    float *resid_norm2) {
+  if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_BF16_RESCORE) return RSC_ERR_INVALID;
+  if (P == 0) return RSC_OK;
+  if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
+  int rc = check_device(dict);
+  if (rc != RSC_OK) return rc;
+  const int64_t vec = (int64_t)dict->H * dict->J * 2;
+  const int64_t chunk = P < (1 << 18) ? P : (1 << 18);
+  struct Buf {
+    float *x = nullptr;
+    int32_t *atom = nullptr, *ang = nullptr;
+    float *angf = nullptr, *rn2 = nullptr;
+    double *coef = nullptr;
+  } b[2];
+  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b[i].x, chunk * vec * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b[i].atom, chunk * K * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b[i].ang, chunk * K * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b[i].angf, chunk * K * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b[i].coef, chunk * K * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b[i].rn2, chunk * sizeof(float));
+  }
+  rc = RSC_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    rc = RSC_ERR_OOM;
+  } else if (e != cudaSuccess) {
+    rc = rsc_cuda_fail(e);
+  }
+  for (int64_t lo = 0, ci = 0; rc == RSC_OK && lo < P; lo += chunk, ++ci) {
+    const int64_t n = (P - lo) < chunk ? (P - lo) : chunk;
+    Buf &B = b[ci & 1];
+    cudaStream_t st = s[ci & 1];
+    e = cudaMemcpyAsync(B.x, x + lo * vec, n * vec * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      rc = rsc_cuda_fail(e);
+      break;
+    }
+    rc = rsc_encode(dict, B.x, n, K, prec, B.atom, B.ang, angle ? B.angf : nullptr, B.coef,
+                    resid_norm2 ? B.rn2 : nullptr, st);
+    if (rc != RSC_OK) break;
+    e = cudaMemcpyAsync(atom + lo * K, B.atom, n * K * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(angle_idx + lo * K, B.ang, n * K * sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && angle)
+      e = cudaMemcpyAsync(angle + lo * K, B.angf, n * K * sizeof(float), cudaMemcpyDeviceToHost,
+                          st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(coef + lo * K, B.coef, n * K * sizeof(double), cudaMemcpyDeviceToHost,
+                          st);
+    if (e == cudaSuccess && resid_norm2)
+      e = cudaMemcpyAsync(resid_norm2 + lo, B.rn2, n * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (s[i]) {
+      cudaError_t se = cudaStreamSynchronize(s[i]);
+      if (se != cudaSuccess && rc == RSC_OK) rc = rsc_cuda_fail(se);
+      cudaStreamDestroy(s[i]);
+    }
+    cudaFree(b[i].x);
+    cudaFree(b[i].atom);
+    cudaFree(b[i].ang);
+    cudaFree(b[i].angf);
+    cudaFree(b[i].coef);
+    cudaFree(b[i].rn2);
+  }
+  return rc;
+}
+
+int rsc_dict_check(const rsc_dict *dict, void *stream) {
+  if (!dict) return RSC_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  int v = 0;
+  e = cudaMemcpy(&v, dict->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(dict->err, 0, sizeof(int));
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  return v;
+}
+
+int rsc_dict_fallback_count(const rsc_dict *dict, int64_t *count) {
+  if (!dict || !count) return RSC_ERR_INVALID;
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpy(&v, dict->fallbacks, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(dict->fallbacks, 0, sizeof v);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  *count = (int64_t)v;
+  return RSC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+"""GPU parity: librsc (through the C ABI) against the FP64 oracle.
+
+Selections must match the oracle wherever its top-two margin exceeds 1e-6
+relative; weights must match the oracle's least-squares weights along the
+GPU's path within 1e-5 relative (FP32 scoring path) -- see tests/parity.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_04374_gb300 import synth
+
+from parity import check
+
+pytestmark = pytest.mark.gpu
+
+COEF_TOL = {"fp32": 1e-5, "bf16": 1e-3}
+
+
+@pytest.fixture(scope="module")
+def rsc(cuda_ok):
+    import paper_1806_04374_gb300 as rsc
+    rsc.load_library()
+    return rsc
+
+
+def run_gpu(rsc, x, d, R, K, precision="fp32"):
+    import torch
+    dev = torch.device("cuda:0")
+    dic = rsc.Dictionary(torch.from_numpy(np.ascontiguousarray(d)).to(dev), R)
+    xt = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    out = rsc.encode(dic, xt, K, precision)
+    torch.cuda.synchronize()
+    assert rsc.rsc_dict_check(dic.handle) == 0
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["fallbacks"] = rsc.rsc_dict_fallback_count(dic.handle)
+    dic.close()
+    return res
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_small_workload_full(rsc, precision):
+    """1000 patches, M=16, R=32, K=3, sigma 0.05 (plus 3 ragged extra)."""
+    d, x, _, wl = synth.workload_inputs("omp_small")
+    x2, _ = synth.make_patches(d, 3, wl.n_terms, wl.sigma, 777)
+    x = np.concatenate([x, x2])
+    g = run_gpu(rsc, x, d, wl.R, wl.K, precision)
+    s = check(x, d, wl.R, wl.K, g, COEF_TOL[precision])
+    assert s["pinned_steps"] > 0.99 * x.shape[0] * wl.K - 50
+    print(precision, s, "fallbacks", g["fallbacks"])
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_1m_workload_sampled(rsc, precision):
+    """The 1,000,000-patch workload (M=64, R=64, K=5) coded in one launch as
+    the benchmark does; 768 sampled patches (incl. the first and last) are
+    checked against the oracle one by one."""
+    d, x, _, wl = synth.workload_inputs("omp_1m")
+    g = run_gpu(rsc, x, d, wl.R, wl.K, precision)
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([[0, wl.P - 1], rng.choice(wl.P, 766, replace=False)]))
+    sub = {k: (v[idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+    s = check(x[idx], d, wl.R, wl.K, sub, COEF_TOL[precision])
+    print(precision, s, "fallbacks", g["fallbacks"])
+    # every patch coded: no atom index out of range, no NaN weights
+    assert g["atom"].min() >= -1 and g["atom"].max() < wl.M
+    assert np.isfinite(g["coef"]).all()
+
+
+CASES = [
+    # (name, M, J, kmax, R, K, P, n_terms, sigma)
+    ("R1_textbook_omp", 12, 6, 8, 1, 4, 97, 3, 0.05),
+    ("R60_paper_angles", 10, 6, 8, 60, 3, 131, 3, 0.05),
+    ("R33_ragged_lanes", 7, 6, 8, 33, 3, 67, 2, 0.1),
+    ("R128_max", 9, 6, 8, 128, 3, 45, 3, 0.05),
+    ("K16_reuse_atoms", 2, 6, 8, 16, 16, 41, 4, 0.2),
+    ("K1", 20, 6, 8, 64, 1, 100, 3, 0.05),
+    ("M256_global_dict", 256, 6, 8, 64, 4, 60, 3, 0.05),
+    ("kmax12_J10", 32, 10, 12, 64, 4, 40, 3, 0.05),
+    ("kmax16_J4", 16, 4, 16, 64, 3, 40, 3, 0.05),
+    ("kmax0_rotation_invariant", 8, 6, 0, 16, 3, 30, 3, 0.05),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_edge_shapes(rsc, case):
+    name, M, J, kmax, R, K, P, n_terms, sigma = case
+    d = synth.make_dictionary(M, J, kmax, 1000 + M + R)
+    x, _ = synth.make_patches(d, P, n_terms, sigma, 2000 + R)
+    g = run_gpu(rsc, x, d, R, K)
+    s = check(x, d, R, K, g, COEF_TOL["fp32"])
+    print(name, s, "fallbacks", g["fallbacks"])
+
+
+def test_degenerate_patches(rsc):
+    """Zero patch (no step), exactly one steered atom on the grid (one step,
+    then stop), and an exactly sparse patch recovered with zero residual."""
+    M, J, kmax, R = 6, 6, 8, 8
+    d = synth.make_dictionary(M, J, kmax, 42)
+    xs = [np.zeros((kmax + 1, J, 2), np.float32), d[3].copy()]
+    q = oracle.steer(d[1].astype(np.float64), 2 * np.pi * 2 / R)  # a quarter turn: exact
+    xs.append(q.astype(np.float32))
+    x = np.stack(xs)
+    g = run_gpu(rsc, x, d, R, 3)
+    assert np.all(g["atom"][0] == -1) and np.all(g["coef"][0] == 0)
+    assert g["atom"][1, 0] == 3 and g["angle_idx"][1, 0] == 0 and np.all(g["atom"][1, 1:] == -1)
+    assert g["atom"][2, 0] == 1 and g["angle_idx"][2, 0] == 2 and np.all(g["atom"][2, 1:] == -1)
+    assert abs(g["coef"][1, 0] - 1.0) < 1e-9 and abs(g["coef"][2, 0] - 1.0) < 1e-9
+    check(x, d, R, 3, g, COEF_TOL["fp32"])
+
+
+def test_rotation_covariance_gpu(rsc):
+    """Rotating every patch by s grid steps shifts every GPU-selected angle by
+    s (Eq. 3) wherever the oracle's margins pin the selections."""
+    d, x, _, wl = synth.workload_inputs("omp_small", P=200)
+    s = 5
+    xr = np.stack([oracle.steer(v.astype(np.float64), 2 * np.pi * s / wl.R) for v in x]).astype(
+        np.float32)
+    g0 = run_gpu(rsc, x, d, wl.R, wl.K)
+    g1 = run_gpu(rsc, xr, d, wl.R, wl.K)
+    o0 = oracle.romp(x, d, wl.R, wl.K)
+    o1 = oracle.romp(xr, d, wl.R, wl.K)
+    ok = np.all(o0["margin"] > 1e-4, axis=1) & np.all(o1["margin"] > 1e-4, axis=1)
+    assert ok.sum() > 150
+    assert np.array_equal(g1["atom"][ok], g0["atom"][ok])
+    assert np.array_equal(g1["angle_idx"][ok], (g0["angle_idx"][ok] + s) % wl.R)
+
+
+def test_empty_and_errors(rsc):
+    import torch
+    d = synth.make_dictionary(4, 6, 8, 1)
+    dic = rsc.Dictionary(torch.from_numpy(d).cuda(), 8)
+    x = torch.zeros((0, 9, 6, 2), device="cuda")
+    out = rsc.encode(dic, x, 3)
+    assert out["atom"].shape == (0, 3)
+    x = torch.from_numpy(synth.make_patches(d, 4, 2, 0.1, 3)[0]).cuda()
+    outs = rsc.encode(dic, x, 2)
+    p = {k: v.data_ptr() for k, v in outs.items()}
+    bad = [
+        (dict(K=0), rsc.RSC_ERR_INVALID),
+        (dict(K=17), rsc.RSC_ERR_INVALID),
+        (dict(prec=7), rsc.RSC_ERR_INVALID),
+        (dict(x_ptr=x.data_ptr() + 4), rsc.RSC_ERR_INVALID),  # misaligned
+        (dict(atom_ptr=0), rsc.RSC_ERR_INVALID),
+        (dict(P=-1), rsc.RSC_ERR_INVALID),
+    ]
+    for kw, want in bad:
+        args = dict(handle=dic.handle, x_ptr=x.data_ptr(), P=4, K=2, prec=0, atom_ptr=p["atom"],
+                    angle_idx_ptr=p["angle_idx"], angle_ptr=p["angle"], coef_ptr=p["coef"],
+                    resid_norm2_ptr=p["resid_norm2"])
+        args.update(kw)
+        assert rsc.rsc_encode(**args) == want, kw
+    torch.cuda.synchronize()
+    # a dictionary whose atoms are not unit norm is rejected
+    with pytest.raises(rsc.RscError):
+        rsc.Dictionary(torch.from_numpy(2.0 * d).cuda(), 8)
+    # sizes beyond this build
+    with pytest.raises(rsc.RscError):
+        rsc.Dictionary(torch.from_numpy(d).cuda(), 129)
+
+
+def test_host_entry_point_matches_device(rsc):
+    """rsc_encode_host (chunked copies + coding on two streams) returns the
+    same codes as rsc_encode on device buffers."""
+    import torch
+    d, x, _, wl = synth.workload_inputs("omp_1m", P=300_000)
+    dic = rsc.Dictionary(torch.from_numpy(d).cuda(), wl.R)
+    xd = torch.from_numpy(x).cuda()
+    a = rsc.encode(dic, xd, wl.K)
+    torch.cuda.synchronize()
+    b = rsc.encode_host(dic, torch.from_numpy(x).pin_memory(), wl.K)
+    for k in ("atom", "angle_idx", "coef", "resid_norm2", "angle"):
+        assert np.array_equal(a[k].cpu().numpy(), b[k].numpy()), k
