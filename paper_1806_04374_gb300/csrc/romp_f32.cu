@@ -25,8 +25,7 @@
 
 namespace {
 
-constexpr int kWarps = 8;      // warps per block
-constexpr int kChunk = 64;     // atoms per contraction chunk (g buffer rows)
+constexpr int kChunk = 32;     // atoms per contraction chunk (g buffer rows)
 constexpr int kCandCap = 128;  // candidates kept per step (4 per lane)
 
 template <int KM>
@@ -40,16 +39,18 @@ struct Layout {
   int dT_off;             // transposed atoms [2][HJ][M] or -1 (read from global)
   // per-warp
   int warp_off, warp_bytes;
-  int x_off, rhi_off, rlo_off, g_off, cand_off, L_off, z_off, a_off, sel_off, gram_off;
+  int x_off, rhi_off, rlo_off, g_off, cand_off, L_off, z_off, a_off, adf_off, sel_off, gram_off;
+  int acache_off;  // [K][HJ] float4: steered selected atoms (re hi, re lo, im hi, im lo)
   int total;
 };
 
 __host__ __device__ inline int align16(int v) { return (v + 15) & ~15; }
 
 template <int KM>
-__host__ __device__ inline Layout make_layout(int M, int J, int H, int R, bool dT_in_smem) {
+__host__ __device__ inline Layout make_layout(int M, int J, int H, int R, int K, int warps,
+                                              bool dT_in_smem) {
   Layout L;
-  int HJ = H * J;
+  const int HJ = H * J;
   int off = 0;
   L.tw_stride = R + 1;
   L.tw_off = off;
@@ -58,18 +59,20 @@ __host__ __device__ inline Layout make_layout(int M, int J, int H, int R, bool d
   if (dT_in_smem) off = align16(off + 2 * HJ * M * 4);
   L.warp_off = off;
   int w = 0;
-  L.x_off = w;   w = align16(w + 2 * HJ * 4);
-  L.rhi_off = w; w = align16(w + 2 * HJ * 4);
-  L.rlo_off = w; w = align16(w + 2 * HJ * 4);
-  L.g_off = w;   w = align16(w + kChunk * GStride<KM>::v * 4);
+  L.x_off = w;    w = align16(w + 2 * HJ * 4);
+  L.rhi_off = w;  w = align16(w + 2 * HJ * 4);
+  L.rlo_off = w;  w = align16(w + 2 * HJ * 4);
+  L.g_off = w;    w = align16(w + kChunk * GStride<KM>::v * 4);
   L.cand_off = w; w = align16(w + kCandCap * 4);
-  L.L_off = w;   w = align16(w + kMaxK * (kMaxK + 1) / 2 * 8);
-  L.z_off = w;   w = align16(w + kMaxK * 8);
-  L.a_off = w;   w = align16(w + kMaxK * 8);
-  L.sel_off = w; w = align16(w + kMaxK * 4);
-  L.gram_off = w; w = align16(w + (kMaxK + 2) * 8);
+  L.L_off = w;    w = align16(w + K * (K + 1) / 2 * 8);
+  L.z_off = w;    w = align16(w + K * 8);
+  L.a_off = w;    w = align16(w + K * 8);
+  L.adf_off = w;  w = align16(w + 2 * K * 4);
+  L.sel_off = w;  w = align16(w + K * 4);
+  L.gram_off = w; w = align16(w + (2 * K + 2) * 8);
+  L.acache_off = w; w = align16(w + K * HJ * 16);
   L.warp_bytes = w;
-  L.total = off + kWarps * w;
+  L.total = off + warps * w;
   return L;
 }
 
@@ -90,16 +93,28 @@ struct Cdf {
 
 // Entry e = k*J + j of the steered atom S_{2 pi r / R} d_m in double-float:
 // e^{-ik theta} (dre + i dim) = (c dre + s dim) + i (c dim - s dre).
-__device__ __forceinline__ Cdf steered_entry(const float *__restrict__ d, int H, int J, int m,
+__device__ __forceinline__ Cdf steered_entry(const float *__restrict__ d, int HJ, int k, int m,
                                              int r, int e, const Tw &tw) {
-  int k = e / J;
-  float2 dv = __ldg(reinterpret_cast<const float2 *>(d) + (size_t)m * H * J + e);
+  float2 dv = __ldg(reinterpret_cast<const float2 *>(d) + (size_t)m * HJ + e);
   float dim = (k == 0) ? 0.0f : dv.y;
   df c = tw.cosv(k, r), s = tw.sinv(k, r);
   Cdf out;
   out.re = df_add(df_mul_f(c, dv.x), df_mul_f(s, dim));
   out.im = df_sub(df_mul_f(c, dim), df_mul_f(s, dv.x));
   return out;
+}
+
+// |a| > |b| for normalised double-float values.
+__device__ __forceinline__ bool df_abs_gt(df a, df b) {
+  if (a.hi < 0.0f) a = df_neg(a);
+  if (b.hi < 0.0f) b = df_neg(b);
+  return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+
+__device__ __forceinline__ bool df_abs_eq(df a, df b) {
+  if (a.hi < 0.0f) a = df_neg(a);
+  if (b.hi < 0.0f) b = df_neg(b);
+  return a.hi == b.hi && a.lo == b.lo;
 }
 
 // Inserts (v, idx) into the descending top-4 (v, i); disc keeps the largest
@@ -125,14 +140,21 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+__device__ __forceinline__ float4 cdf_pack(const Cdf &a) {
+  return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
+}
+
+__device__ __forceinline__ Cdf cdf_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+
 template <int KM, int RPL>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(256)
     romp_f32_kernel(RompArgs a, int dT_in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int GS = GStride<KM>::v;
   const int M = a.M, J = a.J, H = a.H, R = a.R, K = a.K, kmax = a.kmax;
   const int HJ = H * J;
-  const Layout Lo = make_layout<KM>(M, J, H, R, dT_in_smem != 0);
+  const int warps = blockDim.x >> 5;
+  const Layout Lo = make_layout<KM>(M, J, H, R, K, warps, dT_in_smem != 0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // ---- block setup: twiddles (padded stride) and transposed atoms
@@ -159,8 +181,10 @@ __global__ void __launch_bounds__(kWarps * 32)
   double *s_L = reinterpret_cast<double *>(wbase + Lo.L_off);
   double *s_z = reinterpret_cast<double *>(wbase + Lo.z_off);
   double *s_a = reinterpret_cast<double *>(wbase + Lo.a_off);
+  float *s_adf = reinterpret_cast<float *>(wbase + Lo.adf_off);
   int *s_sel = reinterpret_cast<int *>(wbase + Lo.sel_off);
   double *s_gram = reinterpret_cast<double *>(wbase + Lo.gram_off);
+  float4 *s_A = reinterpret_cast<float4 *>(wbase + Lo.acache_off);
 
   // FP32 angle factors of this lane's angles r = lane + 32 i, harmonics 1..KM
   float tc[RPL][KM], ts[RPL][KM];
@@ -181,17 +205,25 @@ __global__ void __launch_bounds__(kWarps * 32)
   // of (b) adds gamma_{2kmax+1}; summed with the weights 1, 2 and bounded by
   // Cauchy-Schwarz (unit atoms) this is <= (4J + 4 kmax + 5) u ||r||.  The
   // factor 4 and the +8 are headroom.
-  const double err_per_norm = 4.0 * (4.0 * J + 4.0 * kmax + 8.0) * 5.9604644775390625e-8;
+  const float err_per_norm = 4.0f * (4.0f * J + 4.0f * kmax + 8.0f) * 5.9604644775390625e-8f;
 
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  for (int64_t p = (int64_t)blockIdx.x * kWarps + warp; p < a.P; p += nwarps) {
+  const int64_t nwarps = (int64_t)gridDim.x * warps;
+  for (int64_t it = (int64_t)blockIdx.x * warps + warp;; it += nwarps) {
+    int64_t p;
+    if (a.redo_list) {
+      if (it >= *a.redo_count) break;
+      p = a.redo_list[it];
+    } else {
+      if (it >= a.P) break;
+      p = it;
+    }
     const float *xp = a.x + p * (int64_t)(2 * HJ);
     // ---- load the patch; residual = x
     df acc = df_make(0.0f);
     for (int e = lane; e < HJ; e += 32) {
       float2 v = *reinterpret_cast<const float2 *>(xp + 2 * e);
-      int k = e / J;
-      if (k == 0) v.y = 0.0f;
+      const bool k0 = e < J;
+      if (k0) v.y = 0.0f;
       s_x[2 * e] = v.x;
       s_x[2 * e + 1] = v.y;
       s_rhi[2 * e] = v.x;
@@ -199,10 +231,12 @@ __global__ void __launch_bounds__(kWarps * 32)
       s_rlo[2 * e] = 0.0f;
       s_rlo[2 * e + 1] = 0.0f;
       df q = df_add(two_prod(v.x, v.x), two_prod(v.y, v.y));
-      acc = df_add(acc, k ? df_mul_f(q, 2.0f) : q);
+      acc = df_add(acc, k0 ? q : df_mul_f(q, 2.0f));
     }
-    const double xnorm = sqrt(fmax(df_to_d(df_warp_sum(acc)), 0.0));
-    double rnorm = xnorm;
+    acc = df_warp_sum(acc);
+    const float xnorm = sqrtf(fmaxf(acc.hi + acc.lo, 0.0f));
+    const float stop_level = (float)kStopRel * xnorm;
+    float rnorm = xnorm;
     __syncwarp();
 
     int t = 0;
@@ -213,31 +247,43 @@ __global__ void __launch_bounds__(kWarps * 32)
       float disc = -INFINITY;
       for (int mc = 0; mc < M; mc += kChunk) {
         const int mend = min(kChunk, M - mc);
+        // (a) one lane per atom: G_k = sum_j conj(d[j,k]) r[j,k]
         for (int ml = lane; ml < mend; ml += 32) {
           const int m = mc + ml;
-          float *gr = s_g + ml * GS;
-          for (int k = 0; k < H; ++k) {
-            float gre = 0.f, gim = 0.f;
-            for (int j = 0; j < J; ++j) {
-              const int e = k * J + j;
-              const float dre = dT[(size_t)e * M + m];
-              const float dim = dT[(size_t)(HJ + e) * M + m];
-              const float rre = s_rhi[2 * e], rim = s_rhi[2 * e + 1];
-              gre = fmaf(dre, rre, gre);
-              gre = fmaf(dim, rim, gre);
-              gim = fmaf(dre, rim, gim);
-              gim = fmaf(-dim, rre, gim);
-            }
-            if (k == 0) {
-              gr[0] = gre;
-            } else {
-              gr[2 * k - 1] = 2.0f * gre;
-              gr[2 * k] = -2.0f * gim;
+          float gv[GS];
+#pragma unroll
+          for (int q = 0; q < GS; ++q) gv[q] = 0.0f;
+          const float *pre = dT + m;
+          const float *pim = dT + (size_t)HJ * M + m;
+          const float2 *r2 = reinterpret_cast<const float2 *>(s_rhi);
+          int e = 0;
+#pragma unroll
+          for (int k = 0; k <= KM; ++k) {
+            if (k < H) {
+              float gre0 = 0.f, gre1 = 0.f, gim0 = 0.f, gim1 = 0.f;
+              for (int j = 0; j < J; ++j, ++e) {
+                const float dre = pre[(size_t)e * M], dim = pim[(size_t)e * M];
+                const float2 rv = r2[e];
+                gre0 = fmaf(dre, rv.x, gre0);
+                gre1 = fmaf(dim, rv.y, gre1);
+                gim0 = fmaf(dre, rv.y, gim0);
+                gim1 = fmaf(-dim, rv.x, gim1);
+              }
+              if (k == 0) {
+                gv[0] = gre0 + gre1;
+              } else {
+                gv[2 * k - 1] = 2.0f * (gre0 + gre1);
+                gv[2 * k] = -2.0f * (gim0 + gim1);
+              }
             }
           }
-          for (int q = 2 * H - 1; q < GS; ++q) gr[q] = 0.0f;
+          float4 *g4 = reinterpret_cast<float4 *>(s_g + ml * GS);
+#pragma unroll
+          for (int q = 0; q < GS / 4; ++q)
+            g4[q] = make_float4(gv[4 * q], gv[4 * q + 1], gv[4 * q + 2], gv[4 * q + 3]);
         }
         __syncwarp();
+        // (b) one lane per angle, (c) per-lane top-4
         for (int ml = 0; ml < mend; ++ml) {
           const float4 *g4 = reinterpret_cast<const float4 *>(s_g + ml * GS);
           float gv[GS];
@@ -251,22 +297,22 @@ __global__ void __launch_bounds__(kWarps * 32)
           }
 #pragma unroll
           for (int i = 0; i < RPL; ++i) {
-            float sc = gv[0];
+            float sa = gv[0], sb = 0.0f;
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
-              sc = fmaf(gv[2 * k + 1], tc[i][k], sc);
-              sc = fmaf(gv[2 * k + 2], ts[i][k], sc);
+              sa = fmaf(gv[2 * k + 1], tc[i][k], sa);
+              sb = fmaf(gv[2 * k + 2], ts[i][k], sb);
             }
             const int r = lane + 32 * i;
-            if (r < R) top4_insert(tv, ti, disc, fabsf(sc), (mc + ml) * R + r);
+            if (r < R) top4_insert(tv, ti, disc, fabsf(sa + sb), (mc + ml) * R + r);
           }
         }
         __syncwarp();
       }
       const float s1 = warp_max(tv[0]);
-      const double E = err_per_norm * rnorm;
-      if ((double)s1 + E <= kStopRel * xnorm) break;  // every exact score is below the stop level
-      const float thr = (float)((double)s1 - 2.0 * E);
+      const float E = err_per_norm * rnorm;
+      if (s1 + E <= stop_level) break;  // every exact score is below the stop level
+      const float thr = s1 - 2.0f * E;
       const bool overflow = __any_sync(0xffffffffu, disc >= thr);
 
       // ---- candidates, re-scored in double-float against the exact residual
@@ -284,79 +330,91 @@ __global__ void __launch_bounds__(kWarps * 32)
         ncand = M * R;
       }
       __syncwarp();
-      double best_v = -1.0;
+      df best_v = df_make(-1.0f);
       int best_c = -1;
       for (int ci = 0; ci < ncand; ++ci) {
         const int c = overflow ? ci : s_cand[ci];
-        const int m = c / R, r = c - (c / R) * R;
+        const int m = c / R, r = c - m * R;
         df s = df_make(0.0f);
         for (int e = lane; e < HJ; e += 32) {
-          Cdf A = steered_entry(a.d, H, J, m, r, e, tw);
+          const int k = e / J;
+          Cdf A = steered_entry(a.d, HJ, k, m, r, e, tw);
           df rr = {s_rhi[2 * e], s_rlo[2 * e]};
           df ri = {s_rhi[2 * e + 1], s_rlo[2 * e + 1]};
           df q = df_add(df_mul(A.re, rr), df_mul(A.im, ri));
-          s = df_add(s, (e >= J) ? df_mul_f(q, 2.0f) : q);
+          s = df_add(s, k ? df_mul_f(q, 2.0f) : q);
         }
-        const double v = fabs(df_to_d(df_warp_sum(s)));
-        if (v > best_v || (v == best_v && c < best_c)) {
-          best_v = v;
+        s = df_warp_sum(s);
+        if (df_abs_gt(s, best_v) || (df_abs_eq(s, best_v) && c < best_c)) {
+          best_v = s;
           best_c = c;
         }
       }
-      if (!(best_v > kStopRel * xnorm)) break;
+      if (best_c < 0 || !(fabsf(best_v.hi) > stop_level)) break;
 
-      // ---- (e) Gram row, diagonal and right-hand side of the new atom
-      const int mc_ = best_c / R, rc_ = best_c - (best_c / R) * R;
-      for (int i = 0; i <= t + 1; ++i) {
-        // i < t: <A_new, A_sel[i]>;  i == t: <A_new, A_new>;  i == t+1: <A_new, x>
-        df s = df_make(0.0f);
-        int mi = 0, ri = 0;
-        if (i < t) {
-          mi = s_sel[i] / R;
-          ri = s_sel[i] - mi * R;
-        }
+      // ---- (e) new steered atom (cached), its Gram row, diagonal, right-hand side
+      const int mn = best_c / R, rn = best_c - mn * R;
+      {
+        df sd = df_make(0.0f), sb = df_make(0.0f);
         for (int e = lane; e < HJ; e += 32) {
-          Cdf A = steered_entry(a.d, H, J, mc_, rc_, e, tw);
-          df q;
-          if (i < t) {
-            Cdf B = steered_entry(a.d, H, J, mi, ri, e, tw);
-            q = df_add(df_mul(A.re, B.re), df_mul(A.im, B.im));
-          } else if (i == t) {
-            q = df_add(df_mul(A.re, A.re), df_mul(A.im, A.im));
-          } else {
-            q = df_add(df_mul_f(A.re, s_x[2 * e]), df_mul_f(A.im, s_x[2 * e + 1]));
-          }
+          const int k = e / J;
+          Cdf A = steered_entry(a.d, HJ, k, mn, rn, e, tw);
+          s_A[t * HJ + e] = cdf_pack(A);
+          df qd = df_add(df_mul(A.re, A.re), df_mul(A.im, A.im));
+          df qb = df_add(df_mul_f(A.re, s_x[2 * e]), df_mul_f(A.im, s_x[2 * e + 1]));
+          sd = df_add(sd, k ? df_mul_f(qd, 2.0f) : qd);
+          sb = df_add(sb, k ? df_mul_f(qb, 2.0f) : qb);
+        }
+        sd = df_warp_sum(sd);
+        sb = df_warp_sum(sb);
+        if (lane == 0) {
+          s_gram[t] = df_to_d(sd);
+          s_gram[t + 1] = df_to_d(sb);
+        }
+      }
+      __syncwarp();
+      for (int i = 0; i < t; ++i) {
+        df s = df_make(0.0f);
+        for (int e = lane; e < HJ; e += 32) {
+          const Cdf A = cdf_unpack(s_A[t * HJ + e]);
+          const Cdf B = cdf_unpack(s_A[i * HJ + e]);
+          df q = df_add(df_mul(A.re, B.re), df_mul(A.im, B.im));
           s = df_add(s, (e >= J) ? df_mul_f(q, 2.0f) : q);
         }
         s = df_warp_sum(s);
-        if (lane == 0) s_gram[i] = df_to_d(s);
+        if (lane == 0) s_gram[K + 1 + i] = df_to_d(s);  // Gram row, after diag/rhs slots
       }
       __syncwarp();
       int ok = 0;
       if (lane == 0) {
-        // new row t of L (packed lower triangle, row i starts at i(i+1)/2)
+        // new row t of L (packed lower triangle, row i starts at i(i+1)/2); FP64
+        const double diag = s_gram[t], rhs = s_gram[t + 1];
         double *Lt = s_L + t * (t + 1) / 2;
-        double p2 = s_gram[t];
+        double p2 = diag;
         for (int i = 0; i < t; ++i) {
           const double *Li = s_L + i * (i + 1) / 2;
-          double v = s_gram[i];
+          double v = s_gram[K + 1 + i];
           for (int j = 0; j < i; ++j) v -= Li[j] * Lt[j];
           v /= Li[i];
           Lt[i] = v;
           p2 -= v * v;
         }
-        if (p2 > kPivotRel * s_gram[t]) {
+        if (p2 > kPivotRel * diag) {
           ok = 1;
           const double ltt = sqrt(p2);
           Lt[t] = ltt;
-          double zt = s_gram[t + 1];
+          double zt = rhs;
           for (int i = 0; i < t; ++i) zt -= Lt[i] * s_z[i];
           s_z[t] = zt / ltt;
           // back substitution L^T a = z over the t+1 selected atoms
           for (int i = t; i >= 0; --i) {
             double v = s_z[i];
             for (int q = i + 1; q <= t; ++q) v -= s_L[q * (q + 1) / 2 + i] * s_a[q];
-            s_a[i] = v / s_L[i * (i + 1) / 2 + i];
+            v /= s_L[i * (i + 1) / 2 + i];
+            s_a[i] = v;
+            const float hi = __double2float_rn(v);
+            s_adf[2 * i] = hi;
+            s_adf[2 * i + 1] = __double2float_rn(v - (double)hi);
           }
           s_sel[t] = best_c;
         }
@@ -372,21 +430,22 @@ __global__ void __launch_bounds__(kWarps * 32)
         df rr = df_make(s_x[2 * e]);
         df ri = df_make(s_x[2 * e + 1]);
         for (int i = 0; i < t; ++i) {
-          const int mi = s_sel[i] / R, rI = s_sel[i] - (s_sel[i] / R) * R;
-          Cdf A = steered_entry(a.d, H, J, mi, rI, e, tw);
-          const df ai = df_from_d(s_a[i]);
+          const Cdf A = cdf_unpack(s_A[i * HJ + e]);
+          const df ai = {s_adf[2 * i], s_adf[2 * i + 1]};
           rr = df_sub(rr, df_mul(ai, A.re));
           ri = df_sub(ri, df_mul(ai, A.im));
         }
-        if (e < J) ri = df_make(0.0f);
+        const bool k0 = e < J;
+        if (k0) ri = df_make(0.0f);
         s_rhi[2 * e] = rr.hi;
         s_rlo[2 * e] = rr.lo;
         s_rhi[2 * e + 1] = ri.hi;
         s_rlo[2 * e + 1] = ri.lo;
         df q = df_add(df_mul(rr, rr), df_mul(ri, ri));
-        nacc = df_add(nacc, (e >= J) ? df_mul_f(q, 2.0f) : q);
+        nacc = df_add(nacc, k0 ? q : df_mul_f(q, 2.0f));
       }
-      rnorm = sqrt(fmax(df_to_d(df_warp_sum(nacc)), 0.0));
+      nacc = df_warp_sum(nacc);
+      rnorm = sqrtf(fmaxf(nacc.hi + nacc.lo, 0.0f));
       __syncwarp();
     }
 
@@ -395,7 +454,7 @@ __global__ void __launch_bounds__(kWarps * 32)
       const int64_t o = p * K + i;
       if (i < t) {
         const int c = s_sel[i];
-        const int m = c / R, r = c - (c / R) * R;
+        const int m = c / R, r = c - m * R;
         a.atom[o] = m;
         a.angle_idx[o] = r;
         if (a.angle) a.angle[o] = (float)(6.283185307179586 * r / R);
@@ -407,7 +466,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         a.coef[o] = 0.0;
       }
     }
-    if (lane == 0 && a.resid_norm2) a.resid_norm2[p] = (float)(rnorm * rnorm);
+    if (lane == 0 && a.resid_norm2) a.resid_norm2[p] = rnorm * rnorm;
     __syncwarp();
   }
 }
@@ -422,23 +481,35 @@ int launch_t(const RompArgs &a, cudaStream_t stream) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int HJ = a.H * a.J;
   bool dT_smem = (size_t)2 * HJ * a.M * 4 <= 64 * 1024;
-  Layout L = make_layout<KM>(a.M, a.J, a.H, a.R, dT_smem);
+  int warps = 8;
+  Layout L = make_layout<KM>(a.M, a.J, a.H, a.R, a.K, warps, dT_smem);
+  while (L.total > max_optin && warps > 1) {
+    warps >>= 1;
+    L = make_layout<KM>(a.M, a.J, a.H, a.R, a.K, warps, dT_smem);
+  }
   if (L.total > max_optin && dT_smem) {
     dT_smem = false;
-    L = make_layout<KM>(a.M, a.J, a.H, a.R, false);
+    warps = 8;
+    L = make_layout<KM>(a.M, a.J, a.H, a.R, a.K, warps, false);
+    while (L.total > max_optin && warps > 1) {
+      warps >>= 1;
+      L = make_layout<KM>(a.M, a.J, a.H, a.R, a.K, warps, false);
+    }
   }
   if (L.total > max_optin) return RSC_ERR_UNSUPPORTED;
   auto kern = romp_f32_kernel<KM, RPL>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, L.total);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, L.total);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   if (per_sm < 1) return RSC_ERR_UNSUPPORTED;
-  int64_t need = (a.P + kWarps - 1) / kWarps;
   int64_t grid = (int64_t)nsm * per_sm;
-  if (need < grid) grid = need;
-  kern<<<(unsigned)grid, kWarps * 32, L.total, stream>>>(a, dT_smem ? 1 : 0);
+  if (!a.redo_list) {
+    const int64_t need = (a.P + warps - 1) / warps;
+    if (need < grid) grid = need;
+  }
+  kern<<<(unsigned)grid, warps * 32, L.total, stream>>>(a, dT_smem ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return RSC_OK;

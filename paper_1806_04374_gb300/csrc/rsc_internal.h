@@ -44,6 +44,9 @@ struct RompArgs {
   float *resid_norm2;
   int *err;
   unsigned long long *fallbacks;
+  // when set, code only patches redo_list[0 .. *redo_count) (device memory)
+  const int *redo_list = nullptr;
+  const int *redo_count = nullptr;
 };
 
 // FP32 CUDA-core scoring path (romp_f32.cu).
