@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256)
         ncand = M * R;
       }
       __syncwarp();
-      df best_v = df_make(-1.0f);
+      df best_v = df_make(0.0f);
       int best_c = -1;
       for (int ci = 0; ci < ncand; ++ci) {
         const int c = overflow ? ci : s_cand[ci];
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(256)
           s = df_add(s, k ? df_mul_f(q, 2.0f) : q);
         }
         s = df_warp_sum(s);
-        if (df_abs_gt(s, best_v) || (df_abs_eq(s, best_v) && c < best_c)) {
+        if (best_c < 0 || df_abs_gt(s, best_v) || (df_abs_eq(s, best_v) && c < best_c)) {
           best_v = s;
           best_c = c;
         }

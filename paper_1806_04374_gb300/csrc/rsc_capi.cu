@@ -5,6 +5,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cuda_bf16.h>
+
 #include <vector>
 
 #include "rsc_internal.h"
@@ -28,7 +30,100 @@ void free_dict(rsc_dict *d) {
   cudaFree(d->err);
   cudaFree(d->fallbacks);
   cudaFree(d->steered_bf16);
+  cudaFree(d->xgram);
   delete d;
+}
+
+uint16_t bf16_bits(double v) {
+  const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+  return *reinterpret_cast<const uint16_t *>(&b);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tables of the tensor-core path: the packed steered dictionary (bf16, one
+// row per (m, r), the packed layout described in rsc_internal.h), the
+// per-harmonic cross-Gram table H_k(a, b) in double-float and the TMA map.
+// Returns RSC_OK also when the sizes are outside the path (tables left null).
+int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
+  const int M = d->M, J = d->J, H = d->H, R = d->R, HJ = H * J;
+  const int n = J + 2 * d->kmax * J;
+  d->n = n;
+  const size_t rows = (size_t)M * R;
+  if (n > kTcMaxN || rows * kTcKst * 2 > ((size_t)1 << 30) ||
+      (size_t)M * M * H * 16 > ((size_t)1 << 28))
+    return RSC_OK;
+  std::vector<uint16_t> B(rows * kTcKst, 0);
+  for (int m = 0; m < M; ++m)
+    for (int r = 0; r < R; ++r) {
+      uint16_t *row = &B[((size_t)m * R + r) * kTcKst];
+      for (int k = 0; k < H; ++k) {
+        const double th = 2.0 * M_PI * (double)(((int64_t)k * r) % R) / (double)R;
+        const double c = cos(th), s = sin(th);
+        for (int j = 0; j < J; ++j) {
+          const double dre = h[((size_t)m * HJ + k * J + j) * 2];
+          const double dim = k ? h[((size_t)m * HJ + k * J + j) * 2 + 1] : 0.0;
+          const double re = c * dre + s * dim, im = c * dim - s * dre;
+          if (k == 0) {
+            row[j] = bf16_bits(re);
+          } else {
+            const int q = J + 2 * ((k - 1) * J + j);
+            row[q] = bf16_bits(M_SQRT2 * re);
+            row[q + 1] = bf16_bits(M_SQRT2 * im);
+          }
+        }
+      }
+    }
+  std::vector<float4> X((size_t)M * M * H);
+  for (int ma = 0; ma < M; ++ma)
+    for (int mb = 0; mb < M; ++mb)
+      for (int k = 0; k < H; ++k) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < J; ++j) {
+          const double ar = h[((size_t)ma * HJ + k * J + j) * 2];
+          const double ai = k ? h[((size_t)ma * HJ + k * J + j) * 2 + 1] : 0.0;
+          const double br = h[((size_t)mb * HJ + k * J + j) * 2];
+          const double bi = k ? h[((size_t)mb * HJ + k * J + j) * 2 + 1] : 0.0;
+          re += ar * br + ai * bi;  // conj(a) b
+          im += ar * bi - ai * br;
+        }
+        const float rh = (float)re, ih = (float)im;
+        X[((size_t)ma * M + mb) * H + k] =
+            make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+      }
+  cudaError_t e = cudaMalloc(&d->steered_bf16, B.size() * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&d->xgram, X.size() * sizeof(float4));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return RSC_ERR_OOM;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->steered_bf16, B.data(), B.size() * 2, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->xgram, X.data(), X.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return rsc_cuda_fail(e);
+  const cuuint64_t gdim[2] = {(cuuint64_t)kTcKst, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)kTcKst * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)kTcBN};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult cr = reinterpret_cast<EncodeTiledFn>(fn)(
+      &d->tmap_b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, d->steered_bf16, gdim, gstride, box, estr,
+      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    snprintf(g_cuda_msg, sizeof g_cuda_msg, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    return RSC_ERR_CUDA;
+  }
+  return RSC_OK;
 }
 
 int check_device(const rsc_dict *d) {
@@ -145,6 +240,11 @@ int rsc_dict_create(const float *coef, rsc_dims dims, void *stream, rsc_dict **o
     free_dict(d);
     return rsc_cuda_fail(e);
   }
+  const int rc = build_tc_tables(d, h, st);
+  if (rc != RSC_OK) {
+    free_dict(d);
+    return rc;
+  }
   *out = d;
   return RSC_OK;
 }
@@ -197,7 +297,52 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   a.fallbacks = dict->fallbacks;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (prec == RSC_FP32) return rsc_launch_f32(a, st);
-  return RSC_ERR_UNSUPPORTED;
+
+  // BF16 tensor-core scoring; patches it hands back are coded by the FP32 path
+  if (!dict->steered_bf16 || K > kTcMaxK || P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
+  int *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (P + 4) * sizeof(int), st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return RSC_ERR_OOM;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, sizeof(int), st);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  TcArgs ta;
+  ta.x = x;
+  ta.P = P;
+  ta.K = K;
+  ta.M = dict->M;
+  ta.J = dict->J;
+  ta.kmax = dict->kmax;
+  ta.R = dict->R;
+  ta.H = dict->H;
+  ta.n = dict->n;
+  ta.ksteps = (dict->n + 15) / 16;
+  ta.MR = dict->M * dict->R;
+  ta.nchunks = (ta.MR + kTcBN - 1) / kTcBN;
+  ta.d = dict->d;
+  ta.tw = dict->tw;
+  ta.xgram = dict->xgram;
+  ta.atom = atom;
+  ta.angle_idx = angle_idx;
+  ta.angle = angle;
+  ta.coef = coef;
+  ta.resid_norm2 = resid_norm2;
+  ta.err = dict->err;
+  ta.redo_count = scratch;
+  ta.redo_list = scratch + 4;
+  ta.fallbacks = dict->fallbacks;
+  rc = rsc_launch_tc(ta, dict->tmap_b, st);
+  if (rc == RSC_OK) {
+    a.redo_count = ta.redo_count;
+    a.redo_list = ta.redo_list;
+    a.fallbacks = nullptr;
+    rc = rsc_launch_f32(a, st);
+  }
+  e = cudaFreeAsync(scratch, st);
+  if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
+  return rc;
 }
 
 int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,

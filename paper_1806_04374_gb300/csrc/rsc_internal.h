@@ -1,6 +1,7 @@
 // rsc_internal.h -- state shared by the host side of librsc and its kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,10 +25,45 @@ struct rsc_dict {
   float *tw;     // [4][H][R]     cos hi, cos lo, sin hi, sin lo of 2 pi k r / R
   int *err;      // device error word (first error code recorded)
   unsigned long long *fallbacks;  // device counter of exact re-scans
-  // tensor-core path (bf16 steered dictionary), built lazily
-  void *steered_bf16;    // [M*R][Kpad] bf16, row (m*R + r) = packed S_r d_m
-  int kpad;              // padded contraction depth (multiple of 16)
+  // tensor-core path: steered dictionary and cross-Gram table (null when the
+  // sizes are outside what the path handles)
+  void *steered_bf16;    // [M*R][kTcKst] bf16, row m*R + r = packed S_r d_m
+  float4 *xgram;         // [M][M][H] double-float complex H_k(a,b) = sum_j conj(d_a) d_b
+  int n;                 // packed real length J (2 kmax + 1)
+  CUtensorMap tmap_b;    // TMA map of steered_bf16, box 64 x kTcBN, 128B swizzle
 };
+
+// Packed real coordinates of a half spectrum, shared by the tensor-core
+// operands: slot q < J is Re c[j=q, k=0]; slot J + 2 ((k-1) J + j) + c holds
+// sqrt(2) Re (c = 0) or sqrt(2) Im (c = 1) of c[j, k], k >= 1.  The Euclidean
+// dot product of two packed vectors is the coefficient inner product.
+constexpr int kTcKst = 112;  // stored row length of the steered dictionary (bf16)
+constexpr int kTcMaxN = 112; // packed lengths the tensor-core path handles
+constexpr int kTcBN = 128;   // steered atoms per MMA (N) and per TMA box
+constexpr int kTcMaxK = 8;   // greedy steps the tensor-core path handles
+
+struct TcArgs {
+  const float *x;
+  int64_t P;
+  int K;
+  int M, J, kmax, R, H, n, ksteps, MR, nchunks;
+  const float *d;
+  const float *tw;
+  const float4 *xgram;
+  int32_t *atom;
+  int32_t *angle_idx;
+  float *angle;
+  double *coef;
+  float *resid_norm2;
+  int *err;
+  int *redo_list;
+  int *redo_count;
+  unsigned long long *fallbacks;
+};
+
+// BF16 tensor-core scoring path (romp_tc.cu); patches whose candidates
+// overflow are appended to redo_list for the FP32 path.
+int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream);
 
 struct RompArgs {
   const float *x;

@@ -38,7 +38,7 @@ def run_gpu(rsc, x, d, R, K, precision="fp32"):
     return res
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_small_workload_full(rsc, precision):
     """1000 patches, M=16, R=32, K=3, sigma 0.05 (plus 3 ragged extra)."""
     d, x, _, wl = synth.workload_inputs("omp_small")
@@ -50,7 +50,7 @@ def test_small_workload_full(rsc, precision):
     print(precision, s, "fallbacks", g["fallbacks"])
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_1m_workload_sampled(rsc, precision):
     """The 1,000,000-patch workload (M=64, R=64, K=5) coded in one launch as
     the benchmark does; 768 sampled patches (incl. the first and last) are
@@ -82,17 +82,30 @@ CASES = [
 ]
 
 
+def tc_supported(J, kmax, K):
+    """Shapes the tensor-core path handles: packed length J(2 kmax + 1) <= 112
+    and K <= 8."""
+    return J * (2 * kmax + 1) <= 112 and K <= 8
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_edge_shapes(rsc, case):
+def test_edge_shapes(rsc, case, precision):
     name, M, J, kmax, R, K, P, n_terms, sigma = case
     d = synth.make_dictionary(M, J, kmax, 1000 + M + R)
     x, _ = synth.make_patches(d, P, n_terms, sigma, 2000 + R)
-    g = run_gpu(rsc, x, d, R, K)
-    s = check(x, d, R, K, g, COEF_TOL["fp32"])
-    print(name, s, "fallbacks", g["fallbacks"])
+    if precision == "bf16" and not tc_supported(J, kmax, K):
+        with pytest.raises(rsc.RscError) as ei:
+            run_gpu(rsc, x, d, R, K, precision)
+        assert ei.value.status == rsc.RSC_ERR_UNSUPPORTED
+        return
+    g = run_gpu(rsc, x, d, R, K, precision)
+    s = check(x, d, R, K, g, COEF_TOL[precision])
+    print(name, precision, s, "fallbacks", g["fallbacks"])
 
 
-def test_degenerate_patches(rsc):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_degenerate_patches(rsc, precision):
     """Zero patch (no step), exactly one steered atom on the grid (one step,
     then stop), and an exactly sparse patch recovered with zero residual."""
     M, J, kmax, R = 6, 6, 8, 8
@@ -101,23 +114,24 @@ def test_degenerate_patches(rsc):
     q = oracle.steer(d[1].astype(np.float64), 2 * np.pi * 2 / R)  # a quarter turn: exact
     xs.append(q.astype(np.float32))
     x = np.stack(xs)
-    g = run_gpu(rsc, x, d, R, 3)
+    g = run_gpu(rsc, x, d, R, 3, precision)
     assert np.all(g["atom"][0] == -1) and np.all(g["coef"][0] == 0)
     assert g["atom"][1, 0] == 3 and g["angle_idx"][1, 0] == 0 and np.all(g["atom"][1, 1:] == -1)
     assert g["atom"][2, 0] == 1 and g["angle_idx"][2, 0] == 2 and np.all(g["atom"][2, 1:] == -1)
     assert abs(g["coef"][1, 0] - 1.0) < 1e-9 and abs(g["coef"][2, 0] - 1.0) < 1e-9
-    check(x, d, R, 3, g, COEF_TOL["fp32"])
+    check(x, d, R, 3, g, COEF_TOL[precision])
 
 
-def test_rotation_covariance_gpu(rsc):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_rotation_covariance_gpu(rsc, precision):
     """Rotating every patch by s grid steps shifts every GPU-selected angle by
     s (Eq. 3) wherever the oracle's margins pin the selections."""
     d, x, _, wl = synth.workload_inputs("omp_small", P=200)
     s = 5
     xr = np.stack([oracle.steer(v.astype(np.float64), 2 * np.pi * s / wl.R) for v in x]).astype(
         np.float32)
-    g0 = run_gpu(rsc, x, d, wl.R, wl.K)
-    g1 = run_gpu(rsc, xr, d, wl.R, wl.K)
+    g0 = run_gpu(rsc, x, d, wl.R, wl.K, precision)
+    g1 = run_gpu(rsc, xr, d, wl.R, wl.K, precision)
     o0 = oracle.romp(x, d, wl.R, wl.K)
     o1 = oracle.romp(xr, d, wl.R, wl.K)
     ok = np.all(o0["margin"] > 1e-4, axis=1) & np.all(o1["margin"] > 1e-4, axis=1)
@@ -159,15 +173,32 @@ def test_empty_and_errors(rsc):
         rsc.Dictionary(torch.from_numpy(d).cuda(), 129)
 
 
-def test_host_entry_point_matches_device(rsc):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_host_entry_point_matches_device(rsc, precision):
     """rsc_encode_host (chunked copies + coding on two streams) returns the
     same codes as rsc_encode on device buffers."""
     import torch
     d, x, _, wl = synth.workload_inputs("omp_1m", P=300_000)
     dic = rsc.Dictionary(torch.from_numpy(d).cuda(), wl.R)
     xd = torch.from_numpy(x).cuda()
-    a = rsc.encode(dic, xd, wl.K)
+    a = rsc.encode(dic, xd, wl.K, precision)
     torch.cuda.synchronize()
-    b = rsc.encode_host(dic, torch.from_numpy(x).pin_memory(), wl.K)
+    b = rsc.encode_host(dic, torch.from_numpy(x).pin_memory(), wl.K, precision)
     for k in ("atom", "angle_idx", "coef", "resid_norm2", "angle"):
         assert np.array_equal(a[k].cpu().numpy(), b[k].numpy()), k
+
+
+def test_bf16_and_fp32_paths_agree(rsc):
+    """Both scoring paths certify their picks against exact re-scoring, so on
+    the 1M workload they return the same selections wherever the oracle's
+    margin pins them; compared here on every patch of the first 200k, with
+    the weights equal to ~1e-12 relative (both solve the same FP64 system)."""
+    d, x, _, wl = synth.workload_inputs("omp_1m", P=200_000)
+    g32 = run_gpu(rsc, x, d, wl.R, wl.K, "fp32")
+    g16 = run_gpu(rsc, x, d, wl.R, wl.K, "bf16")
+    same = np.all((g32["atom"] == g16["atom"]) & (g32["angle_idx"] == g16["angle_idx"]), axis=1)
+    assert same.mean() > 0.9999, same.mean()
+    rel = np.abs(g32["coef"][same] - g16["coef"][same]).max() / np.abs(g32["coef"]).max()
+    assert rel < 1e-9, rel
+    print("identical patches", same.sum(), "of", same.size, "max rel coef diff", rel,
+          "bf16 handed to fp32:", g16["fallbacks"])
