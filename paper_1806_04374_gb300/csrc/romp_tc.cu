@@ -161,8 +161,8 @@ __device__ df gram_entry(const float4 *__restrict__ xg, int M, int H, int R, int
   df acc = df_make(0.0f);
   for (int k = 0; k < H; ++k) {
     const float4 v = __ldg(h + k);
-    const int idx = (int)(((int64_t)k * dr) % R);
-    df term = df_sub(df_mul(tw.cosv(k, idx), df{v.x, v.y}), df_mul(tw.sinv(k, idx), df{v.z, v.w}));
+    // the table row k already holds the angles k * 2 pi r / R
+    df term = df_sub(df_mul(tw.cosv(k, dr), df{v.x, v.y}), df_mul(tw.sinv(k, dr), df{v.z, v.w}));
     acc = df_add(acc, k ? df_mul_f(term, 2.0f) : term);
   }
   return acc;
