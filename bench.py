@@ -34,11 +34,21 @@ FP32_LANES_PER_SM = 128
 
 
 def algorithmic_flops_per_patch(wl) -> dict:
-    """Per patch per greedy step: (a) contraction 2J(1+4kmax)M, (b) direct
-    angle transform M R (4kmax+1); times K steps."""
+    """Per patch per greedy step: (a) per-harmonic contraction 2J(1+4kmax)M
+    flops, (b) angle transform 2.5 R log2(R) flops per atom (radix-2
+    convention; the direct form is M R (4kmax+1)); times K steps."""
+    import math
     fa = 2 * wl.J * (1 + 4 * wl.kmax) * wl.M
-    fb = wl.M * wl.R * (4 * wl.kmax + 1)
-    return {"a": fa, "b": fb, "per_patch": wl.K * (fa + fb)}
+    fb = int(2.5 * wl.R * math.log2(wl.R) * wl.M)
+    fb_direct = wl.M * wl.R * (4 * wl.kmax + 1)
+    return {"a": fa, "b": fb, "b_direct": fb_direct, "per_patch": wl.K * (fa + fb)}
+
+
+def mma_flops_per_patch(wl) -> int:
+    """Dense flops the tensor-core path executes per patch: K steps x
+    2 x (padded depth 112) x (M R steered atoms)."""
+    n = wl.J * (2 * wl.kmax + 1)
+    return wl.K * 2 * (((n + 15) // 16) * 16) * wl.M * wl.R
 
 
 def algorithmic_bytes_per_patch(wl) -> int:
@@ -172,7 +182,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip timing the plain FP32 path beside the headline path")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--patches", type=int, default=None, help="override P (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -216,35 +228,50 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            rsc.encode(dic, xd, K, args.precision, stream=stream, out=out)
-        stream.synchronize()
+    def timed(precision: str, sample_clocks: bool):
+        """W warm-up steps, then K timed steps between barriers; returns the
+        step times, the max-over-ranks total, clocks, hand-offs and the
+        per-kernel event times recorded by the library."""
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                rsc.encode(dic, xd, K, precision, stream=stream, out=out)
+            stream.synchronize()
+            if rsc.rsc_dict_check(dic.handle, int(stream.cuda_stream)) != 0:
+                raise RuntimeError("device-side error during warm-up")
+            rsc.rsc_dict_fallback_count(dic.handle)
+            rsc.rsc_dict_set_timing(dic.handle, True)
+            rsc.rsc_dict_timing(dic.handle)
+            barrier()
+            torch.cuda.synchronize(dev)
+            clocks = ClockSampler(dev.index if dev.index is not None else 0) if sample_clocks else None
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            evs[0].record(stream)
+            for s in range(args.steps):
+                rsc.encode(dic, xd, K, precision, stream=stream, out=out)
+                evs[s + 1].record(stream)
+            stream.synchronize()
+            torch.cuda.synchronize(dev)
+            barrier()
+            clk = clocks.stop() if clocks else None
+        step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        total_ms = evs[0].elapsed_time(evs[-1])
         if rsc.rsc_dict_check(dic.handle, int(stream.cuda_stream)) != 0:
-            raise RuntimeError("device-side error during warm-up")
-        rsc.rsc_dict_fallback_count(dic.handle)
+            raise RuntimeError("device-side error during the timed steps")
+        kms, kn = rsc.rsc_dict_timing(dic.handle)
+        rsc.rsc_dict_set_timing(dic.handle, False)
+        handoffs = rsc.rsc_dict_fallback_count(dic.handle)
+        if world > 1:
+            tt = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(tt.item())
+        return {"step_ms": step_ms, "total_ms": total_ms, "clocks": clk, "handoffs": handoffs,
+                "kernel_ms": kms, "kernel_launches": kn}
 
-        barrier()
-        torch.cuda.synchronize(dev)
-        clocks = ClockSampler(dev.index if dev.index is not None else 0)
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        evs[0].record(stream)
-        for s in range(args.steps):
-            rsc.encode(dic, xd, K, args.precision, stream=stream, out=out)
-            evs[s + 1].record(stream)
-        stream.synchronize()
-        torch.cuda.synchronize(dev)
-        barrier()
-        clk = clocks.stop()
-    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if rsc.rsc_dict_check(dic.handle, int(stream.cuda_stream)) != 0:
-        raise RuntimeError("device-side error during the timed steps")
-    fallbacks = rsc.rsc_dict_fallback_count(dic.handle)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    main_run = timed(args.precision, True)
+    cmp_run = None
+    if args.precision != "fp32" and not args.no_fp32_compare:
+        cmp_run = timed("fp32", False)
+    step_ms, total_ms, clk = main_run["step_ms"], main_run["total_ms"], main_run["clocks"]
     ms_per_step = total_ms / args.steps
     value = world * P * args.steps / (total_ms / 1e3)
 
@@ -273,11 +300,21 @@ def main():
 
     if rank == 0:
         fl = algorithmic_flops_per_patch(wl)
-        launch_s = float(np.mean(step_ms)) / 1e3  # one kernel launch per step
+        # dominant kernel: the scoring kernel of the path (phase 0 events)
+        launch_s = main_run["kernel_ms"][0] / max(main_run["kernel_launches"][0], 1) / 1e3
         achieved = fl["per_patch"] * P / launch_s / 1e12
         sm_max = (clk or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peaks = measured_peaks()
+        if args.precision == "bf16":
+            kname, bound = "romp_tc_kernel", "tensor"
+            peak = peaks.get("bf16_tflops") or 1900.0
+            peak_note = ("dense bf16, MEASURED_PEAKS burst" if peaks.get("bf16_tflops")
+                         else "dense bf16, fallback 1.9 PFLOP/s")
+        else:
+            kname, bound = "romp_f32_kernel", "alu"
+            peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+            peak_note = f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz"
         line = {
             "metric": METRIC,
             "value": value,
@@ -294,7 +331,9 @@ def main():
             "config": {
                 "workload": f"{WORKLOAD}: P={P} patches/GPU, n=102 (J=6, kmax=8), M=64, R=64, "
                             f"K=5, 3 planted atoms + noise 0.1",
-                "path": f"{args.precision} scoring + double-float re-scoring + FP64 Cholesky",
+                "path": (f"{args.precision} scoring ("
+                         + ("tcgen05 tensor cores" if args.precision == "bf16" else "CUDA cores")
+                         + ") + double-float re-scoring + FP64 Cholesky"),
                 "l2": "inputs (432 MB) larger than L2, no flush",
                 "parallelism": f"dp{world} (patches sharded, no collective)",
             },
@@ -302,26 +341,38 @@ def main():
                            "p99": float(np.percentile(step_ms, 99)),
                            "unit": "one step (all patches of one GPU)"},
             "roofline": {
-                "kernel": "romp_f32_kernel",
-                "bound": "alu",
+                "kernel": kname,
+                "bound": bound,
                 "achieved": achieved,
                 "peak": peak,
                 "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": None,
                 "flops_per_patch": fl["per_patch"],
-                "peak_note": f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                             f"{sm_max:.0f} MHz",
+                "flops_convention": "(a) 2J(1+4kmax)M + (b) 2.5 R log2 R M per patch-step, x K",
+                "kernel_ms": launch_s * 1e3,
+                "peak_note": peak_note,
             },
             "hbm": {"algorithmic_bytes_per_patch": algorithmic_bytes_per_patch(wl),
                     "achieved_gbs": algorithmic_bytes_per_patch(wl) * P / launch_s / 1e9,
                     "peak_gbs": measured_peaks().get("hbm_gbs")},
             "e2e": {"value": world * P * e2e_steps / t_e2e, "unit": "patches/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps,
-            "exact_rescans": fallbacks,
+            "gpu_launches": int(sum(main_run["kernel_launches"])),
+            "handoffs": main_run["handoffs"],
+            "kernel_ms_per_step": [t / args.steps for t in main_run["kernel_ms"]],
             "clocks": clk,
         }
+        if args.precision == "bf16":
+            mf = mma_flops_per_patch(wl)
+            line["mma_executed"] = {"flops_per_patch": mf,
+                                    "tflops": mf * P / launch_s / 1e12,
+                                    "frac_of_peak": mf * P / launch_s / 1e12 / peak}
+        if cmp_run is not None:
+            v32 = world * P * args.steps / (cmp_run["total_ms"] / 1e3)
+            line["fp32_path"] = {"value": v32, "unit": "patches/s",
+                                 "ms_per_step": cmp_run["total_ms"] / args.steps,
+                                 "speedup_of_headline": value / v32}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(d, x, wl)
         print(json.dumps(line))

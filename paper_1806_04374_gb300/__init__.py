@@ -29,8 +29,8 @@ PRECISIONS = {"fp32": RSC_FP32, "bf16": RSC_BF16_RESCORE}
 # every symbol include/rsc.h declares
 EXPORTS = (
     "rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode", "rsc_encode_host",
-    "rsc_dict_check", "rsc_dict_fallback_count", "rsc_status_string", "rsc_last_cuda_error",
-    "rsc_version",
+    "rsc_dict_check", "rsc_dict_fallback_count", "rsc_dict_set_timing", "rsc_dict_timing",
+    "rsc_status_string", "rsc_last_cuda_error", "rsc_version",
 )
 
 
@@ -67,13 +67,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_encode_host.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.rsc_dict_check.argtypes = [vp, vp]
     lib.rsc_dict_fallback_count.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.rsc_dict_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.rsc_dict_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.rsc_status_string.argtypes = [ctypes.c_int]
     lib.rsc_status_string.restype = ctypes.c_char_p
     lib.rsc_last_cuda_error.argtypes = []
     lib.rsc_last_cuda_error.restype = ctypes.c_char_p
     lib.rsc_version.argtypes = []
     for name in ("rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode",
-                 "rsc_encode_host", "rsc_dict_check", "rsc_dict_fallback_count", "rsc_version"):
+                 "rsc_encode_host", "rsc_dict_check", "rsc_dict_fallback_count",
+                 "rsc_dict_set_timing", "rsc_dict_timing", "rsc_version"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -134,6 +137,20 @@ def rsc_dict_fallback_count(handle: int) -> int:
     if st != RSC_OK:
         raise RscError(st, "rsc_dict_fallback_count")
     return v.value
+
+
+def rsc_dict_set_timing(handle: int, enable: bool) -> int:
+    return load_library().rsc_dict_set_timing(ctypes.c_void_p(handle), int(bool(enable)))
+
+
+def rsc_dict_timing(handle: int):
+    """Returns ([ms phase 0, ms phase 1], [launches phase 0, launches phase 1])."""
+    ms = (ctypes.c_double * 2)()
+    n = (ctypes.c_int64 * 2)()
+    st = load_library().rsc_dict_timing(ctypes.c_void_p(handle), ms, n)
+    if st != RSC_OK:
+        raise RscError(st, "rsc_dict_timing")
+    return [ms[0], ms[1]], [n[0], n[1]]
 
 
 # ----------------------------------------------------------- torch helpers

@@ -22,8 +22,51 @@ bool aligned_as(const void *p) {
   return (reinterpret_cast<uintptr_t>(p) % alignof(T)) == 0;
 }
 
+struct TimedPair {
+  int phase;
+  cudaEvent_t a, b;
+};
+typedef std::vector<TimedPair> TimingLog;
+
+void clear_timing(rsc_dict *d) {
+  TimingLog *log = static_cast<TimingLog *>(d->timing_state);
+  if (!log) return;
+  for (auto &p : *log) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  log->clear();
+}
+
+// Records the start event of a timed launch; returns its slot or -1.
+int timing_begin(const rsc_dict *dc, int phase, cudaStream_t st) {
+  rsc_dict *d = const_cast<rsc_dict *>(dc);
+  if (!d->timing) return -1;
+  TimingLog *log = static_cast<TimingLog *>(d->timing_state);
+  if (!log) {
+    log = new TimingLog();
+    d->timing_state = log;
+  }
+  TimedPair p{phase, nullptr, nullptr};
+  if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  cudaEventRecord(p.a, st);
+  log->push_back(p);
+  return (int)log->size() - 1;
+}
+
+void timing_end(const rsc_dict *d, int slot, cudaStream_t st) {
+  if (slot < 0) return;
+  TimingLog *log = static_cast<TimingLog *>(d->timing_state);
+  cudaEventRecord((*log)[slot].b, st);
+}
+
 void free_dict(rsc_dict *d) {
   if (!d) return;
+  clear_timing(d);
+  delete static_cast<TimingLog *>(d->timing_state);
   cudaFree(d->d);
   cudaFree(d->dT);
   cudaFree(d->tw);
@@ -296,7 +339,12 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   a.err = dict->err;
   a.fallbacks = dict->fallbacks;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (prec == RSC_FP32) return rsc_launch_f32(a, st);
+  if (prec == RSC_FP32) {
+    const int slot = timing_begin(dict, 0, st);
+    rc = rsc_launch_f32(a, st);
+    timing_end(dict, slot, st);
+    return rc;
+  }
 
   // BF16 tensor-core scoring; patches it hands back are coded by the FP32 path
   if (!dict->steered_bf16 || K > kTcMaxK || P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
@@ -333,12 +381,16 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   ta.redo_count = scratch;
   ta.redo_list = scratch + 4;
   ta.fallbacks = dict->fallbacks;
+  int slot = timing_begin(dict, 0, st);
   rc = rsc_launch_tc(ta, dict->tmap_b, st);
+  timing_end(dict, slot, st);
   if (rc == RSC_OK) {
     a.redo_count = ta.redo_count;
     a.redo_list = ta.redo_list;
     a.fallbacks = nullptr;
+    slot = timing_begin(dict, 1, st);
     rc = rsc_launch_f32(a, st);
+    timing_end(dict, slot, st);
   }
   e = cudaFreeAsync(scratch, st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
@@ -432,6 +484,35 @@ int rsc_dict_check(const rsc_dict *dict, void *stream) {
   if (e == cudaSuccess) e = cudaMemset(dict->err, 0, sizeof(int));
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return v;
+}
+
+int rsc_dict_set_timing(rsc_dict *dict, int enable) {
+  if (!dict) return RSC_ERR_INVALID;
+  dict->timing = enable ? 1 : 0;
+  return RSC_OK;
+}
+
+int rsc_dict_timing(rsc_dict *dict, double ms[2], int64_t launches[2]) {
+  if (!dict || !ms || !launches) return RSC_ERR_INVALID;
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  TimingLog *log = static_cast<TimingLog *>(dict->timing_state);
+  int rc = RSC_OK;
+  if (log) {
+    for (auto &p : *log) {
+      cudaError_t e = cudaEventSynchronize(p.b);
+      float t = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.a, p.b);
+      if (e != cudaSuccess) {
+        rc = rsc_cuda_fail(e);
+        break;
+      }
+      ms[p.phase] += t;
+      launches[p.phase] += 1;
+    }
+    clear_timing(dict);
+  }
+  return rc;
 }
 
 int rsc_dict_fallback_count(const rsc_dict *dict, int64_t *count) {

@@ -30,6 +30,9 @@ struct rsc_dict {
   void *steered_bf16;    // [M*R][kTcKst] bf16, row m*R + r = packed S_r d_m
   float4 *xgram;         // [M][M][H] double-float complex H_k(a,b) = sum_j conj(d_a) d_b
   int n;                 // packed real length J (2 kmax + 1)
+  // per-phase timing (diagnostic): event pairs recorded around launches
+  int timing;
+  void *timing_state;    // owned std::vector of recorded pairs, see rsc_capi.cu
   CUtensorMap tmap_b;    // TMA map of steered_bf16, box 64 x kTcBN, 128B swizzle
 };
 
