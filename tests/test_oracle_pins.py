@@ -329,3 +329,12 @@ def test_generator_recovers_truth_on_small_workload():
         r_near = int(np.round(truth["theta"][p, i] * wl.R / (2 * np.pi))) % wl.R
         hit += (o["atom"][p, 0] == truth["atom"][p, i]) and (o["angle"][p, 0] == r_near)
     assert hit > 120
+
+
+def test_scores_equal_packed_augmented_products():
+    """oracle.scores(x) = [pack(S_r d_m) . pack(x)] for every (m, r)."""
+    d, x, _ = small_case(17, M=5, R=12, P=3)
+    Aug = augmented_packed(d, 12)
+    for p in range(3):
+        s = oracle.scores(x[p], d, 12)
+        assert np.allclose(s.ravel(), Aug.T @ pack(x[p]), atol=1e-12)
