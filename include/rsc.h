@@ -128,6 +128,34 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
                     float *resid_norm2);
 
 /*
+ * rsc_encode_noalloc -- the RSC_BF16_RESCORE path of rsc_encode, for callers
+ * that cannot allocate device memory while they code (a server that reserves
+ * all of its memory up front and forbids allocation in steady state, code
+ * that runs inside another framework's memory pool, or latency-bound callers
+ * that must not meet an allocation failure or an allocator synchronisation
+ * mid-request).  rsc_encode takes its one per-call scratch buffer (the list
+ * of patches the tensor-core kernel hands to the FP32 kernel) from the
+ * stream-ordered allocator; this call uses a fixed 4 MiB device array inside
+ * the library instead and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The paper has no counterpart: it is a property of this library.
+ *   Arguments and outputs: as rsc_encode with prec = RSC_BF16_RESCORE.
+ *   Limits: P <= 1048576 (2^20) per call, else RSC_ERR_UNSUPPORTED; the
+ *   dictionary must support the tensor-core path (packed length <= 112,
+ *   K <= 8), else RSC_ERR_UNSUPPORTED.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress), at which point the CUDA runtime may load the
+ *   array into device memory; make that first call during set-up, before
+ *   any stream capture.  Later calls take no device memory.
+ *   Every call on a device shares the one array and overwrites it (the call
+ *   clears its counter first): calls whose work may overlap on the GPU race
+ *   and give wrong results, so issue them on one stream or synchronise
+ *   between them.  The array stays allocated until the process exits.
+ */
+int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
+                       int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
+                       float *resid_norm2, void *stream);
+
+/*
  * rsc_dict_check -- synchronise `stream` and report the first device-side
  * error recorded by kernels that used `dict` since the last check
  * (RSC_ERR_TIMEOUT when a bounded wait gave up), then clear it.

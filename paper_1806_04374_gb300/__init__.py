@@ -30,7 +30,7 @@ PRECISIONS = {"fp32": RSC_FP32, "bf16": RSC_BF16_RESCORE}
 EXPORTS = (
     "rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode", "rsc_encode_host",
     "rsc_dict_check", "rsc_dict_fallback_count", "rsc_dict_set_timing", "rsc_dict_timing",
-    "rsc_status_string", "rsc_last_cuda_error", "rsc_version",
+    "rsc_status_string", "rsc_last_cuda_error", "rsc_version", "rsc_encode_noalloc",
 )
 
 
@@ -65,6 +65,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_dict_dims.argtypes = [vp, ctypes.POINTER(rsc_dims)]
     lib.rsc_encode.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_encode_host.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
+    lib.rsc_encode_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_dict_check.argtypes = [vp, vp]
     lib.rsc_dict_fallback_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.rsc_dict_set_timing.argtypes = [vp, ctypes.c_int]
@@ -76,7 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_version.argtypes = []
     for name in ("rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode",
                  "rsc_encode_host", "rsc_dict_check", "rsc_dict_fallback_count",
-                 "rsc_dict_set_timing", "rsc_dict_timing", "rsc_version"):
+                 "rsc_dict_set_timing", "rsc_dict_timing", "rsc_version", "rsc_encode_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -125,6 +126,15 @@ def rsc_encode_host(handle: int, x_ptr: int, P: int, K: int, prec: int, atom_ptr
     return load_library().rsc_encode_host(vp(handle), vp(x_ptr), int(P), int(K), int(prec),
                                           vp(atom_ptr), vp(angle_idx_ptr), vp(angle_ptr or None),
                                           vp(coef_ptr), vp(resid_norm2_ptr or None))
+
+
+def rsc_encode_noalloc(handle: int, x_ptr: int, P: int, K: int, atom_ptr: int, angle_idx_ptr: int,
+                       angle_ptr: int, coef_ptr: int, resid_norm2_ptr: int, stream: int = 0) -> int:
+    """Raw call of the allocation-free BF16 entry point; returns the status."""
+    vp = ctypes.c_void_p
+    return load_library().rsc_encode_noalloc(vp(handle), vp(x_ptr), int(P), int(K), vp(atom_ptr),
+                                             vp(angle_idx_ptr), vp(angle_ptr or None),
+                                             vp(coef_ptr), vp(resid_norm2_ptr or None), vp(stream))
 
 
 def rsc_dict_check(handle: int, stream: int = 0) -> int:
