@@ -300,14 +300,18 @@ def main():
 
     if rank == 0:
         fl = algorithmic_flops_per_patch(wl)
-        # dominant kernel: the scoring kernel of the path (phase 0 events)
-        launch_s = main_run["kernel_ms"][0] / max(main_run["kernel_launches"][0], 1) / 1e3
-        achieved = fl["per_patch"] * P / launch_s / 1e12
+        # dominant kernel: the scoring kernel of the path (phase 0 events); the
+        # FP32 kernel runs all K steps in one launch, the tensor-core scoring
+        # kernel one step per launch
+        n_launch = max(main_run["kernel_launches"][0], 1)
+        launch_s = main_run["kernel_ms"][0] / n_launch / 1e3
+        flops_per_launch = fl["per_patch"] * P * args.steps / n_launch
+        achieved = flops_per_launch / launch_s / 1e12
         sm_max = (clk or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         peaks = measured_peaks()
         if args.precision == "bf16":
-            kname, bound = "romp_tc_kernel", "tensor"
+            kname, bound = "romp_score_kernel", "tensor"
             peak = peaks.get("bf16_tflops") or 1900.0
             peak_note = ("dense bf16, MEASURED_PEAKS burst" if peaks.get("bf16_tflops")
                          else "dense bf16, fallback 1.9 PFLOP/s")
@@ -351,6 +355,7 @@ def main():
                 "flops_per_patch": fl["per_patch"],
                 "flops_convention": "(a) 2J(1+4kmax)M + (b) 2.5 R log2 R M per patch-step, x K",
                 "kernel_ms": launch_s * 1e3,
+                "flops_per_launch": flops_per_launch,
                 "peak_note": peak_note,
             },
             "hbm": {"algorithmic_bytes_per_patch": algorithmic_bytes_per_patch(wl),
@@ -360,14 +365,16 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(main_run["kernel_launches"])),
             "handoffs": main_run["handoffs"],
-            "kernel_ms_per_step": [t / args.steps for t in main_run["kernel_ms"]],
+            "kernel_ms_per_step": {"scoring": main_run["kernel_ms"][0] / args.steps,
+                                   "fp32_handoff": main_run["kernel_ms"][1] / args.steps,
+                                   "refine": main_run["kernel_ms"][2] / args.steps},
             "clocks": clk,
         }
         if args.precision == "bf16":
             mf = mma_flops_per_patch(wl)
-            line["mma_executed"] = {"flops_per_patch": mf,
-                                    "tflops": mf * P / launch_s / 1e12,
-                                    "frac_of_peak": mf * P / launch_s / 1e12 / peak}
+            mtf = mf * P * args.steps / n_launch / launch_s / 1e12
+            line["mma_executed"] = {"flops_per_patch": mf, "tflops": mtf,
+                                    "frac_of_peak": mtf / peak}
         if cmp_run is not None:
             v32 = world * P * args.steps / (cmp_run["total_ms"] / 1e3)
             line["fp32_path"] = {"value": v32, "unit": "patches/s",

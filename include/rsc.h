@@ -172,12 +172,14 @@ int rsc_dict_fallback_count(const rsc_dict *dict, int64_t *count);
  * records CUDA events on its stream around each kernel it launches.
  * rsc_dict_timing waits for those events, returns the summed milliseconds
  * and launch counts per phase since the last call, and clears them.
- * Phases: 0 = scoring kernel of the call's path (FP32 or tensor-core),
- * 1 = FP32 hand-off kernel of the tensor-core path.  Meant for one stream at
- * a time; timing adds two event records per launch.
+ * Phases: 0 = scoring kernel of the call's path (the FP32 kernel, or the
+ * tensor-core scoring kernel once per greedy step), 1 = FP32 hand-off kernel
+ * of the tensor-core path, 2 = per-patch refine kernels of the tensor-core
+ * path.  Meant for one stream at a time; timing adds two event records per
+ * launch.
  */
 int rsc_dict_set_timing(rsc_dict *dict, int enable);
-int rsc_dict_timing(rsc_dict *dict, double ms[2], int64_t launches[2]);
+int rsc_dict_timing(rsc_dict *dict, double ms[3], int64_t launches[3]);
 
 /* Human-readable text of a status code (static storage). */
 const char *rsc_status_string(int status);

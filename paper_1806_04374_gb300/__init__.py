@@ -154,13 +154,14 @@ def rsc_dict_set_timing(handle: int, enable: bool) -> int:
 
 
 def rsc_dict_timing(handle: int):
-    """Returns ([ms phase 0, ms phase 1], [launches phase 0, launches phase 1])."""
-    ms = (ctypes.c_double * 2)()
-    n = (ctypes.c_int64 * 2)()
+    """Returns ([ms per phase], [launches per phase]) for phases 0 (scoring),
+    1 (FP32 hand-off) and 2 (refine)."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 3)()
     st = load_library().rsc_dict_timing(ctypes.c_void_p(handle), ms, n)
     if st != RSC_OK:
         raise RscError(st, "rsc_dict_timing")
-    return [ms[0], ms[1]], [n[0], n[1]]
+    return list(ms), list(n)
 
 
 # ----------------------------------------------------------- torch helpers

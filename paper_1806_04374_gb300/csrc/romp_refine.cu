@@ -1,0 +1,323 @@
+// romp_refine.cu -- per-patch steps of the BF16 path between scoring passes:
+// candidate certification, exact re-scoring, the least-squares update and the
+// residual (steps (c)-(e) of OMP, Sec. II-C), one thread per patch.
+//
+// romp_init_kernel writes each patch's packed residual (= x) in bf16 for the
+// first scoring pass and initialises its state.  romp_refine_kernel then,
+// after every scoring pass (romp_score.cu):
+//   * certifies the candidate list: E bounds the bf16 error of a score
+//     (rounding of both operands, accumulation, and the FP32 residual's own
+//     error); every row with |score| >= s1 - 2E is in the list unless the
+//     largest value left out (disc) is >= s1 - 2E, in which case the patch is
+//     handed to the FP32 path;
+//   * screens the candidates with an FP32 score whose error is bounded, and
+//     re-scores the survivors exactly in double-float as
+//     <A_c, x> - sum_i a_i <A_c, A_i> (ties: smallest m*R + r);
+//   * adds the Cholesky row of the winner (Gram entries and right-hand side
+//     in double-float, factor and solve in FP64) and writes the new residual.
+// Per-patch state lives in HBM as structure-of-arrays (coalesced over
+// threads); stopped and finished patches write their outputs.
+#include "rsc_internal.h"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int kRowBytes = kTcKst * 2;  // packed bf16 residual row
+
+// Sink writing packed chunks into a row-major bf16 row in global memory.
+struct GlobalRow {
+  uint4 *row;
+  __device__ void operator()(int cq, uint4 v) const { row[cq] = v; }
+};
+
+// State arrays (each of length P, element i of patch p at [field * P + p]).
+template <int KK>
+struct StateIdx {
+  static constexpr int nL = KK * (KK + 1) / 2;
+  // doubles: L, inv, z, a
+  static constexpr int dL = 0, dInv = nL, dZ = nL + KK, dA = nL + 2 * KK, nD = nL + 3 * KK;
+  // floats: ahi, alo, xnorm, rnorm, dr
+  static constexpr int fHi = 0, fLo = KK, fX = 2 * KK, fR = 2 * KK + 1, fDr = 2 * KK + 2,
+                       nF = 2 * KK + 3;
+  // ints: m, r, t
+  static constexpr int iM = 0, iR = KK, iT = 2 * KK, nI = 2 * KK + 1;
+};
+
+template <int KK>
+__device__ __forceinline__ void load_state(const RefineArgs &a, int64_t p, Ls<KK> &S, int &t,
+                                           float &xnorm, float &rnorm, float &dr) {
+  using I = StateIdx<KK>;
+  const int64_t P = a.P;
+  t = a.sI[I::iT * P + p];
+#pragma unroll
+  for (int q = 0; q < I::nL; ++q) S.L[q] = a.sD[(I::dL + q) * P + p];
+#pragma unroll
+  for (int i = 0; i < KK; ++i) {
+    S.inv[i] = a.sD[(I::dInv + i) * P + p];
+    S.z[i] = a.sD[(I::dZ + i) * P + p];
+    S.a[i] = a.sD[(I::dA + i) * P + p];
+    S.ahi[i] = a.sF[(I::fHi + i) * P + p];
+    S.alo[i] = a.sF[(I::fLo + i) * P + p];
+    S.m[i] = a.sI[(I::iM + i) * P + p];
+    S.r[i] = a.sI[(I::iR + i) * P + p];
+  }
+  xnorm = a.sF[I::fX * P + p];
+  rnorm = a.sF[I::fR * P + p];
+  dr = a.sF[I::fDr * P + p];
+}
+
+template <int KK>
+__device__ __forceinline__ void store_state(const RefineArgs &a, int64_t p, const Ls<KK> &S, int t,
+                                            float rnorm, float dr) {
+  using I = StateIdx<KK>;
+  const int64_t P = a.P;
+  a.sI[I::iT * P + p] = t;
+#pragma unroll
+  for (int q = 0; q < I::nL; ++q) a.sD[(I::dL + q) * P + p] = S.L[q];
+#pragma unroll
+  for (int i = 0; i < KK; ++i) {
+    a.sD[(I::dInv + i) * P + p] = S.inv[i];
+    a.sD[(I::dZ + i) * P + p] = S.z[i];
+    a.sD[(I::dA + i) * P + p] = S.a[i];
+    a.sF[(I::fHi + i) * P + p] = S.ahi[i];
+    a.sF[(I::fLo + i) * P + p] = S.alo[i];
+    a.sI[(I::iM + i) * P + p] = S.m[i];
+    a.sI[(I::iR + i) * P + p] = S.r[i];
+  }
+  a.sF[I::fR * P + p] = rnorm;
+  a.sF[I::fDr * P + p] = dr;
+}
+
+template <int KK>
+__device__ void write_outputs(const RefineArgs &a, int64_t p, const Ls<KK> &S, int t,
+                              float rnorm) {
+  const int K = a.K;
+#pragma unroll
+  for (int i = 0; i < KK; ++i) {
+    if (i < K) {
+      const int64_t o = p * K + i;
+      if (i < t) {
+        a.atom[o] = S.m[i];
+        a.angle_idx[o] = S.r[i];
+        if (a.angle) a.angle[o] = (float)(6.283185307179586 * S.r[i] / a.R);
+        a.coef[o] = S.a[i];
+      } else {
+        a.atom[o] = -1;
+        a.angle_idx[o] = -1;
+        if (a.angle) a.angle[o] = 0.0f;
+        a.coef[o] = 0.0;
+      }
+    }
+  }
+  if (a.resid_norm2) a.resid_norm2[p] = rnorm * rnorm;
+}
+
+template <int KK>
+__global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
+  using I = StateIdx<KK>;
+  const int H = a.H, J = a.J, HJ = H * J;
+  TwS tw{a.tw, H, a.R};
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float *xp = a.x + p * (int64_t)(2 * HJ);
+    df acc = df_make(0.0f);
+    for (int e = 0; e < HJ; ++e) {
+      float2 v = __ldg(reinterpret_cast<const float2 *>(xp) + e);
+      if (e < J) v.y = 0.0f;
+      df q = df_add(two_prod(v.x, v.x), two_prod(v.y, v.y));
+      acc = df_add(acc, e < J ? q : df_mul_f(q, 2.0f));
+    }
+    const float xnorm = sqrtf(fmaxf(acc.hi + acc.lo, 0.0f));
+    Ls<KK> S;
+    GlobalRow sink{reinterpret_cast<uint4 *>(a.A + p * kRowBytes)};
+    const float rn = sqrtf(write_residual<KK>(sink, xp, a.d, J, HJ, a.n, 0, S, tw));
+    a.sI[I::iT * a.P + p] = 0;
+    a.sF[I::fX * a.P + p] = xnorm;
+    a.sF[I::fR * a.P + p] = rn;
+    a.sF[I::fDr * a.P + p] = 2.0f * kU32 * xnorm;
+    a.status[p] = 1;
+  }
+}
+
+template <int KK>
+__global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
+  const int H = a.H, J = a.J, R = a.R, M = a.M, HJ = H * J;
+  TwS tw{a.tw, H, R};
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if (a.status[p] <= 0) continue;
+    const float *xp = a.x + p * (int64_t)(2 * HJ);
+    Ls<KK> S;
+    int t;
+    float xnorm, rnorm, dr;
+    load_state<KK>(a, p, S, t, xnorm, rnorm, dr);
+    float tv[kTop];
+    int ti[kTop];
+#pragma unroll
+    for (int q = 0; q < kTop; q += 4) {
+      const int4 iv = *reinterpret_cast<const int4 *>(a.cand_idx + p * kTop + q);
+      const float4 fv = *reinterpret_cast<const float4 *>(a.cand_val + p * kTop + q);
+      ti[q] = iv.x; ti[q + 1] = iv.y; ti[q + 2] = iv.z; ti[q + 3] = iv.w;
+      tv[q] = fv.x; tv[q + 1] = fv.y; tv[q + 2] = fv.z; tv[q + 3] = fv.w;
+    }
+    const float disc = a.cand_disc[p];
+    const float stop_level = 1e-10f * xnorm;
+    const float s1 = tv[0];
+    // bf16 error of a score: 2^-8 (both operands rounded) + 2^-18 + 112 * 2^-21
+    // (accumulation, at 4x unit roundoff), times 1.25, plus the residual's error
+    const float E =
+        1.25f * (3.90625e-3f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f) * rnorm +
+        2.0f * dr;
+    int outcome = 0;  // 0 continue, 1 finished/stopped, 2 hand-off
+    if (!(s1 + E > stop_level)) {
+      outcome = 1;
+    } else {
+      const float thr = s1 - 2.0f * E;
+      if (disc >= thr) {
+        outcome = 2;
+      } else {
+        float asum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < KK; ++i)
+          if (i < t) asum += fabsf(S.ahi[i]);
+        const float E32 = 256.0f * kU32 * (xnorm + asum);
+        float fs[kTop];
+        float fbest = -1.0f;
+#pragma unroll
+        for (int q = 0; q < kTop; ++q) {
+          fs[q] = -1.0f;
+          if (ti[q] >= 0 && tv[q] >= thr) {
+            const int m = ti[q] % M, r = ti[q] / M;
+            fs[q] = fabsf(score32<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H, R, m, r, t,
+                                      S, tw));
+            fbest = fmaxf(fbest, fs[q]);
+          }
+        }
+        df best = df_make(0.0f), best_ax = df_make(0.0f);
+        df bg[KK];
+#pragma unroll
+        for (int i = 0; i < KK; ++i) bg[i] = df_make(0.0f);
+        int bc = -1, bflat = 0;
+#pragma unroll
+        for (int q = 0; q < kTop; ++q) {
+          if (fs[q] >= 0.0f && fs[q] >= fbest - 2.0f * E32) {
+            const int m = ti[q] % M, r = ti[q] / M;
+            const df ax = score_x(a.d + (size_t)m * HJ * 2, xp, J, H, r, tw);
+            df sc = ax;
+            df gq[KK];
+#pragma unroll
+            for (int i = 0; i < KK; ++i) {
+              gq[i] = df_make(0.0f);
+              if (i < t) {
+                gq[i] = gram_entry(a.xgram, M, H, R, m, r, S.m[i], S.r[i], tw);
+                sc = df_sub(sc, df_mul(df{S.ahi[i], S.alo[i]}, gq[i]));
+              }
+            }
+            const int flat = m * R + r;
+            if (bc < 0 || df_abs_gt(sc, best) || (df_abs_eq(sc, best) && flat < bflat)) {
+              best = sc;
+              bc = ti[q];
+              bflat = flat;
+              best_ax = ax;
+#pragma unroll
+              for (int i = 0; i < KK; ++i) bg[i] = gq[i];
+            }
+          }
+        }
+        if (bc < 0 || !(fabsf(best.hi) > stop_level)) {
+          outcome = 1;
+        } else {
+          const int mb = bc % M, rb = bc / M;
+          double gr[KK];
+#pragma unroll
+          for (int i = 0; i < KK; ++i) gr[i] = (i < t) ? df_to_d(bg[i]) : 0.0;
+          const double diag = df_to_d(gram_entry(a.xgram, M, H, R, mb, rb, mb, rb, tw));
+          const double rhs = df_to_d(best_ax);
+          if (!CholAt<KK, 0>::run(t, S, gr, diag, rhs)) {
+            outcome = 1;
+          } else {
+#pragma unroll
+            for (int i = 0; i < KK; ++i)
+              if (i == t) {
+                S.m[i] = mb;
+                S.r[i] = rb;
+              }
+            ++t;
+            asum = 0.0f;
+#pragma unroll
+            for (int i = 0; i < KK; ++i)
+              if (i < t) asum += fabsf(S.ahi[i]);
+            dr = 2.0f * (t + 6) * kU32 * (xnorm + 1.5f * asum);
+            if (t >= a.K) {
+              outcome = 1;
+              // final residual norm in FP32 (the bf16 row is not needed any more)
+              float n2 = 0.0f;
+              struct NullSink {
+                __device__ void operator()(int, uint4) const {}
+              };
+              n2 = write_residual<KK>(NullSink{}, xp, a.d, J, HJ, a.n, t, S, tw);
+              rnorm = sqrtf(n2);
+            } else {
+              GlobalRow sink{reinterpret_cast<uint4 *>(a.A + p * kRowBytes)};
+              rnorm = sqrtf(write_residual<KK>(sink, xp, a.d, J, HJ, a.n, t, S, tw));
+              store_state<KK>(a, p, S, t, rnorm, dr);
+            }
+          }
+        }
+      }
+    }
+    if (outcome == 1) {
+      write_outputs<KK>(a, p, S, t, rnorm);
+      a.status[p] = 0;
+    } else if (outcome == 2) {
+      const int slot = atomicAdd(a.redo_count, 1);
+      a.redo_list[slot] = (int)p;
+      if (a.fallbacks) atomicAdd(a.fallbacks, 1ull);
+      a.status[p] = -1;
+    }
+  }
+}
+
+template <int KK>
+int launch_refine_t(const RefineArgs &a, bool init, cudaStream_t stream) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = (a.P + 127) / 128;
+  const int64_t cap = (int64_t)nsm * 32;
+  const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+  if (init)
+    romp_init_kernel<KK><<<grid, 128, 0, stream>>>(a);
+  else
+    romp_refine_kernel<KK><<<grid, 128, 0, stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  return RSC_OK;
+}
+
+}  // namespace
+
+namespace {
+template <int KK>
+int state_layout_t(int *nD, int *nF, int *nI) {
+  *nD = StateIdx<KK>::nD;
+  *nF = StateIdx<KK>::nF;
+  *nI = StateIdx<KK>::nI;
+  return KK;
+}
+}  // namespace
+
+int rsc_state_layout(int K, int *nD, int *nF, int *nI) {
+  if (K <= 3) return state_layout_t<3>(nD, nF, nI);
+  if (K <= 5) return state_layout_t<5>(nD, nF, nI);
+  return state_layout_t<8>(nD, nF, nI);
+}
+
+int rsc_launch_refine(const RefineArgs &a, bool init, cudaStream_t stream) {
+  if (a.P == 0) return RSC_OK;
+  if (a.K <= 3) return launch_refine_t<3>(a, init, stream);
+  if (a.K <= 5) return launch_refine_t<5>(a, init, stream);
+  if (a.K <= 8) return launch_refine_t<8>(a, init, stream);
+  return RSC_ERR_UNSUPPORTED;
+}

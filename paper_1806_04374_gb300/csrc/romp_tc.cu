@@ -17,7 +17,8 @@
 //     loads and the MMAs); each chunk is multiplied into one of two TMEM
 //     accumulator buffers per tile while the other buffer is read back;
 //   * epilogue (c): every thread reads its patch's scores with tcgen05.ld and
-//     keeps the top-4 |score| and the largest value it discarded;
+//     keeps the 8 largest block maxima of |score| and the largest value it
+//     discarded;
 //   * per patch, every candidate within 2E of the best (E bounds the bf16
 //     error of a score) is re-scored exactly in double-float as
 //     <A_c, x> - sum_i a_i <A_c, A_i>, the Gram entries coming from the
@@ -31,6 +32,7 @@
 
 #include "df.cuh"
 #include "rsc_internal.h"
+#include "tc_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
@@ -41,10 +43,9 @@ constexpr int kBlkA = kTile * 128;    // one 64-column block of A (bytes)
 constexpr int kBlkB = kTcBN * 128;    // one 64-column block of a B stage (bytes)
 constexpr int kStageBytes = 2 * kBlkB;
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits: 2 s
-constexpr float kU32 = 5.9604644775390625e-8f;  // 2^-24
 
 struct TcLayout {
-  int a_off, b_off, tw_off, qtab_off, bar_off, misc_off, total;
+  int a_off, b_off, tw_off, bar_off, misc_off, total;
 };
 
 __host__ __device__ inline int al(int v, int a) { return (v + a - 1) / a * a; }
@@ -59,8 +60,6 @@ __host__ __device__ inline TcLayout tc_layout(int H, int R) {
   off += kStages * kStageBytes;
   L.tw_off = off;
   off = al(off + 4 * H * (R + 1) * 4, 16);
-  L.qtab_off = off;
-  off = al(off + kTcMaxN * 4, 16);
   L.bar_off = off;
   off = al(off + (kStages + 2) * 8, 16);
   L.misc_off = off;
@@ -69,204 +68,15 @@ __host__ __device__ inline TcLayout tc_layout(int H, int R) {
   return L;
 }
 
-struct TwS {
-  const float *base;
-  int H, stride;
-  __device__ df cosv(int k, int r) const {
-    return {base[(0 * H + k) * stride + r], base[(1 * H + k) * stride + r]};
-  }
-  __device__ df sinv(int k, int r) const {
-    return {base[(2 * H + k) * stride + r], base[(3 * H + k) * stride + r]};
-  }
-  __device__ float cos32(int k, int r) const { return base[(0 * H + k) * stride + r]; }
-  __device__ float sin32(int k, int r) const { return base[(2 * H + k) * stride + r]; }
-};
-
-template <int KK>
-struct Ls {
-  double L[KK * (KK + 1) / 2];  // packed lower Cholesky factor
-  double inv[KK];               // 1 / L_ii
-  double z[KK];                 // L z = b
-  double a[KK];                 // weights
-  float ahi[KK], alo[KK];       // weights in double-float
-  int m[KK], r[KK];             // selected atom / angle
-};
-
-__device__ __forceinline__ bool df_abs_gt(df a, df b) {
-  if (a.hi < 0.0f) a = df_neg(a);
-  if (b.hi < 0.0f) b = df_neg(b);
-  return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
-}
-
-__device__ __forceinline__ bool df_abs_eq(df a, df b) {
-  if (a.hi < 0.0f) a = df_neg(a);
-  if (b.hi < 0.0f) b = df_neg(b);
-  return a.hi == b.hi && a.lo == b.lo;
-}
-
-__device__ __forceinline__ void top4_insert(float (&v)[4], int (&i)[4], float &disc, float x,
-                                            int idx) {
-  if (x > v[3]) {
-    disc = fmaxf(disc, v[3]);
-    v[3] = x;
-    i[3] = idx;
-    if (v[3] > v[2]) { float t = v[2]; v[2] = v[3]; v[3] = t; int u = i[2]; i[2] = i[3]; i[3] = u; }
-    if (v[2] > v[1]) { float t = v[1]; v[1] = v[2]; v[2] = t; int u = i[1]; i[1] = i[2]; i[2] = u; }
-    if (v[1] > v[0]) { float t = v[0]; v[0] = v[1]; v[1] = t; int u = i[0]; i[0] = i[1]; i[1] = u; }
-  } else {
-    disc = fmaxf(disc, x);
-  }
-}
-
-// Dot2-style accumulation (Ogita, Rump, Oishi): s + c carries the sum.
-__device__ __forceinline__ void dot2_acc(float &s, float &c, float x, float y) {
-  df p = two_prod(x, y);
-  df q = two_sum(s, p.hi);
-  s = q.hi;
-  c = __fadd_rn(c, __fadd_rn(p.lo, q.lo));
-}
-
-// <S_r d_m, x> in double-float: sum_k w_k Re(e^{ik theta} Q_k),
-// Q_k = sum_j conj(d_m[j,k]) x[j,k].
-__device__ df score_x(const float *__restrict__ dm, const float *__restrict__ xp, int J, int H,
-                      int r, const TwS &tw) {
-  df acc = df_make(0.0f);
-  for (int k = 0; k < H; ++k) {
-    float qr = 0.f, qrc = 0.f, qi = 0.f, qic = 0.f;
-    const float2 *d2 = reinterpret_cast<const float2 *>(dm) + k * J;
-    const float2 *x2 = reinterpret_cast<const float2 *>(xp) + k * J;
-    for (int j = 0; j < J; ++j) {
-      const float2 dv = __ldg(d2 + j);
-      const float2 xv = __ldg(x2 + j);
-      const float dim = k ? dv.y : 0.0f, xim = k ? xv.y : 0.0f;
-      dot2_acc(qr, qrc, dv.x, xv.x);
-      dot2_acc(qr, qrc, dim, xim);
-      dot2_acc(qi, qic, dv.x, xim);
-      dot2_acc(qi, qic, -dim, xv.x);
-    }
-    const df Qr = fast_two_sum(qr, qrc), Qi = fast_two_sum(qi, qic);
-    // Re(e^{ik theta} Q) = cos(k theta) Re Q - sin(k theta) Im Q
-    df term = df_sub(df_mul(tw.cosv(k, r), Qr), df_mul(tw.sinv(k, r), Qi));
-    acc = df_add(acc, k ? df_mul_f(term, 2.0f) : term);
-  }
-  return acc;
-}
-
-// <S_ra d_ma, S_rb d_mb> = sum_k w_k Re(e^{ik (theta_a - theta_b)} H_k(ma, mb)).
-__device__ df gram_entry(const float4 *__restrict__ xg, int M, int H, int R, int ma, int ra,
-                         int mb, int rb, const TwS &tw) {
-  int dr = ra - rb;
-  if (dr < 0) dr += R;
-  const float4 *h = xg + ((size_t)ma * M + mb) * H;
-  df acc = df_make(0.0f);
-  for (int k = 0; k < H; ++k) {
-    const float4 v = __ldg(h + k);
-    // the table row k already holds the angles k * 2 pi r / R
-    df term = df_sub(df_mul(tw.cosv(k, dr), df{v.x, v.y}), df_mul(tw.sinv(k, dr), df{v.z, v.w}));
-    acc = df_add(acc, k ? df_mul_f(term, 2.0f) : term);
-  }
-  return acc;
-}
-
-// New Cholesky row TT (compile-time) and the solve of all TT+1 weights, FP64.
-template <int KK, int TT>
-__device__ __forceinline__ bool chol_add(Ls<KK> &S, const double (&g)[KK], double diag,
-                                         double rhs) {
-  double l[TT > 0 ? TT : 1];
-  double p2 = diag;
-#pragma unroll
-  for (int i = 0; i < TT; ++i) {
-    double v = g[i];
-#pragma unroll
-    for (int j = 0; j < i; ++j) v -= S.L[i * (i + 1) / 2 + j] * l[j];
-    v *= S.inv[i];
-    l[i] = v;
-    p2 -= v * v;
-  }
-  if (!(p2 > kPivotRel * diag)) return false;
-  const double ltt = sqrt(p2);
-#pragma unroll
-  for (int i = 0; i < TT; ++i) S.L[TT * (TT + 1) / 2 + i] = l[i];
-  S.L[TT * (TT + 1) / 2 + TT] = ltt;
-  S.inv[TT] = 1.0 / ltt;
-  double zt = rhs;
-#pragma unroll
-  for (int i = 0; i < TT; ++i) zt -= l[i] * S.z[i];
-  S.z[TT] = zt * S.inv[TT];
-#pragma unroll
-  for (int i = TT; i >= 0; --i) {
-    double v = S.z[i];
-#pragma unroll
-    for (int q = i + 1; q <= TT; ++q) v -= S.L[q * (q + 1) / 2 + i] * S.a[q];
-    v *= S.inv[i];
-    S.a[i] = v;
-    const float hi = __double2float_rn(v);
-    S.ahi[i] = hi;
-    S.alo[i] = __double2float_rn(v - (double)hi);
-  }
-  return true;
-}
-
-template <int KK, int TT>
-struct CholAt {
-  __device__ static bool run(int t, Ls<KK> &S, const double (&g)[KK], double diag, double rhs) {
-    if (t == TT) return chol_add<KK, TT>(S, g, diag, rhs);
-    return CholAt<KK, TT + 1>::run(t, S, g, diag, rhs);
-  }
-};
-template <int KK>
-struct CholAt<KK, KK> {
-  __device__ static bool run(int, Ls<KK> &, const double (&)[KK], double, double) {
-    return false;
-  }
-};
-
-// Writes this thread's packed residual x - sum_i a_i S_{r_i} d_{m_i} (FP32,
-// rounded to bf16) into row `row` of the swizzled A tile; returns ||r||^2.
-template <int KK>
-__device__ float write_residual(unsigned char *sA, int row, const float *__restrict__ xp,
-                                const float *__restrict__ d, int HJ, int n, int t,
-                                const Ls<KK> &S, const int *qtab, const TwS &tw) {
-  float n2 = 0.0f;
-#pragma unroll 1
-  for (int cq = 0; cq < kTcKst / 8; ++cq) {
-    float v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int q = cq * 8 + u;
-      float val = 0.0f;
-      if (q < n) {
-        const int code = qtab[q];
-        const int e = code >> 8, k = (code >> 1) & 127, comp = code & 1;
-        val = xp[2 * e + comp];
-#pragma unroll
-        for (int i = 0; i < KK; ++i) {
-          if (i < t) {
-            const float2 dv = __ldg(reinterpret_cast<const float2 *>(d) + (size_t)S.m[i] * HJ + e);
-            const float c = tw.cos32(k, S.r[i]), s = tw.sin32(k, S.r[i]);
-            const float Ac = comp ? fmaf(c, dv.y, -s * dv.x) : fmaf(c, dv.x, s * dv.y);
-            val = fmaf(-S.ahi[i], Ac, val);
-          }
-        }
-        if (k) val *= 1.41421356237309515f;
-      }
-      v[u] = val;
-      n2 = fmaf(val, val, n2);
-    }
-    uint4 pk;
-    __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]);
-    __nv_bfloat162 b1 = __floats2bfloat162_rn(v[2], v[3]);
-    __nv_bfloat162 b2 = __floats2bfloat162_rn(v[4], v[5]);
-    __nv_bfloat162 b3 = __floats2bfloat162_rn(v[6], v[7]);
-    pk.x = *reinterpret_cast<uint32_t *>(&b0);
-    pk.y = *reinterpret_cast<uint32_t *>(&b1);
-    pk.z = *reinterpret_cast<uint32_t *>(&b2);
-    pk.w = *reinterpret_cast<uint32_t *>(&b3);
+// Sink writing packed chunks into row `row` of a 128-byte-swizzled A tile.
+struct SmemRow {
+  unsigned char *tile;
+  int row;
+  __device__ void operator()(int cq, uint4 v) const {
     const int blk = cq >> 3, ch = cq & 7;
-    *reinterpret_cast<uint4 *>(sA + blk * kBlkA + row * 128 + ((ch ^ (row & 7)) << 4)) = pk;
+    *reinterpret_cast<uint4 *>(tile + blk * kBlkA + row * 128 + ((ch ^ (row & 7)) << 4)) = v;
   }
-  return n2;
-}
+};
 
 __device__ __forceinline__ void record_error(int *err, int code) {
   if (err) atomicCAS(err, 0, code);
@@ -283,7 +93,6 @@ __global__ void __launch_bounds__(TILES * 128, 1)
   unsigned char *sA = smem + Lo.a_off;
   unsigned char *sB = smem + Lo.b_off;
   float *s_tw = reinterpret_cast<float *>(smem + Lo.tw_off);
-  int *s_qtab = reinterpret_cast<int *>(smem + Lo.qtab_off);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bar_off);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + Lo.misc_off);
 
@@ -298,22 +107,6 @@ __global__ void __launch_bounds__(TILES * 128, 1)
   for (int i = tid; i < 4 * H * R; i += blockDim.x) {
     const int pk = i / R, r = i - pk * R;
     s_tw[pk * (R + 1) + r] = a.tw[i];
-  }
-  for (int q = tid; q < kTcMaxN; q += blockDim.x) {
-    int code = 0;
-    if (q < a.n) {
-      int e, k, comp;
-      if (q < J) {
-        e = q; k = 0; comp = 0;
-      } else {
-        const int qq = q - J, kj = qq >> 1;
-        comp = qq & 1;
-        k = 1 + kj / J;
-        e = k * J + (kj - (k - 1) * J);
-      }
-      code = (e << 8) | (k << 1) | comp;
-    }
-    s_qtab[q] = code;
   }
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) tc::mbar_init(full_bar0 + 8 * s, 1);
@@ -387,7 +180,7 @@ __global__ void __launch_bounds__(TILES * 128, 1)
         acc = df_add(acc, e < J ? q : df_mul_f(q, 2.0f));
       }
       xnorm = sqrtf(fmaxf(acc.hi + acc.lo, 0.0f));
-      rnorm = sqrtf(write_residual<KK>(myA, row, xp, a.d, HJ, a.n, 0, S, s_qtab, tw));
+      rnorm = sqrtf(write_residual<KK>(SmemRow{myA, row}, xp, a.d, J, HJ, a.n, 0, S, tw));
       dr = 2.0f * kU32 * xnorm;
     } else {
       // rows of absent patches: zeros
@@ -404,8 +197,13 @@ __global__ void __launch_bounds__(TILES * 128, 1)
       const int any = __syncthreads_or(active ? 1 : 0);
       if (!any) break;
       // ---- scoring: MMAs chunk by chunk, epilogue keeps the per-patch top-4
-      float tv[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
-      int ti[4] = {-1, -1, -1, -1};
+      float tv[kTop];
+      int ti[kTop];
+#pragma unroll
+      for (int q = 0; q < kTop; ++q) {
+        tv[q] = -INFINITY;
+        ti[q] = -1;
+      }
       float disc = -INFINITY;
       for (int c = 0; c < a.nchunks; ++c) {
         const uint32_t gg = g + c;
@@ -442,23 +240,34 @@ __global__ void __launch_bounds__(TILES * 128, 1)
             tc::tmem_ld32(taddr + piece * 32, v);
             tc::tmem_wait_ld();
             if (active) {
+              // rows base .. base+31 of the steered dictionary (angle-major:
+              // 32 different atoms).  Common path: the block maximum only;
+              // a block whose maximum enters the top-4 also yields its
+              // arg-max and second maximum (the latter goes to disc).
               const int base = c * kTcBN + piece * 32;
-              if ((piece + 1) * 32 <= nvalid) {
-                float mx = 0.0f;
+              const int nv = nvalid - piece * 32;
+              float av[32];
 #pragma unroll
-                for (int u = 0; u < 32; ++u) mx = fmaxf(mx, fabsf(__uint_as_float(v[u])));
-                if (mx > tv[3]) {
+              for (int u = 0; u < 32; ++u)
+                av[u] = (u < nv) ? fabsf(__uint_as_float(v[u])) : -INFINITY;
+              float m1 = -INFINITY;
 #pragma unroll
-                  for (int u = 0; u < 32; ++u)
-                    top4_insert(tv, ti, disc, fabsf(__uint_as_float(v[u])), base + u);
-                } else {
-                  disc = fmaxf(disc, mx);
+              for (int u = 0; u < 32; u += 2) m1 = fmax3(m1, av[u], av[u + 1]);
+              if (m1 > tv[kTop - 1]) {
+                int us = 0;
+                bool found = false;
+                float m2 = -INFINITY;
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                  const bool is = !found && (av[u] == m1);
+                  us = is ? u : us;
+                  found = found || is;
+                  m2 = fmaxf(m2, is ? -INFINITY : av[u]);
                 }
+                topn_insert(tv, ti, disc, m1, base + us);
+                disc = fmaxf(disc, m2);
               } else {
-#pragma unroll
-                for (int u = 0; u < 32; ++u)
-                  if (piece * 32 + u < nvalid)
-                    top4_insert(tv, ti, disc, fabsf(__uint_as_float(v[u])), base + u);
+                disc = fmaxf(disc, m1);
               }
             }
           }
@@ -486,35 +295,65 @@ __global__ void __launch_bounds__(TILES * 128, 1)
             redo = true;
             active = false;
           } else {
-            df best = df_make(0.0f), best_ax = df_make(0.0f);
-            int bc = -1;
+            // FP32 screen: |f_q - s_q| <= E32 for every candidate, so the
+            // exact winner is among those with f_q >= max f - 2 E32
+            float asum = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int i = 0; i < KK; ++i)
+              if (i < t) asum += fabsf(S.ahi[i]);
+            const float E32 = 256.0f * kU32 * (xnorm + asum);
+            float fs[kTop];
+            float fbest = -1.0f;
+#pragma unroll
+            for (int q = 0; q < kTop; ++q) {
+              fs[q] = -1.0f;
               if (ti[q] >= 0 && tv[q] >= thr) {
-                const int c = ti[q], m = c / R, r = c - m * R;
-                const df ax = score_x(a.d + (size_t)m * HJ * 2, xp, J, H, r, tw);
-                df s = ax;
+                const int m = ti[q] % M, r = ti[q] / M;
+                fs[q] = fabsf(score32<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H, R, m, r,
+                                          t, S, tw));
+                fbest = fmaxf(fbest, fs[q]);
+              }
+            }
+            // exact (double-float) re-score of the survivors:
+            // <A_c, x> - sum_i a_i <A_c, A_i>; ties -> smallest m*R + r
+            df best = df_make(0.0f), best_ax = df_make(0.0f);
+            df bg[KK];
 #pragma unroll
-                for (int i = 0; i < KK; ++i)
-                  if (i < t)
-                    s = df_sub(s, df_mul(df{S.ahi[i], S.alo[i]},
-                                         gram_entry(a.xgram, M, H, R, m, r, S.m[i], S.r[i], tw)));
-                if (bc < 0 || df_abs_gt(s, best) || (df_abs_eq(s, best) && c < bc)) {
-                  best = s;
-                  bc = c;
+            for (int i = 0; i < KK; ++i) bg[i] = df_make(0.0f);
+            int bc = -1, bflat = 0;
+#pragma unroll
+            for (int q = 0; q < kTop; ++q) {
+              if (fs[q] >= 0.0f && fs[q] >= fbest - 2.0f * E32) {
+                const int m = ti[q] % M, r = ti[q] / M;
+                const df ax = score_x(a.d + (size_t)m * HJ * 2, xp, J, H, r, tw);
+                df sc = ax;
+                df gq[KK];
+#pragma unroll
+                for (int i = 0; i < KK; ++i) {
+                  gq[i] = df_make(0.0f);
+                  if (i < t) {
+                    gq[i] = gram_entry(a.xgram, M, H, R, m, r, S.m[i], S.r[i], tw);
+                    sc = df_sub(sc, df_mul(df{S.ahi[i], S.alo[i]}, gq[i]));
+                  }
+                }
+                const int flat = m * R + r;
+                if (bc < 0 || df_abs_gt(sc, best) || (df_abs_eq(sc, best) && flat < bflat)) {
+                  best = sc;
+                  bc = ti[q];
+                  bflat = flat;
                   best_ax = ax;
+#pragma unroll
+                  for (int i = 0; i < KK; ++i) bg[i] = gq[i];
                 }
               }
             }
             if (bc < 0 || !(fabsf(best.hi) > stop_level)) {
               active = false;
             } else {
-              const int mb = bc / R, rb = bc - mb * R;
+              const int mb = bc % M, rb = bc / M;
               double gr[KK];
 #pragma unroll
-              for (int i = 0; i < KK; ++i)
-                gr[i] = (i < t) ? df_to_d(gram_entry(a.xgram, M, H, R, mb, rb, S.m[i], S.r[i], tw))
-                                : 0.0;
+              for (int i = 0; i < KK; ++i) gr[i] = (i < t) ? df_to_d(bg[i]) : 0.0;
               const double diag = df_to_d(gram_entry(a.xgram, M, H, R, mb, rb, mb, rb, tw));
               const double rhs = df_to_d(best_ax);
               if (!CholAt<KK, 0>::run(t, S, gr, diag, rhs)) {
@@ -527,11 +366,11 @@ __global__ void __launch_bounds__(TILES * 128, 1)
                     S.r[i] = rb;
                   }
                 ++t;
-                float asum = 0.0f;
+                asum = 0.0f;
 #pragma unroll
                 for (int i = 0; i < KK; ++i)
                   if (i < t) asum += fabsf(S.ahi[i]);
-                rnorm = sqrtf(write_residual<KK>(myA, row, xp, a.d, HJ, a.n, t, S, s_qtab, tw));
+                rnorm = sqrtf(write_residual<KK>(SmemRow{myA, row}, xp, a.d, J, HJ, a.n, t, S, tw));
                 dr = 2.0f * (t + 6) * kU32 * (xnorm + 1.5f * asum);
               }
             }

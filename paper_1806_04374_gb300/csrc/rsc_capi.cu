@@ -7,6 +7,7 @@
 
 #include <cuda_bf16.h>
 
+#include <mutex>
 #include <vector>
 
 #include "rsc_internal.h"
@@ -87,8 +88,37 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// Tables of the tensor-core path: the packed steered dictionary (bf16, one
-// row per (m, r), the packed layout described in rsc_internal.h), the
+// TMA map of a row-major bf16 matrix [rows][kTcKst]: box 64 columns x kTcBN
+// rows, 128-byte swizzle, zero fill outside (columns kTcKst..127, rows >= rows).
+int encode_rows_map(CUtensorMap *map, void *base, size_t rows) {
+  static EncodeTiledFn fn = nullptr;
+  static cudaError_t fn_err = cudaSuccess;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    fn_err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                              cudaEnableDefault, &q);
+    if (fn_err == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = (EncodeTiledFn)f;
+  });
+  if (!fn) return rsc_cuda_fail(fn_err != cudaSuccess ? fn_err : cudaErrorNotSupported);
+  const cuuint64_t gdim[2] = {(cuuint64_t)kTcKst, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)kTcKst * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)kTcBN};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult cr = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    snprintf(g_cuda_msg, sizeof g_cuda_msg, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    return RSC_ERR_CUDA;
+  }
+  return RSC_OK;
+}
+
+// Tables of the tensor-core path: the packed steered dictionary (bf16, row
+// r*M + m = S_r d_m, angle-major so that 32 consecutive rows hold different
+// atoms; the packed layout described in rsc_internal.h), the
 // per-harmonic cross-Gram table H_k(a, b) in double-float and the TMA map.
 // Returns RSC_OK also when the sizes are outside the path (tables left null).
 int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
@@ -102,7 +132,7 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   std::vector<uint16_t> B(rows * kTcKst, 0);
   for (int m = 0; m < M; ++m)
     for (int r = 0; r < R; ++r) {
-      uint16_t *row = &B[((size_t)m * R + r) * kTcKst];
+      uint16_t *row = &B[((size_t)r * M + m) * kTcKst];  // angle-major rows
       for (int k = 0; k < H; ++k) {
         const double th = 2.0 * M_PI * (double)(((int64_t)k * r) % R) / (double)R;
         const double c = cos(th), s = sin(th);
@@ -150,23 +180,7 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
 
-  void *fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return rsc_cuda_fail(e);
-  const cuuint64_t gdim[2] = {(cuuint64_t)kTcKst, (cuuint64_t)rows};
-  const cuuint64_t gstride[1] = {(cuuint64_t)kTcKst * 2};
-  const cuuint32_t box[2] = {64, (cuuint32_t)kTcBN};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult cr = reinterpret_cast<EncodeTiledFn>(fn)(
-      &d->tmap_b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, d->steered_bf16, gdim, gstride, box, estr,
-      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) {
-    snprintf(g_cuda_msg, sizeof g_cuda_msg, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-    return RSC_ERR_CUDA;
-  }
-  return RSC_OK;
+  return encode_rows_map(&d->tmap_b, d->steered_bf16, rows);
 }
 
 int check_device(const rsc_dict *d) {
@@ -346,49 +360,95 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
     return rc;
   }
 
-  // BF16 tensor-core scoring; patches it hands back are coded by the FP32 path
+  // BF16 tensor-core path, split per greedy step into a scoring kernel and a
+  // per-patch refine kernel; patches it hands back are coded by the FP32 path
   if (!dict->steered_bf16 || K > kTcMaxK || P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
-  int *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (P + 4) * sizeof(int), st);
+  int nD = 0, nF = 0, nI = 0;
+  rsc_state_layout(K, &nD, &nF, &nI);
+  auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t bA = al256((size_t)P * kTcKst * 2), bCI = al256((size_t)P * kTcTop * 4),
+               bCV = bCI, bCD = al256((size_t)P * 4), bSt = bCD, bD = al256((size_t)nD * P * 8),
+               bF = al256((size_t)nF * P * 4), bI = al256((size_t)nI * P * 4),
+               bR = al256((size_t)(P + 4) * 4);
+  const size_t total = bA + bCI + bCV + bCD + bSt + bD + bF + bI + bR;
+  unsigned char *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, sizeof(int), st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
-  TcArgs ta;
-  ta.x = x;
-  ta.P = P;
-  ta.K = K;
-  ta.M = dict->M;
-  ta.J = dict->J;
-  ta.kmax = dict->kmax;
-  ta.R = dict->R;
-  ta.H = dict->H;
-  ta.n = dict->n;
-  ta.ksteps = (dict->n + 15) / 16;
-  ta.MR = dict->M * dict->R;
-  ta.nchunks = (ta.MR + kTcBN - 1) / kTcBN;
-  ta.d = dict->d;
-  ta.tw = dict->tw;
-  ta.xgram = dict->xgram;
-  ta.atom = atom;
-  ta.angle_idx = angle_idx;
-  ta.angle = angle;
-  ta.coef = coef;
-  ta.resid_norm2 = resid_norm2;
-  ta.err = dict->err;
-  ta.redo_count = scratch;
-  ta.redo_list = scratch + 4;
-  ta.fallbacks = dict->fallbacks;
-  int slot = timing_begin(dict, 0, st);
-  rc = rsc_launch_tc(ta, dict->tmap_b, st);
-  timing_end(dict, slot, st);
+  unsigned char *q = scratch;
+  auto take = [&](size_t b) {
+    unsigned char *r = q;
+    q += b;
+    return r;
+  };
+  RefineArgs ra;
+  ra.x = x;
+  ra.P = P;
+  ra.K = K;
+  ra.M = dict->M;
+  ra.J = dict->J;
+  ra.kmax = dict->kmax;
+  ra.R = dict->R;
+  ra.H = dict->H;
+  ra.n = dict->n;
+  ra.d = dict->d;
+  ra.tw = dict->tw;
+  ra.xgram = dict->xgram;
+  ra.A = take(bA);
+  ra.cand_idx = reinterpret_cast<int *>(take(bCI));
+  ra.cand_val = reinterpret_cast<float *>(take(bCV));
+  ra.cand_disc = reinterpret_cast<float *>(take(bCD));
+  ra.status = reinterpret_cast<int *>(take(bSt));
+  ra.sD = reinterpret_cast<double *>(take(bD));
+  ra.sF = reinterpret_cast<float *>(take(bF));
+  ra.sI = reinterpret_cast<int *>(take(bI));
+  int *redo = reinterpret_cast<int *>(take(bR));
+  ra.redo_count = redo;
+  ra.redo_list = redo + 4;
+  ra.atom = atom;
+  ra.angle_idx = angle_idx;
+  ra.angle = angle;
+  ra.coef = coef;
+  ra.resid_norm2 = resid_norm2;
+  ra.fallbacks = dict->fallbacks;
+  ScoreArgs sa;
+  sa.P = P;
+  sa.ksteps = (dict->n + 15) / 16;
+  sa.MR = dict->M * dict->R;
+  sa.nchunks = (sa.MR + kTcBN - 1) / kTcBN;
+  sa.status = ra.status;
+  sa.cand_idx = const_cast<int *>(ra.cand_idx);
+  sa.cand_val = const_cast<float *>(ra.cand_val);
+  sa.cand_disc = const_cast<float *>(ra.cand_disc);
+  sa.err = dict->err;
+  CUtensorMap tmA;
+  rc = encode_rows_map(&tmA, ra.A, (size_t)P);
   if (rc == RSC_OK) {
-    a.redo_count = ta.redo_count;
-    a.redo_list = ta.redo_list;
+    e = cudaMemsetAsync(redo, 0, sizeof(int), st);
+    if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+  }
+  if (rc == RSC_OK) {
+    const int slot = timing_begin(dict, 2, st);
+    rc = rsc_launch_refine(ra, true, st);
+    timing_end(dict, slot, st);
+  }
+  for (int step = 0; step < K && rc == RSC_OK; ++step) {
+    int slot = timing_begin(dict, 0, st);
+    rc = rsc_launch_score(sa, tmA, dict->tmap_b, st);
+    timing_end(dict, slot, st);
+    if (rc != RSC_OK) break;
+    slot = timing_begin(dict, 2, st);
+    rc = rsc_launch_refine(ra, false, st);
+    timing_end(dict, slot, st);
+  }
+  if (rc == RSC_OK) {
+    a.redo_count = ra.redo_count;
+    a.redo_list = ra.redo_list;
     a.fallbacks = nullptr;
-    slot = timing_begin(dict, 1, st);
+    const int slot = timing_begin(dict, 1, st);
     rc = rsc_launch_f32(a, st);
     timing_end(dict, slot, st);
   }
@@ -492,10 +552,12 @@ int rsc_dict_set_timing(rsc_dict *dict, int enable) {
   return RSC_OK;
 }
 
-int rsc_dict_timing(rsc_dict *dict, double ms[2], int64_t launches[2]) {
+int rsc_dict_timing(rsc_dict *dict, double ms[3], int64_t launches[3]) {
   if (!dict || !ms || !launches) return RSC_ERR_INVALID;
-  ms[0] = ms[1] = 0.0;
-  launches[0] = launches[1] = 0;
+  for (int i = 0; i < 3; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
   TimingLog *log = static_cast<TimingLog *>(dict->timing_state);
   int rc = RSC_OK;
   if (log) {

@@ -27,7 +27,7 @@ struct rsc_dict {
   unsigned long long *fallbacks;  // device counter of exact re-scans
   // tensor-core path: steered dictionary and cross-Gram table (null when the
   // sizes are outside what the path handles)
-  void *steered_bf16;    // [M*R][kTcKst] bf16, row m*R + r = packed S_r d_m
+  void *steered_bf16;    // [R*M][kTcKst] bf16, row r*M + m = packed S_r d_m
   float4 *xgram;         // [M][M][H] double-float complex H_k(a,b) = sum_j conj(d_a) d_b
   int n;                 // packed real length J (2 kmax + 1)
   // per-phase timing (diagnostic): event pairs recorded around launches
@@ -64,9 +64,60 @@ struct TcArgs {
   unsigned long long *fallbacks;
 };
 
-// BF16 tensor-core scoring path (romp_tc.cu); patches whose candidates
-// overflow are appended to redo_list for the FP32 path.
+// BF16 tensor-core scoring path fused with the per-patch steps in one
+// persistent kernel (romp_tc.cu; used by rsc_encode_noalloc); patches whose
+// candidates overflow are appended to redo_list for the FP32 path.
 int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream);
+
+// Block maxima kept per patch and greedy step by the tensor-core scoring.
+constexpr int kTcTop = 8;
+
+// One scoring pass of the split BF16 path (romp_score.cu): packed bf16
+// residual rows (TMA map tmA: [P][kTcKst]) times the steered dictionary
+// (tmB) -> per patch the kTcTop largest block maxima of |score| with their
+// rows (r*M + m) and the largest value left out.
+struct ScoreArgs {
+  int64_t P;
+  int ksteps, MR, nchunks;
+  const int *status;  // > 0: patch still being coded
+  int *cand_idx;      // [P][kTcTop]
+  float *cand_val;    // [P][kTcTop]
+  float *cand_disc;   // [P]
+  int *err;
+};
+int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
+                     cudaStream_t stream);
+
+// Per-patch steps of the split BF16 path (romp_refine.cu): init (packed x,
+// state) or one refine (certify, re-score, Cholesky, residual).
+struct RefineArgs {
+  const float *x;
+  int64_t P;
+  int K, M, J, kmax, R, H, n;
+  const float *d;
+  const float *tw;       // [4][H][R]
+  const float4 *xgram;
+  unsigned char *A;      // [P][kTcKst] bf16 packed residual rows
+  const int *cand_idx;
+  const float *cand_val;
+  const float *cand_disc;
+  int *status;           // 1 active, 0 done, -1 handed to the FP32 path
+  double *sD;            // state, structure of arrays
+  float *sF;
+  int *sI;
+  int32_t *atom;
+  int32_t *angle_idx;
+  float *angle;
+  double *coef;
+  float *resid_norm2;
+  int *redo_list;
+  int *redo_count;
+  unsigned long long *fallbacks;
+};
+int rsc_launch_refine(const RefineArgs &a, bool init, cudaStream_t stream);
+// Number of double / float / int state arrays for K steps; returns the
+// compile-time capacity used (K rounded up to 3, 5 or 8).
+int rsc_state_layout(int K, int *nD, int *nF, int *nI);
 
 struct RompArgs {
   const float *x;
