@@ -112,11 +112,20 @@ __device__ void write_outputs(const RefineArgs &a, int64_t p, const Ls<KK> &S, i
   if (a.resid_norm2) a.resid_norm2[p] = rnorm * rnorm;
 }
 
+// The steering-factor table [4][H][R] in shared memory.
+__device__ __forceinline__ TwS load_tw(const RefineArgs &a) {
+  extern __shared__ __align__(16) float tws[];
+  const int n = 4 * a.H * a.R;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = a.tw[i];
+  __syncthreads();
+  return TwS{tws, a.H, a.R};
+}
+
 template <int KK>
 __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
   using I = StateIdx<KK>;
   const int H = a.H, J = a.J, HJ = H * J;
-  TwS tw{a.tw, H, a.R};
+  const TwS tw = load_tw(a);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
        p += (int64_t)gridDim.x * blockDim.x) {
     const float *xp = a.x + p * (int64_t)(2 * HJ);
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
 template <int KK>
 __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
   const int H = a.H, J = a.J, R = a.R, M = a.M, HJ = H * J;
-  TwS tw{a.tw, H, R};
+  const TwS tw = load_tw(a);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
        p += (int64_t)gridDim.x * blockDim.x) {
     if (a.status[p] <= 0) continue;
@@ -231,7 +240,8 @@ __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
           double gr[KK];
 #pragma unroll
           for (int i = 0; i < KK; ++i) gr[i] = (i < t) ? df_to_d(bg[i]) : 0.0;
-          const double diag = df_to_d(gram_entry(a.xgram, M, H, R, mb, rb, mb, rb, tw));
+          // <S_r d_m, S_r d_m> = ||d_m||^2: steering preserves the norm
+          const double diag = (double)a.anorm[mb].x + (double)a.anorm[mb].y;
           const double rhs = df_to_d(best_ax);
           if (!CholAt<KK, 0>::run(t, S, gr, diag, rhs)) {
             outcome = 1;
@@ -287,10 +297,11 @@ int launch_refine_t(const RefineArgs &a, bool init, cudaStream_t stream) {
   const int64_t blocks = (a.P + 127) / 128;
   const int64_t cap = (int64_t)nsm * 32;
   const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+  const size_t shm = (size_t)4 * a.H * a.R * 4;
   if (init)
-    romp_init_kernel<KK><<<grid, 128, 0, stream>>>(a);
+    romp_init_kernel<KK><<<grid, 128, shm, stream>>>(a);
   else
-    romp_refine_kernel<KK><<<grid, 128, 0, stream>>>(a);
+    romp_refine_kernel<KK><<<grid, 128, shm, stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return RSC_OK;

@@ -75,6 +75,7 @@ void free_dict(rsc_dict *d) {
   cudaFree(d->fallbacks);
   cudaFree(d->steered_bf16);
   cudaFree(d->xgram);
+  cudaFree(d->anorm);
   delete d;
 }
 
@@ -167,8 +168,21 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
         X[((size_t)ma * M + mb) * H + k] =
             make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
       }
+  std::vector<float2> NA(M);
+  for (int m = 0; m < M; ++m) {
+    double n2 = 0.0;
+    for (int k = 0; k < H; ++k)
+      for (int j = 0; j < J; ++j) {
+        const double re = h[((size_t)m * HJ + k * J + j) * 2];
+        const double im = k ? h[((size_t)m * HJ + k * J + j) * 2 + 1] : 0.0;
+        n2 += (k ? 2.0 : 1.0) * (re * re + im * im);
+      }
+    const float hi = (float)n2;
+    NA[m] = make_float2(hi, (float)(n2 - (double)hi));
+  }
   cudaError_t e = cudaMalloc(&d->steered_bf16, B.size() * 2);
   if (e == cudaSuccess) e = cudaMalloc(&d->xgram, X.size() * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc(&d->anorm, NA.size() * sizeof(float2));
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
@@ -177,6 +191,9 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
     e = cudaMemcpyAsync(d->steered_bf16, B.data(), B.size() * 2, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d->xgram, X.data(), X.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->anorm, NA.data(), NA.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                        st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
 
@@ -397,6 +414,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   ra.d = dict->d;
   ra.tw = dict->tw;
   ra.xgram = dict->xgram;
+  ra.anorm = dict->anorm;
   ra.A = take(bA);
   ra.cand_idx = reinterpret_cast<int *>(take(bCI));
   ra.cand_val = reinterpret_cast<float *>(take(bCV));

@@ -29,6 +29,7 @@ struct rsc_dict {
   // sizes are outside what the path handles)
   void *steered_bf16;    // [R*M][kTcKst] bf16, row r*M + m = packed S_r d_m
   float4 *xgram;         // [M][M][H] double-float complex H_k(a,b) = sum_j conj(d_a) d_b
+  float2 *anorm;         // [M] ||d_m||^2 in double-float
   int n;                 // packed real length J (2 kmax + 1)
   // per-phase timing (diagnostic): event pairs recorded around launches
   int timing;
@@ -97,6 +98,7 @@ struct RefineArgs {
   const float *d;
   const float *tw;       // [4][H][R]
   const float4 *xgram;
+  const float2 *anorm;   // [M] ||d_m||^2 in double-float
   unsigned char *A;      // [P][kTcKst] bf16 packed residual rows
   const int *cand_idx;
   const float *cand_val;
