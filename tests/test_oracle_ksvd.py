@@ -1,0 +1,125 @@
+"""Pins for the FP64 rotational K-SVD update oracle (CPU only).
+
+* Closed forms: patches built from steered copies of true atoms with their
+  exact codes give back exactly those atoms (Fig. "code": aligning each
+  residual with S_{-r0} undoes the rotation, so every column is w * d_m).
+* The aligned-residual columns of the literal pseudocode (materialised
+  augmented dictionary, code vectors with one entry zeroed) equal the direct
+  formula S_{-r0}(x - sum_{i != i0} a_i S_{r_i} d_{m_i}).
+* The first singular vector equals the leading eigenvector of Y Y^T
+  (numpy eigh), the unused-atom reset and the repeated-atom reading.
+"""
+import numpy as np
+
+from oracle import ksvd
+from paper_1806_04374_gb300 import synth
+
+J, KMAX = 6, 8
+H = KMAX + 1
+
+
+def test_pack_unpack_roundtrip_and_norm():
+    rng = np.random.default_rng(0)
+    c = rng.standard_normal((4, H, J, 2))
+    c[:, 0, :, 1] = 0
+    assert np.allclose(ksvd.unpack(ksvd.pack(c), H, J), c)
+    n2 = (c[:, 0, :, 0] ** 2).sum(-1) + 2 * (c[:, 1:] ** 2).sum((-1, -2, -3))
+    assert np.allclose((ksvd.pack(c) ** 2).sum(-1), n2)
+
+
+def test_single_atom_recovered_exactly():
+    rng = np.random.default_rng(1)
+    R = 16
+    d_true = synth.make_dictionary(1, J, KMAX, 11).astype(np.float64)
+    d_old = synth.make_dictionary(1, J, KMAX, 12).astype(np.float64)
+    P = 40
+    r = rng.integers(0, R, P)
+    w = rng.standard_normal(P)
+    x = np.stack([w[p] * ksvd.steer(d_true[0], 2 * np.pi * r[p] / R) for p in range(P)])
+    atom = np.zeros((P, 1), int)
+    d_new, n_used = ksvd.ksvd_update(x, d_old, R, atom, r[:, None], w[:, None])
+    assert n_used[0] == P
+    v_new, v_true = ksvd.pack(d_new[0]), ksvd.pack(d_true[0])
+    v_true /= np.linalg.norm(v_true)
+    assert abs(abs(v_new @ v_true) - 1.0) < 1e-12
+    assert v_new[np.abs(v_new).argmax()] > 0  # sign reading
+
+
+def test_two_atoms_exact_codes_recovered():
+    rng = np.random.default_rng(2)
+    R = 12
+    d = synth.make_dictionary(2, J, KMAX, 21).astype(np.float64)
+    P = 30
+    r = rng.integers(0, R, (P, 2))
+    w = rng.standard_normal((P, 2))
+    x = np.stack([w[p, 0] * ksvd.steer(d[0], 2 * np.pi * r[p, 0] / R) +
+                  w[p, 1] * ksvd.steer(d[1], 2 * np.pi * r[p, 1] / R) for p in range(P)])
+    atom = np.tile(np.array([0, 1]), (P, 1))
+    d_new, n_used = ksvd.ksvd_update(x, d, R, atom, r, w)
+    for m in range(2):
+        v = ksvd.pack(d[m])
+        assert abs(abs(ksvd.pack(d_new[m]) @ v) / np.linalg.norm(v) - 1.0) < 1e-12
+
+
+def _direct_columns(x, d, R, atom, angle, coef, m):
+    """S_{-r0}(x - sum_{i != i0} a_i S_{r_i} d_{m_i}) for patches using m."""
+    cols = []
+    for p in range(x.shape[0]):
+        occ = [i for i in range(atom.shape[1]) if atom[p, i] == m]
+        if not occ:
+            continue
+        i0 = max(occ, key=lambda i: (abs(coef[p, i]), -i))
+        res = x[p].astype(np.float64).copy()
+        for i in range(atom.shape[1]):
+            if i != i0 and atom[p, i] >= 0:
+                res -= coef[p, i] * ksvd.steer(d[atom[p, i]], 2 * np.pi * angle[p, i] / R)
+        cols.append(ksvd.pack(ksvd.steer(res, -2 * np.pi * angle[p, i0] / R)))
+    return np.stack(cols, 1)
+
+
+def test_literal_columns_equal_direct_formula_and_svd_equals_eigh():
+    import oracle
+    d, x, _, wl = synth.workload_inputs("omp_small", P=120)
+    o = oracle.romp(x, d, wl.R, wl.K)
+    d_new, n_used = ksvd.ksvd_update(x, d, wl.R, o["atom"], o["angle"], o["coef"])
+    for m in range(d.shape[0]):
+        if n_used[m] == 0:
+            continue
+        Y = _direct_columns(x, d.astype(np.float64), wl.R, o["atom"], o["angle"], o["coef"], m)
+        assert Y.shape[1] == n_used[m]
+        wv, V = np.linalg.eigh(Y @ Y.T)
+        u = V[:, -1]
+        if u[np.abs(u).argmax()] < 0:
+            u = -u
+        assert np.allclose(ksvd.pack(d_new[m]), u, atol=1e-9), m
+
+
+def test_repeated_atom_uses_largest_weight_and_unused_reset():
+    R = 8
+    d = synth.make_dictionary(3, J, KMAX, 31).astype(np.float64)
+    rng = np.random.default_rng(3)
+    P = 6
+    x = rng.standard_normal((P, H, J, 2))
+    x[:, 0, :, 1] = 0
+    # patch 0 uses atom 0 twice (weights 0.2 at r=1, -0.9 at r=5); atom 2 unused
+    atom = np.array([[0, 0], [1, -1], [1, 0], [0, 1], [1, -1], [0, -1]])
+    angle = np.array([[1, 5], [2, -1], [3, 4], [6, 7], [0, -1], [2, -1]])
+    coef = np.array([[0.2, -0.9], [1.0, 0], [0.5, 0.4], [0.3, 0.7], [0.8, 0], [1.1, 0]])
+    d_new, n_used = ksvd.ksvd_update(x, d, R, atom, angle, coef)
+    assert list(n_used) == [4, 4, 0]
+    Y = _direct_columns(x, d, R, atom, angle, coef, 0)
+    # the column of patch 0 is aligned with the -0.9 occurrence (r0 = 5)
+    res = x[0] - 0.2 * ksvd.steer(d[0], 2 * np.pi * 1 / R)
+    assert np.allclose(Y[:, 0], ksvd.pack(ksvd.steer(res, -2 * np.pi * 5 / R)))
+    # atom 2 reset to the unit-normalised patch with the largest coding error
+    Aug = ksvd.augmented(d, R)
+    X = ksvd.pack(x)
+    errs = []
+    for p in range(P):
+        b = np.zeros(3 * R)
+        for i in range(2):
+            if atom[p, i] >= 0:
+                b[atom[p, i] * R + angle[p, i]] += coef[p, i]
+        errs.append(np.sum((X[p] - Aug @ b) ** 2))
+    p_star = int(np.argmax(errs))
+    assert np.allclose(ksvd.pack(d_new[2]), X[p_star] / np.linalg.norm(X[p_star]))
