@@ -116,6 +116,34 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
                float *resid_norm2, void *stream);
 
 /*
+ * rsc_ksvd_update -- one rotational K-SVD dictionary update (the atom loop
+ * of the R-K-SVD pseudocode, Fig. "code", Sec. II-C) from given codes.
+ * For every atom m, each patch whose code uses m at angle r0 contributes the
+ * column S_{-r0}(x_p - D_aug b_p), b_p = the patch's code without that (m, r0)
+ * entry; the new atom is the first left singular vector of those columns,
+ * computed as the leading eigenvector of their covariance (FP32 products,
+ * FP64 sums, FP64 power iteration from the old atom, to convergence or 5000
+ * iterations).  All atoms are updated from the dictionary `dict` and the same
+ * codes.  Readings of the paper: a patch using m more than once contributes
+ * its occurrence with the largest |weight| (ties: earliest); an atom used by
+ * no patch is reset to the unit-normalised patch with the largest coding
+ * error (several: successive patches in descending error, at most 64
+ * distinct); the largest-magnitude packed entry of each new atom is positive.
+ *   dict      : the dictionary the codes refer to.
+ *   x         : device, P x (kmax+1) x J x 2 floats (the coded patches).
+ *   P, K      : patches (>= 1) and code length (1..16).
+ *   atom, angle_idx, coef : device codes as written by rsc_encode (P x K).
+ *   new_coef  : device output, M x (kmax+1) x J x 2 floats, unit-norm atoms
+ *               (pass it to rsc_dict_create for the next iteration).
+ *   n_used    : device int32 [M] or NULL: patches that used each atom.
+ *   stream    : cudaStream_t.  Returns after launch; scratch comes from the
+ *               stream-ordered allocator.
+ */
+int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
+                    const int32_t *atom, const int32_t *angle_idx, const double *coef,
+                    float *new_coef, int32_t *n_used, void *stream);
+
+/*
  * rsc_encode_host -- rsc_encode on HOST buffers (same shapes and meaning as
  * above, all pointers host memory; pinned memory gives the fastest copies).
  * Copies the patches to the device in chunks, codes them and copies the

@@ -31,6 +31,7 @@ EXPORTS = (
     "rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode", "rsc_encode_host",
     "rsc_dict_check", "rsc_dict_fallback_count", "rsc_dict_set_timing", "rsc_dict_timing",
     "rsc_status_string", "rsc_last_cuda_error", "rsc_version", "rsc_encode_noalloc",
+    "rsc_ksvd_update",
 )
 
 
@@ -66,6 +67,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_encode.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_encode_host.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.rsc_encode_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp]
+    lib.rsc_ksvd_update.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_dict_check.argtypes = [vp, vp]
     lib.rsc_dict_fallback_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.rsc_dict_set_timing.argtypes = [vp, ctypes.c_int]
@@ -77,7 +79,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_version.argtypes = []
     for name in ("rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode",
                  "rsc_encode_host", "rsc_dict_check", "rsc_dict_fallback_count",
-                 "rsc_dict_set_timing", "rsc_dict_timing", "rsc_version", "rsc_encode_noalloc"):
+                 "rsc_dict_set_timing", "rsc_dict_timing", "rsc_version", "rsc_encode_noalloc",
+                 "rsc_ksvd_update"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -135,6 +138,15 @@ def rsc_encode_noalloc(handle: int, x_ptr: int, P: int, K: int, atom_ptr: int, a
     return load_library().rsc_encode_noalloc(vp(handle), vp(x_ptr), int(P), int(K), vp(atom_ptr),
                                              vp(angle_idx_ptr), vp(angle_ptr or None),
                                              vp(coef_ptr), vp(resid_norm2_ptr or None), vp(stream))
+
+
+def rsc_ksvd_update(handle: int, x_ptr: int, P: int, K: int, atom_ptr: int, angle_idx_ptr: int,
+                    coef_ptr: int, new_coef_ptr: int, n_used_ptr: int, stream: int = 0) -> int:
+    """Raw call of the rotational K-SVD dictionary update; returns the status."""
+    vp = ctypes.c_void_p
+    return load_library().rsc_ksvd_update(vp(handle), vp(x_ptr), int(P), int(K), vp(atom_ptr),
+                                          vp(angle_idx_ptr), vp(coef_ptr), vp(new_coef_ptr),
+                                          vp(n_used_ptr or None), vp(stream))
 
 
 def rsc_dict_check(handle: int, stream: int = 0) -> int:
@@ -245,3 +257,19 @@ def encode_host(dic: Dictionary, x, K: int, precision: str = "fp32", out=None):
     if st != RSC_OK:
         raise RscError(st, "rsc_encode_host")
     return out
+
+
+def ksvd_update(dic: Dictionary, x, codes: dict, stream=None):
+    """rsc_ksvd_update on CUDA tensors: x [P, kmax+1, J, 2] float32 and the
+    codes returned by encode().  Returns (new atoms [M, kmax+1, J, 2] float32,
+    n_used [M] int32)."""
+    import torch
+    P, K = codes["atom"].shape
+    new = torch.empty((dic.M, dic.H, dic.J, 2), dtype=torch.float32, device=x.device)
+    used = torch.empty((dic.M,), dtype=torch.int32, device=x.device)
+    st = rsc_ksvd_update(dic.handle, x.data_ptr(), P, K, codes["atom"].data_ptr(),
+                         codes["angle_idx"].data_ptr(), codes["coef"].data_ptr(), new.data_ptr(),
+                         used.data_ptr(), _stream_handle(stream))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_ksvd_update")
+    return new, used

@@ -1,0 +1,440 @@
+// ksvd.cu -- the rotational K-SVD dictionary update (inner loop of the
+// R-K-SVD pseudocode, Fig. "code", Sec. II-C) on the GPU.
+//
+// For atom m, every patch whose code uses m at angle r0 contributes the
+// column y = S_{-r0}(x_p - D_aug b_p), b_p being the patch's code with the
+// (m, r0) entry removed -- equivalently y = S_{-r0} e_p + a_{i0} d_m with the
+// full coding residual e_p = x_p - sum_i a_i S_{r_i} d_{m_i}.  The new atom is
+// the first left singular vector of [y ...], i.e. the leading eigenvector of
+// C_m = sum y y^T.  Every atom is updated from the same (old) dictionary and
+// the same codes.  Readings: a repeated atom uses its occurrence with the
+// largest |weight| (ties: earliest); an unused atom is reset to the
+// unit-normalised patch with the largest coding error (successive patches in
+// descending error for several, ties: smaller index); the eigenvector's
+// largest-magnitude packed entry is made positive.
+//
+// Kernels: per patch (count samples per atom, fill the per-atom sample lists,
+// packed FP32 residuals and coding errors); per atom one CTA accumulating C_m
+// (FP32 partial sums over 32 samples, folded into FP64) and one CTA running an
+// FP64 power iteration from the old atom; one CTA for the resets.  All
+// vectors are packed reals (k = 0 real parts, sqrt(2) Re/Im of k >= 1).
+#include <math.h>
+
+#include <algorithm>
+
+#include "rsc_internal.h"
+
+namespace {
+
+constexpr int kCovThreads = 256;
+constexpr int kCovBatch = 32;
+constexpr int kEigThreads = 256;
+constexpr int kMaxPacked = 2 * kMaxEntries;
+
+struct KsvdArgs {
+  const float *x;
+  int64_t P;
+  int K, M, J, H, R, n, ldE;
+  const float *d;   // [M][H][J][2]
+  const float *tw;  // [4][H][R]
+  const int32_t *atom;
+  const int32_t *angle;
+  const double *coef;
+  float *E;         // [P][ldE] packed residuals
+  float *err;       // [P]
+  int *count;       // [M]
+  int *offset;      // [M + 1]
+  int *cursor;      // [M]
+  int2 *samples;    // [sum count] (patch, occurrence)
+  double *C;        // [M][n][n]
+  float *new_coef;  // [M][H][J][2]
+  int32_t *n_used;  // [M] or null
+};
+
+// Occurrence i of patch p is the one that represents its atom (largest
+// |weight| among the occurrences of that atom, ties: earliest).
+__device__ __forceinline__ bool chosen(const KsvdArgs &a, int64_t p, int i) {
+  const int m = a.atom[p * a.K + i];
+  if (m < 0) return false;
+  const double w = fabs(a.coef[p * a.K + i]);
+  for (int q = 0; q < a.K; ++q) {
+    if (q == i || a.atom[p * a.K + q] != m) continue;
+    const double v = fabs(a.coef[p * a.K + q]);
+    if (v > w || (v == w && q < i)) return false;
+  }
+  return true;
+}
+
+__global__ void ksvd_count_kernel(const KsvdArgs a) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
+       p += (int64_t)gridDim.x * blockDim.x)
+    for (int i = 0; i < a.K; ++i)
+      if (chosen(a, p, i)) atomicAdd(&a.count[a.atom[p * a.K + i]], 1);
+}
+
+__global__ void ksvd_scan_kernel(const KsvdArgs a) {
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int m = 0; m < a.M; ++m) {
+      a.offset[m] = s;
+      a.cursor[m] = s;
+      s += a.count[m];
+      if (a.n_used) a.n_used[m] = a.count[m];
+    }
+    a.offset[a.M] = s;
+  }
+}
+
+// Fills the sample lists and writes each patch's packed FP32 residual.
+__global__ void ksvd_fill_kernel(const KsvdArgs a) {
+  const int J = a.J, H = a.H, HJ = H * J, R = a.R;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    for (int i = 0; i < a.K; ++i)
+      if (chosen(a, p, i)) {
+        const int slot = atomicAdd(&a.cursor[a.atom[p * a.K + i]], 1);
+        a.samples[slot] = make_int2((int)p, i);
+      }
+    const float2 *xp = reinterpret_cast<const float2 *>(a.x + p * (int64_t)(2 * HJ));
+    float *ep = a.E + p * (int64_t)a.ldE;
+    float n2 = 0.0f;
+    for (int e = 0; e < HJ; ++e) {
+      const int k = e / J;
+      float2 v = xp[e];
+      float re = v.x, im = k ? v.y : 0.0f;
+      for (int i = 0; i < a.K; ++i) {
+        const int m = a.atom[p * a.K + i];
+        if (m < 0) continue;
+        const int r = a.angle[p * a.K + i];
+        const float c = a.tw[(0 * H + k) * R + r], s = a.tw[(2 * H + k) * R + r];
+        const float2 dv = reinterpret_cast<const float2 *>(a.d)[(size_t)m * HJ + e];
+        const float dim = k ? dv.y : 0.0f;
+        const float w = (float)a.coef[p * a.K + i];
+        re = fmaf(-w, fmaf(c, dv.x, s * dim), re);
+        im = fmaf(-w, fmaf(c, dim, -s * dv.x), im);
+      }
+      if (k == 0) {
+        ep[e] = re;
+        n2 = fmaf(re, re, n2);
+      } else {
+        const int q = 2 * e - J;
+        ep[q] = 1.41421356237309515f * re;
+        ep[q + 1] = 1.41421356237309515f * im;
+        n2 = fmaf(2.0f * re, re, fmaf(2.0f * im, im, n2));
+      }
+    }
+    a.err[p] = n2;
+  }
+}
+
+// C_m = sum over the atom's samples of y y^T (upper triangle, then mirrored).
+__global__ void __launch_bounds__(kCovThreads) ksvd_cov_kernel(const KsvdArgs a) {
+  extern __shared__ float ysm[];  // kCovBatch rows of n + 1 floats
+  const int m = blockIdx.x;
+  const int n = a.n, J = a.J, H = a.H, HJ = H * J, R = a.R;
+  const int ldy = n + 1;
+  auto ys = [&](int s, int q) -> float & { return ysm[s * ldy + q]; };
+  const int beg = a.offset[m], end = a.offset[m + 1];
+  const int ntri = n * (n + 1) / 2;
+  double *Cm = a.C + (size_t)m * n * n;
+  // this thread's entries of the upper triangle: t = t0 + u * 256 + tid
+  for (int t0 = 0; t0 < ntri; t0 += kCovThreads * 24) {
+    // up to 24 entries per thread per pass (registers)
+    double acc[24];
+    int ii[24], jj[24];
+#pragma unroll
+    for (int u = 0; u < 24; ++u) {
+      acc[u] = 0.0;
+      const int t = t0 + u * kCovThreads + threadIdx.x;
+      int i = -1, j = -1;
+      if (t < ntri) {
+        // row i of the upper triangle starts at i*n - i(i-1)/2
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (mid * n - mid * (mid - 1) / 2 <= t) lo = mid; else hi = mid - 1;
+        }
+        i = lo;
+        j = i + (t - (i * n - i * (i - 1) / 2));
+      }
+      ii[u] = i;
+      jj[u] = j;
+    }
+    for (int b0 = beg; b0 < end; b0 += kCovBatch) {
+      const int nb = min(kCovBatch, end - b0);
+      __syncthreads();
+      // build y for the batch: y = S_{-r0} e_p + a_{i0} d_m (packed)
+      for (int w = threadIdx.x; w < nb * HJ; w += blockDim.x) {
+        const int s = w / HJ, e = w - s * HJ;
+        const int2 smp = a.samples[b0 + s];
+        const int64_t p = smp.x;
+        const int i0 = smp.y;
+        const int r0 = a.angle[p * a.K + i0];
+        const float w0 = (float)a.coef[p * a.K + i0];
+        const int k = e / J;
+        const float *ep = a.E + p * (int64_t)a.ldE;
+        const float2 dv = reinterpret_cast<const float2 *>(a.d)[(size_t)m * HJ + e];
+        if (k == 0) {
+          ys(s, e) = ep[e] + w0 * dv.x;
+        } else {
+          const int q = 2 * e - J;
+          const float re = ep[q], im = ep[q + 1];
+          // S_{-theta}: harmonic k times exp(+i k theta)
+          const float c = a.tw[(0 * H + k) * R + r0], sn = a.tw[(2 * H + k) * R + r0];
+          ys(s, q) = fmaf(re, c, -im * sn) + 1.41421356237309515f * w0 * dv.x;
+          ys(s, q + 1) = fmaf(re, sn, im * c) + 1.41421356237309515f * w0 * dv.y;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 24; ++u) {
+        if (ii[u] < 0) continue;
+        float part = 0.0f;
+        for (int s = 0; s < nb; ++s) part = fmaf(ys(s, ii[u]), ys(s, jj[u]), part);
+        acc[u] += (double)part;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 24; ++u) {
+      if (ii[u] < 0) continue;
+      Cm[(size_t)ii[u] * n + jj[u]] = acc[u];
+      Cm[(size_t)jj[u] * n + ii[u]] = acc[u];
+    }
+  }
+}
+
+__device__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+// Leading eigenvector of C_m by FP64 power iteration from the old atom.
+__global__ void __launch_bounds__(kEigThreads) ksvd_eig_kernel(const KsvdArgs a, int max_iter) {
+  extern __shared__ __align__(16) double es[];
+  const int m = blockIdx.x;
+  if (a.count[m] == 0) return;
+  const int n = a.n, J = a.J, H = a.H, HJ = H * J;
+  double *Cs = es;                 // n * n
+  double *u = Cs + n * n;          // n
+  double *v = u + n;               // n
+  double *red = v + n;             // 32
+  const double *Cm = a.C + (size_t)m * n * n;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) Cs[i] = Cm[i];
+  // start: the old atom, packed
+  for (int e = threadIdx.x; e < HJ; e += blockDim.x) {
+    const int k = e / J;
+    const float2 dv = reinterpret_cast<const float2 *>(a.d)[(size_t)m * HJ + e];
+    if (k == 0) {
+      u[e] = dv.x;
+    } else {
+      u[2 * e - J] = 1.4142135623730951 * dv.x;
+      u[2 * e - J + 1] = 1.4142135623730951 * dv.y;
+    }
+  }
+  __syncthreads();
+  double lam_old = 0.0;
+  for (int it = 0; it < max_iter; ++it) {
+    double loc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s = fma(Cs[i * n + j], u[j], s);
+      v[i] = s;
+      loc = fma(s, s, loc);
+    }
+    const double nv2 = block_sum(loc, red);
+    double dot = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dot = fma(v[i], u[i], dot);
+    const double lam = block_sum(dot, red);  // Rayleigh quotient (u unit)
+    const double inv = nv2 > 0.0 ? 1.0 / sqrt(nv2) : 0.0;
+    double dif = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double nu = v[i] * inv;
+      dif = fma(nu - u[i], nu - u[i], dif);
+      u[i] = nu;
+    }
+    const double d2 = block_sum(dif, red);
+    if (nv2 == 0.0) break;
+    if (it > 0 && d2 < 1e-26 && fabs(lam - lam_old) <= 1e-15 * fabs(lam)) break;
+    lam_old = lam;
+  }
+  __syncthreads();
+  // sign: the largest-magnitude entry positive (first index on ties)
+  if (threadIdx.x == 0) {
+    int arg = 0;
+    for (int i = 1; i < n; ++i)
+      if (fabs(u[i]) > fabs(u[arg])) arg = i;
+    red[0] = u[arg] < 0.0 ? -1.0 : 1.0;
+  }
+  __syncthreads();
+  const double sg = red[0];
+  float *out = a.new_coef + (size_t)m * HJ * 2;
+  for (int e = threadIdx.x; e < HJ; e += blockDim.x) {
+    const int k = e / J;
+    if (k == 0) {
+      out[2 * e] = (float)(sg * u[e]);
+      out[2 * e + 1] = 0.0f;
+    } else {
+      out[2 * e] = (float)(sg * u[2 * e - J] * 0.7071067811865476);
+      out[2 * e + 1] = (float)(sg * u[2 * e - J + 1] * 0.7071067811865476);
+    }
+  }
+}
+
+// Unused atoms: successive patches of largest coding error, unit-normalised.
+__global__ void ksvd_reset_kernel(const KsvdArgs a) {
+  __shared__ float bv[1024];
+  __shared__ long long bi[1024];
+  __shared__ long long picked[64];
+  __shared__ double nrm;
+  const int J = a.J, HJ = a.H * J;
+  int npicked = 0;
+  for (int m = 0; m < a.M; ++m) {
+    if (a.count[m] != 0) continue;
+    float best = -1.0f;
+    long long bp = -1;
+    for (int64_t p = threadIdx.x; p < a.P; p += blockDim.x) {
+      bool taken = false;
+      for (int q = 0; q < npicked && q < 64; ++q) taken |= (picked[q] == p);
+      if (taken) continue;
+      const float e = a.err[p];
+      if (e > best) {
+        best = e;
+        bp = p;
+      }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = bp;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        const float o = bv[threadIdx.x + s];
+        const long long oi = bi[threadIdx.x + s];
+        if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi >= 0 &&
+                                    (bi[threadIdx.x] < 0 || oi < bi[threadIdx.x]))) {
+          bv[threadIdx.x] = o;
+          bi[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    const long long p = bi[0];
+    __syncthreads();
+    if (p < 0) continue;
+    if (threadIdx.x == 0) {
+      if (npicked < 64) picked[npicked] = p;
+      const float *xp = a.x + p * (int64_t)(2 * HJ);
+      double s = 0.0;
+      for (int e = 0; e < HJ; ++e) {
+        const double re = xp[2 * e], im = e < J ? 0.0 : xp[2 * e + 1];
+        s += (e < J ? 1.0 : 2.0) * (re * re + im * im);
+      }
+      nrm = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    }
+    ++npicked;
+    __syncthreads();
+    const float *xp = a.x + p * (int64_t)(2 * HJ);
+    float *out = a.new_coef + (size_t)m * HJ * 2;
+    for (int e = threadIdx.x; e < HJ; e += blockDim.x) {
+      out[2 * e] = (float)(xp[2 * e] * nrm);
+      out[2 * e + 1] = e < J ? 0.0f : (float)(xp[2 * e + 1] * nrm);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
+                               const int32_t *atom, const int32_t *angle_idx, const double *coef,
+                               float *new_coef, int32_t *n_used, void *stream) {
+  if (!dict || P < 1 || K < 1 || K > kMaxK || !x || !atom || !angle_idx || !coef || !new_coef)
+    return RSC_ERR_INVALID;
+  if (P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  if (dev != dict->device) return RSC_ERR_INVALID;
+  const int M = dict->M, J = dict->J, H = dict->H, R = dict->R;
+  const int n = J + 2 * dict->kmax * J;
+  if (n > kMaxPacked) return RSC_ERR_UNSUPPORTED;
+  // the unused-atom reset keeps at most 64 picks
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int ldE = (n + 3) & ~3;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t bE = al((size_t)P * ldE * 4), bErr = al((size_t)P * 4), bCnt = al((size_t)M * 4),
+               bOff = al((size_t)(M + 1) * 4), bSmp = al((size_t)P * K * 8),
+               bC = al((size_t)M * n * n * 8);
+  unsigned char *scratch = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bE + bErr + 2 * bCnt + bOff + bSmp + bC,
+                      st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return RSC_ERR_OOM;
+  }
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  KsvdArgs a;
+  a.x = x;
+  a.P = P;
+  a.K = K;
+  a.M = M;
+  a.J = J;
+  a.H = H;
+  a.R = R;
+  a.n = n;
+  a.ldE = ldE;
+  a.d = dict->d;
+  a.tw = dict->tw;
+  a.atom = atom;
+  a.angle = angle_idx;
+  a.coef = coef;
+  unsigned char *q = scratch;
+  a.E = reinterpret_cast<float *>(q);
+  q += bE;
+  a.err = reinterpret_cast<float *>(q);
+  q += bErr;
+  a.count = reinterpret_cast<int *>(q);
+  q += bCnt;
+  a.cursor = reinterpret_cast<int *>(q);
+  q += bCnt;
+  a.offset = reinterpret_cast<int *>(q);
+  q += bOff;
+  a.samples = reinterpret_cast<int2 *>(q);
+  q += bSmp;
+  a.C = reinterpret_cast<double *>(q);
+  a.new_coef = new_coef;
+  a.n_used = n_used;
+
+  int rc = RSC_OK;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<int64_t>((P + 255) / 256, (int64_t)nsm * 8);
+  const size_t eig_smem = ((size_t)n * n + 2 * n + 32) * 8;
+  e = cudaMemsetAsync(a.count, 0, (size_t)M * 4, st);
+  if (e == cudaSuccess) {
+    ksvd_count_kernel<<<grid, 256, 0, st>>>(a);
+    ksvd_scan_kernel<<<1, 32, 0, st>>>(a);
+    ksvd_fill_kernel<<<grid, 256, 0, st>>>(a);
+    const size_t cov_smem = (size_t)kCovBatch * (n + 1) * 4;
+    e = cudaFuncSetAttribute(ksvd_cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cov_smem);
+    if (e == cudaSuccess) ksvd_cov_kernel<<<M, kCovThreads, cov_smem, st>>>(a);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ksvd_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)eig_smem);
+    if (e == cudaSuccess) {
+      ksvd_eig_kernel<<<M, kEigThreads, eig_smem, st>>>(a, 5000);
+      ksvd_reset_kernel<<<1, 1024, 0, st>>>(a);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (rc == RSC_OK && e2 != cudaSuccess) rc = rsc_cuda_fail(e2);
+  return rc;
+}

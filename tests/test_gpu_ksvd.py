@@ -1,0 +1,89 @@
+"""GPU rotational K-SVD update (rsc_ksvd_update, through the C ABI) against
+the FP64 oracle of oracle/ksvd.py, from identical codes."""
+import numpy as np
+import pytest
+
+from oracle import ksvd
+from paper_1806_04374_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsc(cuda_ok):
+    import paper_1806_04374_gb300 as rsc
+    rsc.load_library()
+    return rsc
+
+
+def gpu_update(rsc, x, d, R, atom, angle, coef):
+    import torch
+    dic = rsc.Dictionary(torch.from_numpy(np.ascontiguousarray(d, np.float32)).cuda(), R)
+    codes = {"atom": torch.from_numpy(np.ascontiguousarray(atom, np.int32)).cuda(),
+             "angle_idx": torch.from_numpy(np.ascontiguousarray(angle, np.int32)).cuda(),
+             "coef": torch.from_numpy(np.ascontiguousarray(coef, np.float64)).cuda()}
+    new, used = rsc.ksvd_update(dic, torch.from_numpy(np.ascontiguousarray(x)).cuda(), codes)
+    torch.cuda.synchronize()
+    out = new.cpu().numpy(), used.cpu().numpy()
+    dic.close()
+    return out
+
+
+def assert_atoms_close(d_gpu, d_ref, tol=2e-5):
+    for m in range(d_ref.shape[0]):
+        u, v = ksvd.pack(d_gpu[m]), ksvd.pack(d_ref[m])
+        assert abs(np.linalg.norm(u) - 1.0) < 1e-5, m
+        assert np.max(np.abs(u - v)) < tol, (m, np.max(np.abs(u - v)))
+
+
+def test_single_atom_closed_form(rsc):
+    rng = np.random.default_rng(1)
+    R = 16
+    d_true = synth.make_dictionary(1, 6, 8, 11)
+    d_old = synth.make_dictionary(1, 6, 8, 12)
+    P = 200
+    r = rng.integers(0, R, P)
+    w = rng.standard_normal(P)
+    x = np.stack([w[p] * ksvd.steer(d_true[0], 2 * np.pi * r[p] / R) for p in range(P)])
+    x = x.astype(np.float32)
+    new, used = gpu_update(rsc, x, d_old, R, np.zeros((P, 1), np.int32), r[:, None], w[:, None])
+    assert used[0] == P
+    u, v = ksvd.pack(new[0]), ksvd.pack(d_true[0])
+    assert abs(abs(u @ v) / np.linalg.norm(v) - 1.0) < 1e-6
+
+
+def test_update_matches_oracle_on_encoded_codes(rsc):
+    """Codes from rsc_encode on the small workload (1000 patches, M = 16,
+    R = 32, K = 3); both updates start from the same codes."""
+    import torch
+    d, x, _, wl = synth.workload_inputs("omp_small")
+    dic = rsc.Dictionary(torch.from_numpy(d).cuda(), wl.R)
+    codes = rsc.encode(dic, torch.from_numpy(x).cuda(), wl.K, "fp32")
+    torch.cuda.synchronize()
+    c = {k: v.cpu().numpy() for k, v in codes.items()}
+    dic.close()
+    ref, used_ref = ksvd.ksvd_update(x, d, wl.R, c["atom"], c["angle_idx"], c["coef"])
+    new, used = gpu_update(rsc, x, d, wl.R, c["atom"], c["angle_idx"], c["coef"])
+    assert np.array_equal(used, used_ref)
+    assert_atoms_close(new, ref)
+
+
+def test_unused_atoms_reset_and_repeated_atoms(rsc):
+    """Atoms 3 and 4 are used by no patch: reset to the two patches with the
+    largest coding error; atom 0 appears twice in some codes."""
+    rng = np.random.default_rng(7)
+    M, R, K, P = 5, 8, 3, 300
+    d = synth.make_dictionary(M, 6, 8, 70)
+    x, _ = synth.make_patches(d[:3], P, 2, 0.2, 71)
+    atom = rng.integers(0, 3, (P, K)).astype(np.int32)
+    atom[::7, 1] = atom[::7, 0]
+    angle = rng.integers(0, R, (P, K)).astype(np.int32)
+    angle[::7, 1] = (angle[::7, 0] + 3) % R
+    coef = rng.standard_normal((P, K))
+    atom[::5, 2] = -1
+    angle[::5, 2] = -1
+    coef[::5, 2] = 0.0
+    ref, used_ref = ksvd.ksvd_update(x, d, R, atom, angle, coef)
+    new, used = gpu_update(rsc, x, d, R, atom, angle, coef)
+    assert np.array_equal(used, used_ref) and used[3] == 0 and used[4] == 0
+    assert_atoms_close(new, ref)
