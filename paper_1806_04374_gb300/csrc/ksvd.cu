@@ -170,7 +170,12 @@ __global__ void __launch_bounds__(kCovThreads) ksvd_cov_kernel(const KsvdArgs a)
         const int64_t p = smp.x;
         const int i0 = smp.y;
         const int r0 = a.angle[p * a.K + i0];
-        const float w0 = (float)a.coef[p * a.K + i0];
+        // the code entry of (m, r0): every occurrence of that pair (Fig.
+        // "code" zeroes the whole entry b_{r0}[m])
+        double wsum = 0.0;
+        for (int i = 0; i < a.K; ++i)
+          if (a.atom[p * a.K + i] == m && a.angle[p * a.K + i] == r0) wsum += a.coef[p * a.K + i];
+        const float w0 = (float)wsum;
         const int k = e / J;
         const float *ep = a.E + p * (int64_t)a.ldE;
         const float2 dv = reinterpret_cast<const float2 *>(a.d)[(size_t)m * HJ + e];

@@ -29,11 +29,24 @@ def gpu_update(rsc, x, d, R, atom, angle, coef):
     return out
 
 
-def assert_atoms_close(d_gpu, d_ref, tol=2e-5):
+def eig_ratio(x, d, R, atom, angle, coef, m):
+    """lambda_1 / (lambda_1 - lambda_2) of the aligned-residual covariance of
+    atom m: the conditioning of its leading eigenvector (Davis-Kahan)."""
+    from test_oracle_ksvd import _direct_columns
+    Y = _direct_columns(x, np.asarray(d, np.float64), R, atom, angle, coef, m)
+    lam = np.linalg.eigvalsh(Y @ Y.T)
+    return lam[-1] / max(lam[-1] - lam[-2], 1e-300)
+
+
+def assert_atoms_close(d_gpu, d_ref, ratios=None):
+    """GPU covariance entries carry ~1e-6 relative error (FP32 products over
+    batches of 32, FP64 sums), so an atom may differ from the exact singular
+    vector by ~1e-6 lambda_1 / (lambda_1 - lambda_2)."""
     for m in range(d_ref.shape[0]):
         u, v = ksvd.pack(d_gpu[m]), ksvd.pack(d_ref[m])
         assert abs(np.linalg.norm(u) - 1.0) < 1e-5, m
-        assert np.max(np.abs(u - v)) < tol, (m, np.max(np.abs(u - v)))
+        tol = 2e-5 + (1e-5 * ratios[m] if ratios is not None and m in ratios else 0.0)
+        assert np.max(np.abs(u - v)) < tol, (m, np.max(np.abs(u - v)), tol)
 
 
 def test_single_atom_closed_form(rsc):
@@ -86,4 +99,5 @@ def test_unused_atoms_reset_and_repeated_atoms(rsc):
     ref, used_ref = ksvd.ksvd_update(x, d, R, atom, angle, coef)
     new, used = gpu_update(rsc, x, d, R, atom, angle, coef)
     assert np.array_equal(used, used_ref) and used[3] == 0 and used[4] == 0
-    assert_atoms_close(new, ref)
+    ratios = {m: eig_ratio(x, d, R, atom, angle, coef, m) for m in range(3)}
+    assert_atoms_close(new, ref, ratios)

@@ -62,16 +62,18 @@ def test_two_atoms_exact_codes_recovered():
 
 
 def _direct_columns(x, d, R, atom, angle, coef, m):
-    """S_{-r0}(x - sum_{i != i0} a_i S_{r_i} d_{m_i}) for patches using m."""
+    """S_{-r0}(x - sum of a_i S_{r_i} d_{m_i} over the steps whose (atom,
+    angle) is not (m, r0)) for the patches using m."""
     cols = []
     for p in range(x.shape[0]):
         occ = [i for i in range(atom.shape[1]) if atom[p, i] == m]
         if not occ:
             continue
         i0 = max(occ, key=lambda i: (abs(coef[p, i]), -i))
+        r0 = angle[p, i0]
         res = x[p].astype(np.float64).copy()
         for i in range(atom.shape[1]):
-            if i != i0 and atom[p, i] >= 0:
+            if atom[p, i] >= 0 and not (atom[p, i] == m and angle[p, i] == r0):
                 res -= coef[p, i] * ksvd.steer(d[atom[p, i]], 2 * np.pi * angle[p, i] / R)
         cols.append(ksvd.pack(ksvd.steer(res, -2 * np.pi * angle[p, i0] / R)))
     return np.stack(cols, 1)
