@@ -56,6 +56,26 @@ def algorithmic_bytes_per_patch(wl) -> int:
     return 4 * n_floats + wl.K * (4 + 4 + 4 + 8) + 4
 
 
+def recovery(d_learned, d_true, R: int, threshold: float = 0.99, refine: int = 16) -> float:
+    """Evaluation of a learned dictionary (host, numpy): the fraction of true
+    atoms t with max over learned atoms m and angles theta (an R*refine grid)
+    of |<S_theta d_m, t>| >= threshold."""
+    dl = np.asarray(d_learned, np.float64)
+    dt = np.asarray(d_true, np.float64)
+    H = dl.shape[1]
+    zl = dl[..., 0] + 1j * dl[..., 1]
+    zt = dt[..., 0] + 1j * dt[..., 1]
+    zl[:, 0] = zl[:, 0].real
+    zt[:, 0] = zt[:, 0].real
+    w = np.ones(H)
+    w[1:] = 2.0
+    G = np.einsum("mkj,tkj->mtk", np.conj(zl), zt)
+    th = 2 * np.pi * np.arange(R * refine) / (R * refine)
+    ph = np.exp(1j * np.outer(th, np.arange(H)))
+    s = np.einsum("ak,mtk->mta", ph * w, G).real
+    return float(np.mean(np.abs(s).max(axis=(0, 2)) >= threshold))
+
+
 def rank_inputs(rank: int, P: int):
     """Rank r codes its own patches: chunks [r*n, (r+1)*n) of the seeded
     generator, with the shared dictionary."""
