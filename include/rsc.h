@@ -144,6 +144,53 @@ int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
                     float *new_coef, int32_t *n_used, void *stream);
 
 /*
+ * Steerable basis and projection (Sec. II-D; steps 1-2 of the proposed
+ * algorithm, Sec. II-E).  rsc_basis_create builds on the host, in FP64, the
+ * basis of circular N x N patches (pixels with distance <= N/2 from the
+ * centre): J Gaussian radial rings (centres j * ring_spacing, j = 1..J,
+ * width ring_width; <= 0 selects the defaults (N-1)/(2J) and 1 pixel) times
+ * the harmonics e^{i k phi}, |k| <= kmax, orthonormalised within each k, and
+ * its analysis operator (pseudo-inverse of the synthesis matrix, cutoff
+ * 1e-10 relative), then uploads it to the current device.  Pixel (row, col)
+ * of a window lies at x = col - (N-1)/2, y = (N-1)/2 - row.
+ *   Limits: N <= 64, kmax <= 16, (kmax+1)*J <= 512 (RSC_ERR_UNSUPPORTED);
+ *   rings that are linearly dependent on the grid give RSC_ERR_INVALID.
+ */
+typedef struct rsc_basis rsc_basis; /* opaque, device-resident, immutable */
+int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, double ring_spacing,
+                     rsc_basis **out);
+int rsc_basis_destroy(rsc_basis *basis);
+/* Masked pixels per window and packed coefficient count J (2 kmax + 1). */
+int rsc_basis_info(const rsc_basis *basis, int32_t *npix, int32_t *n);
+
+/*
+ * rsc_project -- coefficients x_hat = Phi^+ x of every stride-1 N x N window
+ * of one image (device, h x w floats, row-major), written to `coef` (device,
+ * (h-N+1)(w-N+1) x (kmax+1) x J x 2 floats, windows in row-major order of
+ * their top-left corner; the layout rsc_encode takes).  Images smaller than
+ * N give no windows.  Synchronises `stream` before returning.
+ */
+int rsc_project(const rsc_basis *basis, const float *image, int32_t h, int32_t w, float *coef,
+                void *stream);
+
+/*
+ * rsc_encode_images -- rotational OMP of every stride-1 window of a list of
+ * images of different sizes: one projection launch over all images (a prefix
+ * sum of the window counts maps each thread to its image) into scratch
+ * memory, then rsc_encode of all windows at once.
+ *   images : HOST array of n_images DEVICE pointers (h[i] x w[i] floats);
+ *   h, w   : HOST arrays; images smaller than the basis give no windows.
+ *   basis  : must have the dictionary's J and kmax.
+ *   outputs: as rsc_encode, for all windows concatenated image by image,
+ *            row-major within an image.
+ * Synchronises `stream` before returning.
+ */
+int rsc_encode_images(const rsc_dict *dict, const rsc_basis *basis, const float *const *images,
+                      const int32_t *h, const int32_t *w, int32_t n_images, int32_t K,
+                      int32_t prec, int32_t *atom, int32_t *angle_idx, float *angle,
+                      double *coef, float *resid_norm2, void *stream);
+
+/*
  * rsc_encode_host -- rsc_encode on HOST buffers (same shapes and meaning as
  * above, all pointers host memory; pinned memory gives the fastest copies).
  * Copies the patches to the device in chunks, codes them and copies the

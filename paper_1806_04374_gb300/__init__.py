@@ -31,7 +31,8 @@ EXPORTS = (
     "rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode", "rsc_encode_host",
     "rsc_dict_check", "rsc_dict_fallback_count", "rsc_dict_set_timing", "rsc_dict_timing",
     "rsc_status_string", "rsc_last_cuda_error", "rsc_version", "rsc_encode_noalloc",
-    "rsc_ksvd_update",
+    "rsc_ksvd_update", "rsc_basis_create", "rsc_basis_destroy", "rsc_basis_info", "rsc_project",
+    "rsc_encode_images",
 )
 
 
@@ -68,6 +69,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_encode_host.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.rsc_encode_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_ksvd_update.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp]
+    lib.rsc_basis_create.argtypes = [i32, i32, i32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(vp)]
+    lib.rsc_basis_destroy.argtypes = [vp]
+    lib.rsc_basis_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.rsc_project.argtypes = [vp, vp, i32, i32, vp, vp]
+    lib.rsc_encode_images.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32), i32, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_dict_check.argtypes = [vp, vp]
     lib.rsc_dict_fallback_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.rsc_dict_set_timing.argtypes = [vp, ctypes.c_int]
@@ -80,7 +88,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("rsc_dict_create", "rsc_dict_destroy", "rsc_dict_dims", "rsc_encode",
                  "rsc_encode_host", "rsc_dict_check", "rsc_dict_fallback_count",
                  "rsc_dict_set_timing", "rsc_dict_timing", "rsc_version", "rsc_encode_noalloc",
-                 "rsc_ksvd_update"):
+                 "rsc_ksvd_update", "rsc_basis_create", "rsc_basis_destroy", "rsc_basis_info",
+                 "rsc_project", "rsc_encode_images"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -273,3 +282,76 @@ def ksvd_update(dic: Dictionary, x, codes: dict, stream=None):
     if st != RSC_OK:
         raise RscError(st, "rsc_ksvd_update")
     return new, used
+
+
+class Basis:
+    """Owns an rsc_basis handle (steerable basis + analysis operator)."""
+
+    def __init__(self, N: int, J: int, kmax: int, ring_width: float = 0.0,
+                 ring_spacing: float = 0.0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        st = lib.rsc_basis_create(N, J, kmax, ring_width, ring_spacing, ctypes.byref(h))
+        if st != RSC_OK:
+            raise RscError(st, "rsc_basis_create")
+        self.handle = h.value
+        self.N, self.J, self.kmax, self.H = N, J, kmax, kmax + 1
+        npix, n = ctypes.c_int32(), ctypes.c_int32()
+        lib.rsc_basis_info(ctypes.c_void_p(self.handle), ctypes.byref(npix), ctypes.byref(n))
+        self.npix, self.n = npix.value, n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().rsc_basis_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def project(basis: Basis, image, stream=None):
+    """rsc_project: coefficients of every stride-1 window of a CUDA float32
+    image [h, w] -> [(h-N+1)(w-N+1), kmax+1, J, 2]."""
+    import torch
+    image = image.contiguous()
+    h, w = image.shape
+    P = max(h - basis.N + 1, 0) * max(w - basis.N + 1, 0)
+    out = torch.empty((P, basis.H, basis.J, 2), dtype=torch.float32, device=image.device)
+    st = load_library().rsc_project(ctypes.c_void_p(basis.handle), ctypes.c_void_p(image.data_ptr()),
+                                    h, w, ctypes.c_void_p(out.data_ptr() if P else None),
+                                    ctypes.c_void_p(_stream_handle(stream)))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_project")
+    return out
+
+
+def encode_images(dic: Dictionary, basis: Basis, images, K: int, precision: str = "fp32",
+                  stream=None):
+    """rsc_encode_images on a list of CUDA float32 images [h_i, w_i]."""
+    import torch
+    images = [im.contiguous() for im in images]
+    N = basis.N
+    P = sum(max(im.shape[0] - N + 1, 0) * max(im.shape[1] - N + 1, 0) for im in images)
+    dev = images[0].device if images else torch.device("cuda")
+    out = {
+        "atom": torch.empty((P, K), dtype=torch.int32, device=dev),
+        "angle_idx": torch.empty((P, K), dtype=torch.int32, device=dev),
+        "angle": torch.empty((P, K), dtype=torch.float32, device=dev),
+        "coef": torch.empty((P, K), dtype=torch.float64, device=dev),
+        "resid_norm2": torch.empty((P,), dtype=torch.float32, device=dev),
+    }
+    n = len(images)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[im.data_ptr() for im in images])
+    hs = (ctypes.c_int32 * max(n, 1))(*[im.shape[0] for im in images])
+    ws = (ctypes.c_int32 * max(n, 1))(*[im.shape[1] for im in images])
+    st = load_library().rsc_encode_images(
+        ctypes.c_void_p(dic.handle), ctypes.c_void_p(basis.handle), ptrs, hs, ws, n, K,
+        PRECISIONS[precision], *[ctypes.c_void_p(out[k].data_ptr() if P else None)
+                                 for k in ("atom", "angle_idx", "angle", "coef", "resid_norm2")],
+        ctypes.c_void_p(_stream_handle(stream)))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_encode_images")
+    return out

@@ -1,0 +1,407 @@
+// basis.cu -- the discrete steerable basis and the pixel -> coefficient
+// projection (Sec. II-D and steps 1-2 of the proposed algorithm, Sec. II-E),
+// and coding of whole images.
+//
+// rsc_basis_create builds, on the host in FP64: the circular N x N patch
+// (pixels with rho <= N/2), Gaussian-ring radial profiles b_j(rho) times the
+// circular harmonics e^{i k phi} (the synthetic workloads' radial profiles in
+// place of the paper's annulus indicators of Eq. (basis-cont)), made
+// orthonormal within each harmonic (Loewdin, G^{-1/2} from a Jacobi
+// eigendecomposition of the real ring Gram matrix), and the analysis
+// operator: the pseudo-inverse of the real synthesis matrix (one-sided
+// Jacobi SVD, cutoff 1e-10 of the largest singular value), which is the
+// paper's (Phi^* Phi)^{-1} Phi^* whenever Phi^* Phi is invertible.
+// Readings: pixel (row, col) at x = col - c, y = c - row, phi = atan2(y, x);
+// e^{i k phi} = 0 at the centre pixel for k != 0; ring centres
+// r_j = j * spacing (default (N-1)/(2J)), ring width sigma (default 1 px).
+//
+// project_kernel gathers every stride-1 window of a list of images of
+// different sizes (one launch, a prefix sum of patch counts maps a thread to
+// its image) and multiplies it by the analysis operator, writing half
+// spectra in the layout rsc_encode takes.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rsc_internal.h"
+
+struct rsc_basis {
+  int N, J, kmax, H, npix, n, nout, nout_pad;
+  int device;
+  int2 *offs;    // device [npix] (dy, dx) of each masked pixel, row-major
+  float *Po;     // device [npix][nout_pad]: half-spectrum outputs per pixel
+};
+
+namespace {
+
+// Cyclic Jacobi eigendecomposition of a symmetric n x n matrix (row-major,
+// overwritten); V receives the eigenvectors as columns, w the eigenvalues.
+void jacobi_eig(std::vector<double> &A, int n, std::vector<double> &V, std::vector<double> &w) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += A[i * n + j] * A[i * n + j];
+        if (i != j) off += A[i * n + j] * A[i * n + j];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // A <- A J (columns p, q)
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // A <- J^T A (rows p, q)
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+}
+
+// Pseudo-inverse of the m x n matrix X (column-major: X[c * m + r]) by
+// one-sided (Hestenes) Jacobi SVD; returns P (n x m, row-major).
+std::vector<double> pinv(std::vector<double> X, int m, int n, double rcond) {
+  std::vector<double> V((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;  // column-major too
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    double worst = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double al = 0.0, be = 0.0, ga = 0.0;
+        const double *xp = &X[(size_t)p * m], *xq = &X[(size_t)q * m];
+        for (int r = 0; r < m; ++r) {
+          al += xp[r] * xp[r];
+          be += xq[r] * xq[r];
+          ga += xp[r] * xq[r];
+        }
+        if (al == 0.0 || be == 0.0) continue;
+        const double rel = fabs(ga) / sqrt(al * be);
+        worst = std::max(worst, rel);
+        if (rel < 1e-15) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        double *wp = &X[(size_t)p * m], *wq = &X[(size_t)q * m];
+        for (int r = 0; r < m; ++r) {
+          const double a = wp[r], b = wq[r];
+          wp[r] = c * a - s * b;
+          wq[r] = s * a + c * b;
+        }
+        double *vp = &V[(size_t)p * n], *vq = &V[(size_t)q * n];
+        for (int r = 0; r < n; ++r) {
+          const double a = vp[r], b = vq[r];
+          vp[r] = c * a - s * b;
+          vq[r] = s * a + c * b;
+        }
+      }
+    if (worst < 1e-15) break;
+  }
+  // X V = U S: column i of X is sigma_i u_i
+  std::vector<double> sig(n);
+  double smax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double s2 = 0.0;
+    for (int r = 0; r < m; ++r) s2 += X[(size_t)i * m + r] * X[(size_t)i * m + r];
+    sig[i] = sqrt(s2);
+    smax = std::max(smax, sig[i]);
+  }
+  std::vector<double> P((size_t)n * m, 0.0);
+  for (int i = 0; i < n; ++i) {
+    if (!(sig[i] > rcond * smax)) continue;
+    const double inv2 = 1.0 / (sig[i] * sig[i]);
+    for (int a = 0; a < n; ++a) {
+      const double va = V[(size_t)i * n + a] * inv2;
+      if (va == 0.0) continue;
+      for (int r = 0; r < m; ++r) P[(size_t)a * m + r] += va * X[(size_t)i * m + r];
+    }
+  }
+  return P;
+}
+
+struct ImageItem {
+  const float *img;
+  int h, w;
+  int64_t first;  // index of the image's first patch
+};
+
+__global__ void project_kernel(const ImageItem *items, int n_items, int64_t P_total, int N,
+                               int npix, const int2 *offs, const float *Po, int nout,
+                               int nout_pad, float *coef) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P_total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_items - 1;  // last item with first <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].first <= g) lo = mid; else hi = mid - 1;
+    }
+    const ImageItem it = items[lo];
+    const int64_t local = g - it.first;
+    const int nw = it.w - N + 1;
+    const int r0 = (int)(local / nw), c0 = (int)(local - (int64_t)r0 * nw);
+    const float *base = it.img + (int64_t)r0 * it.w + c0;
+    float *out = coef + g * nout;
+    for (int oc = 0; oc < nout; oc += 32) {
+      float acc[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) acc[u] = 0.0f;
+      for (int p = 0; p < npix; ++p) {
+        const int2 o = __ldg(offs + p);
+        const float v = __ldg(base + (int64_t)o.x * it.w + o.y);
+        const float4 *row = reinterpret_cast<const float4 *>(Po + (size_t)p * nout_pad + oc);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float4 q = __ldg(row + u);
+          acc[4 * u] = fmaf(q.x, v, acc[4 * u]);
+          acc[4 * u + 1] = fmaf(q.y, v, acc[4 * u + 1]);
+          acc[4 * u + 2] = fmaf(q.z, v, acc[4 * u + 2]);
+          acc[4 * u + 3] = fmaf(q.w, v, acc[4 * u + 3]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 32; ++u)
+        if (oc + u < nout) out[oc + u] = acc[u];
+    }
+  }
+}
+
+int launch_project(const rsc_basis *b, const ImageItem *items_dev, int n_items, int64_t P_total,
+                   float *coef, cudaStream_t st) {
+  if (P_total == 0) return RSC_OK;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+  const int64_t blocks = (P_total + 127) / 128;
+  const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)nsm * 16);
+  project_kernel<<<grid, 128, 0, st>>>(items_dev, n_items, P_total, b->N, b->npix, b->offs, b->Po,
+                                       b->nout, b->nout_pad, coef);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, double ring_spacing,
+                     rsc_basis **out) {
+  if (!out) return RSC_ERR_INVALID;
+  *out = nullptr;
+  if (N < 1 || J < 1 || kmax < 0) return RSC_ERR_INVALID;
+  if (N > 64 || kmax > kMaxKmax || (int64_t)(kmax + 1) * J > kMaxEntries) return RSC_ERR_UNSUPPORTED;
+  if (!(ring_width > 0.0)) ring_width = 1.0;
+  if (!(ring_spacing > 0.0)) ring_spacing = (N - 1) / (2.0 * J);
+  const int H = kmax + 1;
+  const double c = (N - 1) / 2.0;
+  std::vector<int2> offs;
+  std::vector<double> rho, phi;
+  for (int r = 0; r < N; ++r)
+    for (int col = 0; col < N; ++col) {
+      const double x = col - c, y = c - r;
+      const double rr = sqrt(x * x + y * y);
+      if (rr <= N / 2.0) {
+        offs.push_back(make_int2(r, col));
+        rho.push_back(rr);
+        phi.push_back(atan2(y, x));
+      }
+    }
+  const int npix = (int)offs.size();
+  const int n = J + 2 * kmax * J;
+  // orthonormalised radial profiles q_jk(pixel), one set for k = 0 and one
+  // for k != 0 (the centre pixel is dropped there)
+  std::vector<double> prof((size_t)npix * J);
+  for (int p = 0; p < npix; ++p)
+    for (int j = 0; j < J; ++j) {
+      const double d = (rho[p] - ring_spacing * (j + 1)) / ring_width;
+      prof[(size_t)p * J + j] = exp(-0.5 * d * d);
+    }
+  std::vector<double> q[2];
+  for (int kk = 0; kk < 2; ++kk) {
+    std::vector<double> G((size_t)J * J, 0.0), V, w;
+    for (int p = 0; p < npix; ++p) {
+      if (kk == 1 && rho[p] == 0.0) continue;
+      for (int a = 0; a < J; ++a)
+        for (int bb = 0; bb < J; ++bb) G[a * J + bb] += prof[(size_t)p * J + a] * prof[(size_t)p * J + bb];
+    }
+    jacobi_eig(G, J, V, w);
+    for (int i = 0; i < J; ++i)
+      if (!(w[i] > 0.0)) return RSC_ERR_INVALID;  // rings not independent on this grid
+    std::vector<double> W((size_t)J * J, 0.0);  // G^{-1/2} = V diag(w^-1/2) V^T
+    for (int a = 0; a < J; ++a)
+      for (int bb = 0; bb < J; ++bb) {
+        double s = 0.0;
+        for (int i = 0; i < J; ++i) s += V[a * J + i] * V[bb * J + i] / sqrt(w[i]);
+        W[a * J + bb] = s;
+      }
+    q[kk].assign((size_t)npix * J, 0.0);
+    for (int p = 0; p < npix; ++p) {
+      if (kk == 1 && rho[p] == 0.0) continue;
+      for (int j = 0; j < J; ++j) {
+        double s = 0.0;
+        for (int a = 0; a < J; ++a) s += prof[(size_t)p * J + a] * W[a * J + j];
+        q[kk][(size_t)p * J + j] = s;
+      }
+    }
+  }
+  // real synthesis matrix X (npix x n, column-major), packed coefficient order
+  std::vector<double> X((size_t)n * npix, 0.0);
+  for (int j = 0; j < J; ++j)
+    for (int p = 0; p < npix; ++p) X[(size_t)j * npix + p] = q[0][(size_t)p * J + j];
+  for (int k = 1; k <= kmax; ++k)
+    for (int j = 0; j < J; ++j) {
+      const int col = J + 2 * ((k - 1) * J + j);
+      for (int p = 0; p < npix; ++p) {
+        const double qq = q[1][(size_t)p * J + j];
+        X[(size_t)col * npix + p] = M_SQRT2 * qq * cos(k * phi[p]);
+        X[(size_t)(col + 1) * npix + p] = -M_SQRT2 * qq * sin(k * phi[p]);
+      }
+    }
+  const std::vector<double> Pr = pinv(X, npix, n, 1e-10);  // n x npix
+  // outputs: half spectrum [k][j][re, im]; packed k >= 1 slots carry sqrt(2)
+  const int nout = 2 * H * J;
+  const int nout_pad = (nout + 31) / 32 * 32;
+  std::vector<float> Po((size_t)npix * nout_pad, 0.0f);
+  for (int p = 0; p < npix; ++p) {
+    for (int j = 0; j < J; ++j) Po[(size_t)p * nout_pad + 2 * j] = (float)Pr[(size_t)j * npix + p];
+    for (int k = 1; k <= kmax; ++k)
+      for (int j = 0; j < J; ++j) {
+        const int row = J + 2 * ((k - 1) * J + j);
+        const int o = 2 * (k * J + j);
+        Po[(size_t)p * nout_pad + o] = (float)(Pr[(size_t)row * npix + p] * M_SQRT1_2);
+        Po[(size_t)p * nout_pad + o + 1] = (float)(Pr[(size_t)(row + 1) * npix + p] * M_SQRT1_2);
+      }
+  }
+  rsc_basis *b = new rsc_basis();
+  memset(b, 0, sizeof *b);
+  b->N = N;
+  b->J = J;
+  b->kmax = kmax;
+  b->H = H;
+  b->npix = npix;
+  b->n = n;
+  b->nout = nout;
+  b->nout_pad = nout_pad;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaMalloc(&b->offs, offs.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMalloc(&b->Po, Po.size() * sizeof(float));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->offs, offs.data(), offs.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->Po, Po.data(), Po.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(b->offs);
+    cudaFree(b->Po);
+    delete b;
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return RSC_ERR_OOM;
+    }
+    return rsc_cuda_fail(e);
+  }
+  *out = b;
+  return RSC_OK;
+}
+
+int rsc_basis_destroy(rsc_basis *b) {
+  if (!b) return RSC_OK;
+  cudaFree(b->offs);
+  cudaFree(b->Po);
+  delete b;
+  return RSC_OK;
+}
+
+int rsc_basis_info(const rsc_basis *b, int32_t *npix, int32_t *n) {
+  if (!b) return RSC_ERR_INVALID;
+  if (npix) *npix = b->npix;
+  if (n) *n = b->n;
+  return RSC_OK;
+}
+
+int rsc_project(const rsc_basis *b, const float *image, int32_t h, int32_t w, float *coef,
+                void *stream) {
+  if (!b || h < 0 || w < 0) return RSC_ERR_INVALID;
+  if (h < b->N || w < b->N) return RSC_OK;  // no complete window
+  if (!image || !coef) return RSC_ERR_INVALID;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  if (dev != b->device) return RSC_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ImageItem it{image, h, w, 0};
+  ImageItem *d_it = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&d_it), sizeof(ImageItem), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_it, &it, sizeof it, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  const int64_t P = (int64_t)(h - b->N + 1) * (w - b->N + 1);
+  int rc = launch_project(b, d_it, 1, P, coef, st);
+  cudaFreeAsync(d_it, st);
+  // the host copy of `it` must outlive the async copy
+  e = cudaStreamSynchronize(st);
+  if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
+  return rc;
+}
+
+int rsc_encode_images(const rsc_dict *dict, const rsc_basis *b, const float *const *images,
+                      const int32_t *h, const int32_t *w, int32_t n_images, int32_t K,
+                      int32_t prec, int32_t *atom, int32_t *angle_idx, float *angle,
+                      double *coef, float *resid_norm2, void *stream) {
+  if (!dict || !b || n_images < 0 || (n_images > 0 && (!images || !h || !w)))
+    return RSC_ERR_INVALID;
+  if (b->J != dict->J || b->kmax != dict->kmax) return RSC_ERR_INVALID;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  if (dev != b->device || dev != dict->device) return RSC_ERR_INVALID;
+  std::vector<ImageItem> items;
+  int64_t P = 0;
+  for (int i = 0; i < n_images; ++i) {
+    if (h[i] < 0 || w[i] < 0) return RSC_ERR_INVALID;
+    if (h[i] < b->N || w[i] < b->N) continue;
+    if (!images[i]) return RSC_ERR_INVALID;
+    items.push_back(ImageItem{images[i], h[i], w[i], P});
+    P += (int64_t)(h[i] - b->N + 1) * (w[i] - b->N + 1);
+  }
+  if (P == 0) return RSC_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bI = (items.size() * sizeof(ImageItem) + 255) & ~(size_t)255;
+  unsigned char *scratch = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bI + (size_t)P * b->nout * 4, st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return RSC_ERR_OOM;
+  }
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  ImageItem *d_items = reinterpret_cast<ImageItem *>(scratch);
+  float *xc = reinterpret_cast<float *>(scratch + bI);
+  int rc = RSC_OK;
+  e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(ImageItem),
+                      cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+  if (rc == RSC_OK) rc = launch_project(b, d_items, (int)items.size(), P, xc, st);
+  if (rc == RSC_OK)
+    rc = rsc_encode(dict, xc, P, K, prec, atom, angle_idx, angle, coef, resid_norm2, stream);
+  cudaFreeAsync(scratch, st);
+  // the host work list must outlive its async copy
+  e = cudaStreamSynchronize(st);
+  if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+"""GPU projection (rsc_project) and image coding (rsc_encode_images) against
+the FP64 oracle basis/projection (oracle/basis.py) and oracle OMP."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import basis as obasis
+from paper_1806_04374_gb300 import synth
+
+from parity import check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsc(cuda_ok):
+    import paper_1806_04374_gb300 as rsc
+    rsc.load_library()
+    return rsc
+
+
+def image(h, w, seed):
+    """Seeded test image: Gaussian blobs of random sign and width on noise."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:h, 0:w]
+    img = 0.05 * rng.standard_normal((h, w))
+    for _ in range(max(1, h * w // 60)):
+        cy, cx = rng.uniform(0, h), rng.uniform(0, w)
+        s = rng.uniform(1.0, 3.0)
+        img += rng.standard_normal() * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * s * s))
+    return img.astype(np.float32)
+
+
+@pytest.mark.parametrize("shape", [(11, 6, 8), (21, 10, 12)])
+def test_project_matches_oracle(rsc, shape):
+    import torch
+    N, J, kmax = shape
+    img = image(N + 17, N + 12, 5)
+    b = rsc.Basis(N, J, kmax)
+    assert b.npix == obasis.grid(N)[0].size
+    got = rsc.project(b, torch.from_numpy(img).cuda()).cpu().numpy()
+    ref = obasis.project(img, N, J, kmax)
+    assert got.shape == ref.shape
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print(shape, "max rel err", err)
+    assert err < 2e-5
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_encode_uneven_images(rsc, precision):
+    """Images of different sizes (one smaller than a window) coded in one
+    call; windows are compared with the oracle run on the oracle's own
+    projection.  The two projections differ by FP32 rounding (~1e-6
+    relative), so selections are pinned at a 1e-4 margin and weights
+    compared to 1e-4."""
+    import torch
+    N, J, kmax, M, R, K = 11, 6, 8, 12, 32, 3
+    shapes = [(23, 31), (11, 11), (8, 40), (30, 18)]
+    imgs = [image(h, w, 10 + i) for i, (h, w) in enumerate(shapes)]
+    d = synth.make_dictionary(M, J, kmax, 77)
+    b = rsc.Basis(N, J, kmax)
+    dic = rsc.Dictionary(torch.from_numpy(d).cuda(), R)
+    out = rsc.encode_images(dic, b, [torch.from_numpy(im).cuda() for im in imgs], K, precision)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    x = np.concatenate([obasis.project(im, N, J, kmax) for im in imgs if min(im.shape) >= N])
+    assert g["atom"].shape[0] == x.shape[0] == 13 * 21 + 1 + 0 + 20 * 8
+    s = check(x.astype(np.float32), d, R, K, g, coef_tol=1e-4, margin=1e-4)
+    print(precision, s)
+    dic.close()
+    b.close()
