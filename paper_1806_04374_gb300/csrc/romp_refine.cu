@@ -24,12 +24,6 @@ namespace {
 
 constexpr int kRowBytes = kTcKst * 2;  // packed bf16 residual row
 
-// Sink writing packed chunks into a row-major bf16 row in global memory.
-struct GlobalRow {
-  uint4 *row;
-  __device__ void operator()(int cq, uint4 v) const { row[cq] = v; }
-};
-
 // State arrays (each of length P, element i of patch p at [field * P + p]).
 template <int KK>
 struct StateIdx {
@@ -112,20 +106,100 @@ __device__ void write_outputs(const RefineArgs &a, int64_t p, const Ls<KK> &S, i
   if (a.resid_norm2) a.resid_norm2[p] = rnorm * rnorm;
 }
 
-// The steering-factor table [4][H][R] in shared memory.
-__device__ __forceinline__ TwS load_tw(const RefineArgs &a) {
+// Shared memory of the init/refine kernels: the steering-factor table
+// [4][H][R], then the packed-slot table qtab[q] = (e << 8) | (k << 1) | c
+// (slot q holds Re (c = 0) or Im (c = 1) of entry e = k*J + j).
+__device__ __forceinline__ TwS load_tw(const RefineArgs &a, const int *&qtab) {
   extern __shared__ __align__(16) float tws[];
   const int n = 4 * a.H * a.R;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = a.tw[i];
+  int *qt = reinterpret_cast<int *>(tws + ((n + 3) & ~3));
+  for (int q = threadIdx.x; q < a.n; q += blockDim.x) {
+    int e, k, c;
+    if (q < a.J) {
+      e = q;
+      k = 0;
+      c = 0;
+    } else {
+      const int qq = q - a.J;
+      e = a.J + (qq >> 1);
+      k = e / a.J;
+      c = qq & 1;
+    }
+    qt[q] = (e << 8) | (k << 1) | c;
+  }
   __syncthreads();
+  qtab = qt;
   return TwS{tws, a.H, a.R};
+}
+
+// Packed residual x - sum_i a_i S_{r_i} d_{m_i} of this thread's patch (FP32)
+// written as bf16 (kTcKst slots, zero-padded) to `row` if not null, slot by
+// slot in packed order; the Im slot of an entry reuses the value computed
+// with its Re slot.  Returns ||r||^2.
+template <int KK>
+__device__ __forceinline__ float residual_q(uint4 *row, const float *__restrict__ xp,
+                                            const float *__restrict__ d, int HJ, int n, int t,
+                                            const Ls<KK> &S, const TwS &tw, const int *qtab) {
+  float n2 = 0.0f, pend = 0.0f;
+#pragma unroll 1
+  for (int cq = 0; cq < kTcKst / 8; ++cq) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = cq * 8 + u;
+      float val = 0.0f;
+      if (q < n) {
+        const int code = qtab[q];
+        const int e = code >> 8, k = (code >> 1) & 127;
+        if (code & 1) {
+          val = pend;
+        } else {
+          const float2 xv = __ldg(reinterpret_cast<const float2 *>(xp) + e);
+          float re = xv.x, im = k ? xv.y : 0.0f;
+#pragma unroll
+          for (int i = 0; i < KK; ++i) {
+            if (i < t) {
+              const float2 dv =
+                  __ldg(reinterpret_cast<const float2 *>(d) + (size_t)S.m[i] * HJ + e);
+              const float dim = k ? dv.y : 0.0f;
+              const float c = tw.cos32(k, S.r[i]), sn = tw.sin32(k, S.r[i]);
+              re = fmaf(-S.ahi[i], fmaf(c, dv.x, sn * dim), re);
+              im = fmaf(-S.ahi[i], fmaf(c, dim, -sn * dv.x), im);
+            }
+          }
+          if (k) {
+            re *= 1.41421356237309515f;
+            pend = im * 1.41421356237309515f;
+          }
+          val = re;
+        }
+        n2 = fmaf(val, val, n2);
+      }
+      v[u] = val;
+    }
+    if (row) {
+      uint4 pk;
+      __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]);
+      __nv_bfloat162 b1 = __floats2bfloat162_rn(v[2], v[3]);
+      __nv_bfloat162 b2 = __floats2bfloat162_rn(v[4], v[5]);
+      __nv_bfloat162 b3 = __floats2bfloat162_rn(v[6], v[7]);
+      pk.x = *reinterpret_cast<uint32_t *>(&b0);
+      pk.y = *reinterpret_cast<uint32_t *>(&b1);
+      pk.z = *reinterpret_cast<uint32_t *>(&b2);
+      pk.w = *reinterpret_cast<uint32_t *>(&b3);
+      row[cq] = pk;
+    }
+  }
+  return n2;
 }
 
 template <int KK>
 __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
   using I = StateIdx<KK>;
   const int H = a.H, J = a.J, HJ = H * J;
-  const TwS tw = load_tw(a);
+  const int *qtab;
+  const TwS tw = load_tw(a, qtab);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
        p += (int64_t)gridDim.x * blockDim.x) {
     const float *xp = a.x + p * (int64_t)(2 * HJ);
@@ -138,8 +212,8 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
     }
     const float xnorm = sqrtf(fmaxf(acc.hi + acc.lo, 0.0f));
     Ls<KK> S;
-    GlobalRow sink{reinterpret_cast<uint4 *>(a.A + p * kRowBytes)};
-    const float rn = sqrtf(write_residual<KK>(sink, xp, a.d, J, HJ, a.n, 0, S, tw));
+    const float rn = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes), xp, a.d,
+                                          HJ, a.n, 0, S, tw, qtab));
     a.sI[I::iT * a.P + p] = 0;
     a.sF[I::fX * a.P + p] = xnorm;
     a.sF[I::fR * a.P + p] = rn;
@@ -151,7 +225,8 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
 template <int KK>
 __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
   const int H = a.H, J = a.J, R = a.R, M = a.M, HJ = H * J;
-  const TwS tw = load_tw(a);
+  const int *qtab;
+  const TwS tw = load_tw(a, qtab);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
        p += (int64_t)gridDim.x * blockDim.x) {
     if (a.status[p] <= 0) continue;
@@ -173,10 +248,12 @@ __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
     const float stop_level = 1e-10f * xnorm;
     const float s1 = tv[0];
     // bf16 error of a score: 2^-8 (both operands rounded) + 2^-18 + 112 * 2^-21
-    // (accumulation, at 4x unit roundoff), times 1.25, plus the residual's error
+    // (accumulation, at 4x unit roundoff), times 1.25, plus the residual's
+    // error, plus 2^-16 s1 for the low mantissa bits the scoring kernel
+    // replaces by a column index
     const float E =
         1.25f * (3.90625e-3f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f) * rnorm +
-        2.0f * dr;
+        2.0f * dr + 1.52587890625e-5f * fabsf(s1);
     int outcome = 0;  // 0 continue, 1 finished/stopped, 2 hand-off
     if (!(s1 + E > stop_level)) {
       outcome = 1;
@@ -261,15 +338,10 @@ __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
             if (t >= a.K) {
               outcome = 1;
               // final residual norm in FP32 (the bf16 row is not needed any more)
-              float n2 = 0.0f;
-              struct NullSink {
-                __device__ void operator()(int, uint4) const {}
-              };
-              n2 = write_residual<KK>(NullSink{}, xp, a.d, J, HJ, a.n, t, S, tw);
-              rnorm = sqrtf(n2);
+              rnorm = sqrtf(residual_q<KK>(nullptr, xp, a.d, HJ, a.n, t, S, tw, qtab));
             } else {
-              GlobalRow sink{reinterpret_cast<uint4 *>(a.A + p * kRowBytes)};
-              rnorm = sqrtf(write_residual<KK>(sink, xp, a.d, J, HJ, a.n, t, S, tw));
+              rnorm = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes), xp, a.d,
+                                           HJ, a.n, t, S, tw, qtab));
               store_state<KK>(a, p, S, t, rnorm, dr);
             }
           }
@@ -297,7 +369,7 @@ int launch_refine_t(const RefineArgs &a, bool init, cudaStream_t stream) {
   const int64_t blocks = (a.P + 127) / 128;
   const int64_t cap = (int64_t)nsm * 32;
   const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
-  const size_t shm = (size_t)4 * a.H * a.R * 4;
+  const size_t shm = (size_t)((4 * a.H * a.R + 3) & ~3) * 4 + (size_t)kTcMaxN * 4;
   if (init)
     romp_init_kernel<KK><<<grid, 128, shm, stream>>>(a);
   else

@@ -216,31 +216,30 @@ __global__ void __launch_bounds__(kSThreads, 1)
           tc::tmem_ld32(taddr + piece * 32, v);
           tc::tmem_wait_ld();
           if (act) {
+            // keys: |score| with the low 5 mantissa bits replaced by the
+            // column within the block; non-negative floats order like their
+            // bits, so one max gives the block maximum and its column (the
+            // truncation is < 2^-18 relative and covered by the refine's
+            // error bound)
             const int base = c * kTcBN + piece * 32;
             const int nv = nvalid - piece * 32;
-            float av[32];
-            if (nv >= 32) {
+            float key[32];
 #pragma unroll
-              for (int u = 0; u < 32; ++u) av[u] = fabsf(__uint_as_float(v[u]));
-            } else {
+            for (int u = 0; u < 32; ++u)
+              key[u] = __int_as_float((int)((v[u] & 0x7FFFFFE0u) | (uint32_t)u));
+            if (nv < 32) {
 #pragma unroll
               for (int u = 0; u < 32; ++u)
-                av[u] = (u < nv) ? fabsf(__uint_as_float(v[u])) : -INFINITY;
+                if (u >= nv) key[u] = -1.0f;
             }
-            float m1 = -INFINITY;
+            float m1 = -1.0f;
 #pragma unroll
-            for (int u = 0; u < 32; u += 2) m1 = fmax3(m1, av[u], av[u + 1]);
-            if (m1 > tv[kTop - 1]) {
-              int us = 0;
-              bool found = false;
-              float m2 = -INFINITY;
+            for (int u = 0; u < 32; u += 2) m1 = fmax3(m1, key[u], key[u + 1]);
+            if (m1 >= 0.0f && m1 > tv[kTop - 1]) {
+              const int us = __float_as_int(m1) & 31;
+              float m2 = -1.0f;
 #pragma unroll
-              for (int u = 0; u < 32; ++u) {
-                const bool is = !found && (av[u] == m1);
-                us = is ? u : us;
-                found = found || is;
-                m2 = fmaxf(m2, is ? -INFINITY : av[u]);
-              }
+              for (int u = 0; u < 32; ++u) m2 = fmaxf(m2, key[u] < m1 ? key[u] : -1.0f);
               topn_insert(tv, ti, disc, m1, base + us);
               disc = fmaxf(disc, m2);
             } else {
