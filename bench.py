@@ -89,35 +89,55 @@ def rank_inputs(rank: int, P: int):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms by a
+    reader thread; only the samples taken between start() and stop() (the
+    timed region) are summarised."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
+        import threading
+        self.lines = []
+        self.t0 = self.t1 = None
         self.proc = None
-        self.gpu = gpu_index
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
-            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        # wait (up to 5 s) for the first sample so that the region is covered
+        deadline = time.monotonic() + 5.0
+        while not self.lines and time.monotonic() < deadline and self.proc.poll() is None:
+            time.sleep(0.02)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line))
+
+    def start(self):
+        self.t0 = time.monotonic()
 
     def stop(self) -> dict | None:
+        self.t1 = time.monotonic()
         if self.proc is None:
             return None
+        time.sleep(0.15)  # the sample that closes the region
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+        self.thread.join(timeout=5)
+        inside = [ln for (t, ln) in self.lines if self.t0 <= t <= self.t1 + 0.15]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in inside:
             f = [c.strip() for c in line.split(",")]
             if len(f) < 9:
                 continue
@@ -132,7 +152,46 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window_s": round(self.t1 - self.t0, 3)}
+
+
+SCORE_SOURCES = ("romp_score.cu", "tc_ptx.cuh", "tc_common.cuh", "rsc_internal.h")
+
+
+def source_digest(names=SCORE_SOURCES) -> str:
+    """sha1 over the CUDA sources a kernel is compiled from."""
+    import hashlib
+    h = hashlib.sha1()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_1806_04374_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(P: int):
+    """DRAM bytes per launch of the scoring kernel at P patches, from the
+    committed ncu summary (dram__bytes_read.sum + dram__bytes_write.sum of one
+    capture, per patch, scaled to P: the kernel's traffic is linear in the
+    patches it reads and writes), or None when the kernel's sources changed
+    since the capture."""
+    path = os.path.join(ROOT, "profiles", "romp_score_kernel_omp_1m.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        for key in ("dram_bytes_per_patch:", "source_sha1:"):
+            if line.strip().startswith(key):
+                vals[key] = line.split(":", 1)[1].strip().strip("`")
+    if vals.get("source_sha1:") != source_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_patch:"]) * P
+    except (KeyError, ValueError):
+        return None
 
 
 def measured_peaks() -> dict:
@@ -200,9 +259,9 @@ def run_reference(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="f16", choices=["fp32", "f16"])
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the headline path")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -265,6 +324,8 @@ def main():
             torch.cuda.synchronize(dev)
             clocks = ClockSampler(dev.index if dev.index is not None else 0) if sample_clocks else None
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            if clocks:
+                clocks.start()
             evs[0].record(stream)
             for s in range(args.steps):
                 rsc.encode(dic, xd, K, precision, stream=stream, out=out)
@@ -330,11 +391,12 @@ def main():
         sm_max = (clk or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         peaks = measured_peaks()
-        if args.precision == "bf16":
+        if args.precision == "f16":
             kname, bound = "romp_score_kernel", "tensor"
+            # dense fp16 and bf16 have the same nominal rate (ratio 1)
             peak = peaks.get("bf16_tflops") or 1900.0
-            peak_note = ("dense bf16, MEASURED_PEAKS burst" if peaks.get("bf16_tflops")
-                         else "dense bf16, fallback 1.9 PFLOP/s")
+            peak_note = ("dense fp16 = measured dense bf16 (burst) x nominal ratio 1"
+                         if peaks.get("bf16_tflops") else "dense fp16, fallback 1.9 PFLOP/s")
         else:
             kname, bound = "romp_f32_kernel", "alu"
             peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -350,13 +412,13 @@ def main():
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16",
+            "dtype": "f32" if args.precision == "fp32" else "f16",
             "data": "synthetic",
             "config": {
                 "workload": f"{WORKLOAD}: P={P} patches/GPU, n=102 (J=6, kmax=8), M=64, R=64, "
                             f"K=5, 3 planted atoms + noise 0.1",
                 "path": (f"{args.precision} scoring ("
-                         + ("tcgen05 tensor cores" if args.precision == "bf16" else "CUDA cores")
+                         + ("tcgen05 tensor cores" if args.precision == "f16" else "CUDA cores")
                          + ") + double-float re-scoring + FP64 Cholesky"),
                 "l2": "inputs (432 MB) larger than L2, no flush",
                 "parallelism": f"dp{world} (patches sharded, no collective)",
@@ -371,7 +433,7 @@ def main():
                 "peak": peak,
                 "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": None,
+                "traffic": recorded_traffic(P) if args.precision == "f16" else None,
                 "flops_per_patch": fl["per_patch"],
                 "flops_convention": "(a) 2J(1+4kmax)M + (b) 2.5 R log2 R M per patch-step, x K",
                 "kernel_ms": launch_s * 1e3,
@@ -390,7 +452,7 @@ def main():
                                    "refine": main_run["kernel_ms"][2] / args.steps},
             "clocks": clk,
         }
-        if args.precision == "bf16":
+        if args.precision == "f16":
             mf = mma_flops_per_patch(wl)
             mtf = mf * P * args.steps / n_launch / launch_s / 1e12
             line["mma_executed"] = {"flops_per_patch": mf, "tflops": mtf,

@@ -49,7 +49,7 @@ extern "C" {
  * problem in FP64, so all paths return the same selections wherever the
  * top-two margin of the exact scores exceeds their error bound. */
 #define RSC_FP32 0         /* FP32 CUDA-core contraction + angle DFT */
-#define RSC_BF16_RESCORE 2 /* BF16 tcgen05 tensor-core scores, candidates re-scored */
+#define RSC_F16_RESCORE 2 /* FP16 tcgen05 tensor-core scores, candidates re-scored */
 
 typedef struct {
   int32_t M;    /* atoms, >= 1 */
@@ -65,7 +65,7 @@ typedef struct rsc_dict rsc_dict; /* opaque, device-resident, immutable */
  * proposed algorithm: atoms in steerable-basis coordinates) and precompute
  * its per-angle tables (the steering factors exp(-i k 2 pi r / R) of
  * Eq. (Sr), a transposed copy for the contraction, and, for the tensor-core
- * path, the steered dictionary S_r d_m in bf16).
+ * path, the steered dictionary S_r d_m in fp16, scaled by 256).
  *   coef   : device pointer, M x (kmax+1) x J x 2 floats, atoms of unit
  *            norm (|<d,d> - 1| <= 1e-4, else RSC_ERR_INVALID); read once,
  *            the caller keeps ownership.
@@ -102,7 +102,7 @@ int rsc_dict_dims(const rsc_dict *dict, rsc_dims *dims);
  *   x         : device, P x (kmax+1) x J x 2 floats.
  *   P         : patches, >= 0 (0 is a no-op).
  *   K         : greedy steps, 1 <= K <= 16.
- *   prec      : RSC_FP32 or RSC_BF16_RESCORE.
+ *   prec      : RSC_FP32 or RSC_F16_RESCORE.
  *   atom      : device int32 [P x K], atom index m per step, -1 if none.
  *   angle_idx : device int32 [P x K], angle index r in [0, R), -1 if none.
  *   angle     : device float [P x K] or NULL, the angle 2*pi*r/R in radians.
@@ -203,7 +203,7 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
                     float *resid_norm2);
 
 /*
- * rsc_encode_noalloc -- the RSC_BF16_RESCORE path of rsc_encode, for callers
+ * rsc_encode_noalloc -- the RSC_F16_RESCORE path of rsc_encode, for callers
  * that cannot allocate device memory while they code (a server that reserves
  * all of its memory up front and forbids allocation in steady state, code
  * that runs inside another framework's memory pool, or latency-bound callers
@@ -213,7 +213,7 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
  * stream-ordered allocator; this call uses a fixed 4 MiB device array inside
  * the library instead and calls no cudaMalloc, cudaFree or other allocating
  * routine.  The paper has no counterpart: it is a property of this library.
- *   Arguments and outputs: as rsc_encode with prec = RSC_BF16_RESCORE.
+ *   Arguments and outputs: as rsc_encode with prec = RSC_F16_RESCORE.
  *   Limits: P <= 1048576 (2^20) per call, else RSC_ERR_UNSUPPORTED; the
  *   dictionary must support the tensor-core path (packed length <= 112,
  *   K <= 8), else RSC_ERR_UNSUPPORTED.

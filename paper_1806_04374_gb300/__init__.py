@@ -23,8 +23,8 @@ RSC_ERR_TIMEOUT = -4
 RSC_ERR_UNSUPPORTED = -5
 
 RSC_FP32 = 0
-RSC_BF16_RESCORE = 2
-PRECISIONS = {"fp32": RSC_FP32, "bf16": RSC_BF16_RESCORE}
+RSC_F16_RESCORE = 2
+PRECISIONS = {"fp32": RSC_FP32, "f16": RSC_F16_RESCORE}
 
 # every symbol include/rsc.h declares
 EXPORTS = (
@@ -142,7 +142,7 @@ def rsc_encode_host(handle: int, x_ptr: int, P: int, K: int, prec: int, atom_ptr
 
 def rsc_encode_noalloc(handle: int, x_ptr: int, P: int, K: int, atom_ptr: int, angle_idx_ptr: int,
                        angle_ptr: int, coef_ptr: int, resid_norm2_ptr: int, stream: int = 0) -> int:
-    """Raw call of the allocation-free BF16 entry point; returns the status."""
+    """Raw call of the allocation-free FP16 entry point; returns the status."""
     vp = ctypes.c_void_p
     return load_library().rsc_encode_noalloc(vp(handle), vp(x_ptr), int(P), int(K), vp(atom_ptr),
                                              vp(angle_idx_ptr), vp(angle_ptr or None),

@@ -239,118 +239,126 @@ __global__ void __launch_bounds__(256)
     float rnorm = xnorm;
     __syncwarp();
 
+    // steps already certified elsewhere are taken as given (no scoring)
+    int t0 = 0;
+    if (a.resume_sI) t0 = min(a.resume_sI[(int64_t)2 * a.resume_cap * a.resume_P + p], K);
     int t = 0;
     for (int step = 0; step < K; ++step) {
-      // ---- (a)+(b)+(c): FP32 scores, per-lane top-4
-      float tv[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
-      int ti[4] = {-1, -1, -1, -1};
-      float disc = -INFINITY;
-      for (int mc = 0; mc < M; mc += kChunk) {
-        const int mend = min(kChunk, M - mc);
-        // (a) one lane per atom: G_k = sum_j conj(d[j,k]) r[j,k]
-        for (int ml = lane; ml < mend; ml += 32) {
-          const int m = mc + ml;
-          float gv[GS];
-#pragma unroll
-          for (int q = 0; q < GS; ++q) gv[q] = 0.0f;
-          const float *pre = dT + m;
-          const float *pim = dT + (size_t)HJ * M + m;
-          const float2 *r2 = reinterpret_cast<const float2 *>(s_rhi);
-          int e = 0;
-#pragma unroll
-          for (int k = 0; k <= KM; ++k) {
-            if (k < H) {
-              float gre0 = 0.f, gre1 = 0.f, gim0 = 0.f, gim1 = 0.f;
-              for (int j = 0; j < J; ++j, ++e) {
-                const float dre = pre[(size_t)e * M], dim = pim[(size_t)e * M];
-                const float2 rv = r2[e];
-                gre0 = fmaf(dre, rv.x, gre0);
-                gre1 = fmaf(dim, rv.y, gre1);
-                gim0 = fmaf(dre, rv.y, gim0);
-                gim1 = fmaf(-dim, rv.x, gim1);
-              }
-              if (k == 0) {
-                gv[0] = gre0 + gre1;
-              } else {
-                gv[2 * k - 1] = 2.0f * (gre0 + gre1);
-                gv[2 * k] = -2.0f * (gim0 + gim1);
-              }
-            }
-          }
-          float4 *g4 = reinterpret_cast<float4 *>(s_g + ml * GS);
-#pragma unroll
-          for (int q = 0; q < GS / 4; ++q)
-            g4[q] = make_float4(gv[4 * q], gv[4 * q + 1], gv[4 * q + 2], gv[4 * q + 3]);
-        }
-        __syncwarp();
-        // (b) one lane per angle, (c) per-lane top-4
-        for (int ml = 0; ml < mend; ++ml) {
-          const float4 *g4 = reinterpret_cast<const float4 *>(s_g + ml * GS);
-          float gv[GS];
-#pragma unroll
-          for (int q = 0; q < GS / 4; ++q) {
-            float4 v = g4[q];
-            gv[4 * q] = v.x;
-            gv[4 * q + 1] = v.y;
-            gv[4 * q + 2] = v.z;
-            gv[4 * q + 3] = v.w;
-          }
-#pragma unroll
-          for (int i = 0; i < RPL; ++i) {
-            float sa = gv[0], sb = 0.0f;
-#pragma unroll
-            for (int k = 0; k < KM; ++k) {
-              sa = fmaf(gv[2 * k + 1], tc[i][k], sa);
-              sb = fmaf(gv[2 * k + 2], ts[i][k], sb);
-            }
-            const int r = lane + 32 * i;
-            if (r < R) top4_insert(tv, ti, disc, fabsf(sa + sb), (mc + ml) * R + r);
-          }
-        }
-        __syncwarp();
-      }
-      const float s1 = warp_max(tv[0]);
-      const float E = err_per_norm * rnorm;
-      if (s1 + E <= stop_level) break;  // every exact score is below the stop level
-      const float thr = s1 - 2.0f * E;
-      const bool overflow = __any_sync(0xffffffffu, disc >= thr);
-
-      // ---- candidates, re-scored in double-float against the exact residual
-      int ncand = 0;
-      if (!overflow) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const bool f = (tv[q] >= thr) && (ti[q] >= 0);
-          const unsigned b = __ballot_sync(0xffffffffu, f);
-          if (f) s_cand[ncand + __popc(b & ((1u << lane) - 1u))] = ti[q];
-          ncand += __popc(b);
-        }
-      } else {
-        if (lane == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1ull);
-        ncand = M * R;
-      }
-      __syncwarp();
-      df best_v = df_make(0.0f);
       int best_c = -1;
-      for (int ci = 0; ci < ncand; ++ci) {
-        const int c = overflow ? ci : s_cand[ci];
-        const int m = c / R, r = c - m * R;
-        df s = df_make(0.0f);
-        for (int e = lane; e < HJ; e += 32) {
-          const int k = e / J;
-          Cdf A = steered_entry(a.d, HJ, k, m, r, e, tw);
-          df rr = {s_rhi[2 * e], s_rlo[2 * e]};
-          df ri = {s_rhi[2 * e + 1], s_rlo[2 * e + 1]};
-          df q = df_add(df_mul(A.re, rr), df_mul(A.im, ri));
-          s = df_add(s, k ? df_mul_f(q, 2.0f) : q);
+      if (step < t0) {
+        best_c = a.resume_sI[(int64_t)step * a.resume_P + p] * R +
+                 a.resume_sI[(int64_t)(a.resume_cap + step) * a.resume_P + p];
+      } else {
+        // ---- (a)+(b)+(c): FP32 scores, per-lane top-4
+        float tv[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        int ti[4] = {-1, -1, -1, -1};
+        float disc = -INFINITY;
+        for (int mc = 0; mc < M; mc += kChunk) {
+          const int mend = min(kChunk, M - mc);
+          // (a) one lane per atom: G_k = sum_j conj(d[j,k]) r[j,k]
+          for (int ml = lane; ml < mend; ml += 32) {
+            const int m = mc + ml;
+            float gv[GS];
+#pragma unroll
+            for (int q = 0; q < GS; ++q) gv[q] = 0.0f;
+            const float *pre = dT + m;
+            const float *pim = dT + (size_t)HJ * M + m;
+            const float2 *r2 = reinterpret_cast<const float2 *>(s_rhi);
+            int e = 0;
+#pragma unroll
+            for (int k = 0; k <= KM; ++k) {
+              if (k < H) {
+                float gre0 = 0.f, gre1 = 0.f, gim0 = 0.f, gim1 = 0.f;
+                for (int j = 0; j < J; ++j, ++e) {
+                  const float dre = pre[(size_t)e * M], dim = pim[(size_t)e * M];
+                  const float2 rv = r2[e];
+                  gre0 = fmaf(dre, rv.x, gre0);
+                  gre1 = fmaf(dim, rv.y, gre1);
+                  gim0 = fmaf(dre, rv.y, gim0);
+                  gim1 = fmaf(-dim, rv.x, gim1);
+                }
+                if (k == 0) {
+                  gv[0] = gre0 + gre1;
+                } else {
+                  gv[2 * k - 1] = 2.0f * (gre0 + gre1);
+                  gv[2 * k] = -2.0f * (gim0 + gim1);
+                }
+              }
+            }
+            float4 *g4 = reinterpret_cast<float4 *>(s_g + ml * GS);
+#pragma unroll
+            for (int q = 0; q < GS / 4; ++q)
+              g4[q] = make_float4(gv[4 * q], gv[4 * q + 1], gv[4 * q + 2], gv[4 * q + 3]);
+          }
+          __syncwarp();
+          // (b) one lane per angle, (c) per-lane top-4
+          for (int ml = 0; ml < mend; ++ml) {
+            const float4 *g4 = reinterpret_cast<const float4 *>(s_g + ml * GS);
+            float gv[GS];
+#pragma unroll
+            for (int q = 0; q < GS / 4; ++q) {
+              float4 v = g4[q];
+              gv[4 * q] = v.x;
+              gv[4 * q + 1] = v.y;
+              gv[4 * q + 2] = v.z;
+              gv[4 * q + 3] = v.w;
+            }
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) {
+              float sa = gv[0], sb = 0.0f;
+#pragma unroll
+              for (int k = 0; k < KM; ++k) {
+                sa = fmaf(gv[2 * k + 1], tc[i][k], sa);
+                sb = fmaf(gv[2 * k + 2], ts[i][k], sb);
+              }
+              const int r = lane + 32 * i;
+              if (r < R) top4_insert(tv, ti, disc, fabsf(sa + sb), (mc + ml) * R + r);
+            }
+          }
+          __syncwarp();
         }
-        s = df_warp_sum(s);
-        if (best_c < 0 || df_abs_gt(s, best_v) || (df_abs_eq(s, best_v) && c < best_c)) {
-          best_v = s;
-          best_c = c;
+        const float s1 = warp_max(tv[0]);
+        const float E = err_per_norm * rnorm;
+        if (s1 + E <= stop_level) break;  // every exact score is below the stop level
+        const float thr = s1 - 2.0f * E;
+        const bool overflow = __any_sync(0xffffffffu, disc >= thr);
+
+        // ---- candidates, re-scored in double-float against the exact residual
+        int ncand = 0;
+        if (!overflow) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool f = (tv[q] >= thr) && (ti[q] >= 0);
+            const unsigned b = __ballot_sync(0xffffffffu, f);
+            if (f) s_cand[ncand + __popc(b & ((1u << lane) - 1u))] = ti[q];
+            ncand += __popc(b);
+          }
+        } else {
+          if (lane == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1ull);
+          ncand = M * R;
         }
+        __syncwarp();
+        df best_v = df_make(0.0f);
+        for (int ci = 0; ci < ncand; ++ci) {
+          const int c = overflow ? ci : s_cand[ci];
+          const int m = c / R, r = c - m * R;
+          df s = df_make(0.0f);
+          for (int e = lane; e < HJ; e += 32) {
+            const int k = e / J;
+            Cdf A = steered_entry(a.d, HJ, k, m, r, e, tw);
+            df rr = {s_rhi[2 * e], s_rlo[2 * e]};
+            df ri = {s_rhi[2 * e + 1], s_rlo[2 * e + 1]};
+            df q = df_add(df_mul(A.re, rr), df_mul(A.im, ri));
+            s = df_add(s, k ? df_mul_f(q, 2.0f) : q);
+          }
+          s = df_warp_sum(s);
+          if (best_c < 0 || df_abs_gt(s, best_v) || (df_abs_eq(s, best_v) && c < best_c)) {
+            best_v = s;
+            best_c = c;
+          }
+        }
+        if (best_c < 0 || !(fabsf(best_v.hi) > stop_level)) break;
       }
-      if (best_c < 0 || !(fabsf(best_v.hi) > stop_level)) break;
 
       // ---- (e) new steered atom (cached), its Gram row, diagonal, right-hand side
       const int mn = best_c / R, rn = best_c - mn * R;

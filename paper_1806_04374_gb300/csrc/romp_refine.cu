@@ -1,11 +1,13 @@
-// romp_refine.cu -- per-patch steps of the BF16 path between scoring passes:
+// romp_refine.cu -- per-patch steps of the FP16 path between scoring passes:
 // candidate certification, exact re-scoring, the least-squares update and the
 // residual (steps (c)-(e) of OMP, Sec. II-C), one thread per patch.
 //
-// romp_init_kernel writes each patch's packed residual (= x) in bf16 for the
-// first scoring pass and initialises its state.  romp_refine_kernel then,
+// romp_init_kernel writes each patch's packed residual (= x) in fp16 for the
+// first scoring pass and initialises its state.  Rows are scaled by a power
+// of two chosen from a bound on their norm (rsc_internal.h), so that scores
+// come back as 2^(16 - e) times their true value.  romp_refine_kernel then,
 // after every scoring pass (romp_score.cu):
-//   * certifies the candidate list: E bounds the bf16 error of a score
+//   * certifies the candidate list: E bounds the fp16 error of a score
 //     (rounding of both operands, accumulation, and the FP32 residual's own
 //     error); every row with |score| >= s1 - 2E is in the list unless the
 //     largest value left out (disc) is >= s1 - 2E, in which case the patch is
@@ -22,7 +24,7 @@
 
 namespace {
 
-constexpr int kRowBytes = kTcKst * 2;  // packed bf16 residual row
+constexpr int kRowBytes = kTcKst * 2;  // packed fp16 residual row
 
 // State arrays (each of length P, element i of patch p at [field * P + p]).
 template <int KK>
@@ -33,23 +35,22 @@ struct StateIdx {
   // floats: ahi, alo, xnorm, rnorm, dr
   static constexpr int fHi = 0, fLo = KK, fX = 2 * KK, fR = 2 * KK + 1, fDr = 2 * KK + 2,
                        nF = 2 * KK + 3;
-  // ints: m, r, t
-  static constexpr int iM = 0, iR = KK, iT = 2 * KK, nI = 2 * KK + 1;
+  // ints: m, r, t, e (exponent of the current row's scale)
+  static constexpr int iM = 0, iR = KK, iT = 2 * KK, iE = 2 * KK + 1, nI = 2 * KK + 2;
 };
 
+// The selection state (atoms, angles, weights, norms) is loaded when a patch
+// starts; the FP64 factor only right before the Cholesky update, so that it
+// does not hold registers through the scoring code.
 template <int KK>
 __device__ __forceinline__ void load_state(const RefineArgs &a, int64_t p, Ls<KK> &S, int &t,
-                                           float &xnorm, float &rnorm, float &dr) {
+                                           int &e, float &xnorm, float &rnorm, float &dr) {
   using I = StateIdx<KK>;
   const int64_t P = a.P;
   t = a.sI[I::iT * P + p];
-#pragma unroll
-  for (int q = 0; q < I::nL; ++q) S.L[q] = a.sD[(I::dL + q) * P + p];
+  e = a.sI[I::iE * P + p];
 #pragma unroll
   for (int i = 0; i < KK; ++i) {
-    S.inv[i] = a.sD[(I::dInv + i) * P + p];
-    S.z[i] = a.sD[(I::dZ + i) * P + p];
-    S.a[i] = a.sD[(I::dA + i) * P + p];
     S.ahi[i] = a.sF[(I::fHi + i) * P + p];
     S.alo[i] = a.sF[(I::fLo + i) * P + p];
     S.m[i] = a.sI[(I::iM + i) * P + p];
@@ -61,11 +62,26 @@ __device__ __forceinline__ void load_state(const RefineArgs &a, int64_t p, Ls<KK
 }
 
 template <int KK>
+__device__ __forceinline__ void load_factor(const RefineArgs &a, int64_t p, Ls<KK> &S) {
+  using I = StateIdx<KK>;
+  const int64_t P = a.P;
+#pragma unroll
+  for (int q = 0; q < I::nL; ++q) S.L[q] = a.sD[(I::dL + q) * P + p];
+#pragma unroll
+  for (int i = 0; i < KK; ++i) {
+    S.inv[i] = a.sD[(I::dInv + i) * P + p];
+    S.z[i] = a.sD[(I::dZ + i) * P + p];
+    S.a[i] = a.sD[(I::dA + i) * P + p];
+  }
+}
+
+template <int KK>
 __device__ __forceinline__ void store_state(const RefineArgs &a, int64_t p, const Ls<KK> &S, int t,
-                                            float rnorm, float dr) {
+                                            int e, float rnorm, float dr) {
   using I = StateIdx<KK>;
   const int64_t P = a.P;
   a.sI[I::iT * P + p] = t;
+  a.sI[I::iE * P + p] = e;
 #pragma unroll
   for (int q = 0; q < I::nL; ++q) a.sD[(I::dL + q) * P + p] = S.L[q];
 #pragma unroll
@@ -134,11 +150,11 @@ __device__ __forceinline__ TwS load_tw(const RefineArgs &a, const int *&qtab) {
 }
 
 // Packed residual x - sum_i a_i S_{r_i} d_{m_i} of this thread's patch (FP32)
-// written as bf16 (kTcKst slots, zero-padded) to `row` if not null, slot by
-// slot in packed order; the Im slot of an entry reuses the value computed
-// with its Re slot.  Returns ||r||^2.
+// written times `scale` as fp16 (kTcKst slots, zero-padded) to `row` if not
+// null, slot by slot in packed order; the Im slot of an entry reuses the value
+// computed with its Re slot.  Returns ||r||^2 (unscaled).
 template <int KK>
-__device__ __forceinline__ float residual_q(uint4 *row, const float *__restrict__ xp,
+__device__ __forceinline__ float residual_q(uint4 *row, float scale, const float *__restrict__ xp,
                                             const float *__restrict__ d, int HJ, int n, int t,
                                             const Ls<KK> &S, const TwS &tw, const int *qtab) {
   float n2 = 0.0f, pend = 0.0f;
@@ -180,10 +196,10 @@ __device__ __forceinline__ float residual_q(uint4 *row, const float *__restrict_
     }
     if (row) {
       uint4 pk;
-      __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]);
-      __nv_bfloat162 b1 = __floats2bfloat162_rn(v[2], v[3]);
-      __nv_bfloat162 b2 = __floats2bfloat162_rn(v[4], v[5]);
-      __nv_bfloat162 b3 = __floats2bfloat162_rn(v[6], v[7]);
+      __half2 b0 = __floats2half2_rn(v[0] * scale, v[1] * scale);
+      __half2 b1 = __floats2half2_rn(v[2] * scale, v[3] * scale);
+      __half2 b2 = __floats2half2_rn(v[4] * scale, v[5] * scale);
+      __half2 b3 = __floats2half2_rn(v[6] * scale, v[7] * scale);
       pk.x = *reinterpret_cast<uint32_t *>(&b0);
       pk.y = *reinterpret_cast<uint32_t *>(&b1);
       pk.z = *reinterpret_cast<uint32_t *>(&b2);
@@ -212,9 +228,12 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
     }
     const float xnorm = sqrtf(fmaxf(acc.hi + acc.lo, 0.0f));
     Ls<KK> S;
-    const float rn = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes), xp, a.d,
-                                          HJ, a.n, 0, S, tw, qtab));
+    const int e = rsc_row_exponent(xnorm);
+    const float rn = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes),
+                                          ldexpf(1.0f, kRowLog2 - e), xp, a.d, HJ, a.n, 0, S, tw,
+                                          qtab));
     a.sI[I::iT * a.P + p] = 0;
+    a.sI[I::iE * a.P + p] = e;
     a.sF[I::fX * a.P + p] = xnorm;
     a.sF[I::fR * a.P + p] = rn;
     a.sF[I::fDr * a.P + p] = 2.0f * kU32 * xnorm;
@@ -223,7 +242,7 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
 }
 
 template <int KK>
-__global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
+__global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a) {
   const int H = a.H, J = a.J, R = a.R, M = a.M, HJ = H * J;
   const int *qtab;
   const TwS tw = load_tw(a, qtab);
@@ -232,9 +251,11 @@ __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
     if (a.status[p] <= 0) continue;
     const float *xp = a.x + p * (int64_t)(2 * HJ);
     Ls<KK> S;
-    int t;
+    int t, e;
     float xnorm, rnorm, dr;
-    load_state<KK>(a, p, S, t, xnorm, rnorm, dr);
+    load_state<KK>(a, p, S, t, e, xnorm, rnorm, dr);
+    // accumulator scores are 2^(16 - e) times the true scores
+    const float unscale = ldexpf(1.0f, e - 16);
     float tv[kTop];
     int ti[kTop];
 #pragma unroll
@@ -242,19 +263,26 @@ __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
       const int4 iv = *reinterpret_cast<const int4 *>(a.cand_idx + p * kTop + q);
       const float4 fv = *reinterpret_cast<const float4 *>(a.cand_val + p * kTop + q);
       ti[q] = iv.x; ti[q + 1] = iv.y; ti[q + 2] = iv.z; ti[q + 3] = iv.w;
-      tv[q] = fv.x; tv[q + 1] = fv.y; tv[q + 2] = fv.z; tv[q + 3] = fv.w;
+      tv[q] = fv.x * unscale; tv[q + 1] = fv.y * unscale;
+      tv[q + 2] = fv.z * unscale; tv[q + 3] = fv.w * unscale;
     }
-    const float disc = a.cand_disc[p];
+    const float disc = a.cand_disc[p] * unscale;
     const float stop_level = 1e-10f * xnorm;
     const float s1 = tv[0];
-    // bf16 error of a score: 2^-8 (both operands rounded) + 2^-18 + 112 * 2^-21
-    // (accumulation, at 4x unit roundoff), times 1.25, plus the residual's
-    // error, plus 2^-16 s1 for the low mantissa bits the scoring kernel
-    // replaces by a column index
-    const float E =
-        1.25f * (3.90625e-3f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f) * rnorm +
-        2.0f * dr + 1.52587890625e-5f * fabsf(s1);
+    // fp16 error of a score, times 1.25: 2^-10 ||r|| (both operands rounded,
+    // unit atoms) + 2^-18 ||r|| (second order) + 112 * 2^-21 ||r|| (the
+    // accumulation, at 4x unit roundoff) + 11 * 2^-33 ||r|| and 11 * 2^(e-33)
+    // (subnormal rounding of a dictionary entry, <= 2^-25 / kDictScale, and of
+    // a row entry, <= 2^-25 / row scale, over sqrt(112) < 11 entries); plus the
+    // FP32 residual's own error, plus 2^-16 s1 for the low mantissa bits the
+    // scoring kernel replaces by a column index
+    const float E = 1.25f * (9.765625e-4f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f +
+                             11.0f * 1.16415321826934814e-10f) *
+                        rnorm +
+                    1.25f * 11.0f * ldexpf(1.0f, e - 33) + 2.0f * dr +
+                    1.52587890625e-5f * fabsf(s1);
     int outcome = 0;  // 0 continue, 1 finished/stopped, 2 hand-off
+    bool have_factor = false;
     if (!(s1 + E > stop_level)) {
       outcome = 1;
     } else {
@@ -269,13 +297,21 @@ __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
         const float E32 = 256.0f * kU32 * (xnorm + asum);
         float fs[kTop];
         float fbest = -1.0f;
+        int nwin = 0;
+#pragma unroll
+        for (int q = 0; q < kTop; ++q) nwin += (ti[q] >= 0 && tv[q] >= thr) ? 1 : 0;
+        // a single candidate in the certified window is the winner: no screen
 #pragma unroll
         for (int q = 0; q < kTop; ++q) {
           fs[q] = -1.0f;
           if (ti[q] >= 0 && tv[q] >= thr) {
-            const int m = ti[q] % M, r = ti[q] / M;
-            fs[q] = fabsf(score32<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H, R, m, r, t,
-                                      S, tw));
+            if (nwin > 1) {
+              const int m = ti[q] % M, r = ti[q] / M;
+              fs[q] = fabsf(score32<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H, R, m, r,
+                                        t, S, tw));
+            } else {
+              fs[q] = 0.0f;
+            }
             fbest = fmaxf(fbest, fs[q]);
           }
         }
@@ -320,6 +356,8 @@ __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
           // <S_r d_m, S_r d_m> = ||d_m||^2: steering preserves the norm
           const double diag = (double)a.anorm[mb].x + (double)a.anorm[mb].y;
           const double rhs = df_to_d(best_ax);
+          load_factor<KK>(a, p, S);
+          have_factor = true;
           if (!CholAt<KK, 0>::run(t, S, gr, diag, rhs)) {
             outcome = 1;
           } else {
@@ -337,18 +375,27 @@ __global__ void __launch_bounds__(128) romp_refine_kernel(const RefineArgs a) {
             dr = 2.0f * (t + 6) * kU32 * (xnorm + 1.5f * asum);
             if (t >= a.K) {
               outcome = 1;
-              // final residual norm in FP32 (the bf16 row is not needed any more)
-              rnorm = sqrtf(residual_q<KK>(nullptr, xp, a.d, HJ, a.n, t, S, tw, qtab));
+              // final residual norm in FP32 (the fp16 row is not needed any more)
+              rnorm = sqrtf(residual_q<KK>(nullptr, 1.0f, xp, a.d, HJ, a.n, t, S, tw, qtab));
             } else {
-              rnorm = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes), xp, a.d,
-                                           HJ, a.n, t, S, tw, qtab));
-              store_state<KK>(a, p, S, t, rnorm, dr);
+              // the previous residual's norm bounds the new one (least squares
+              // over a larger support)
+              const int en = rsc_row_exponent(rnorm);
+              rnorm = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes),
+                                           ldexpf(1.0f, kRowLog2 - en), xp, a.d, HJ, a.n, t, S,
+                                           tw, qtab));
+              store_state<KK>(a, p, S, t, en, rnorm, dr);
             }
           }
         }
       }
     }
     if (outcome == 1) {
+      if (!have_factor) {
+#pragma unroll
+        for (int i = 0; i < KK; ++i)
+          if (i < t) S.a[i] = a.sD[(StateIdx<KK>::dA + i) * a.P + p];
+      }
       write_outputs<KK>(a, p, S, t, rnorm);
       a.status[p] = 0;
     } else if (outcome == 2) {

@@ -1,16 +1,16 @@
 // romp_score.cu -- one greedy step's scores on the tensor cores (tcgen05),
-// warp-specialised, for the BF16 path of rsc_encode.
+// warp-specialised, for the FP16 path of rsc_encode.
 //
 // score(p, m, r) = <S_r d_m, r_p> for every patch p and every steered atom
-// (m, r) is the dense contraction of the packed residuals (bf16, 112 columns,
-// in HBM) with the steered dictionary [S_0 D ... S_{R-1} D] (bf16, M*R rows,
+// (m, r) is the dense contraction of the packed residuals (fp16, scaled, 112 columns,
+// in HBM) with the steered dictionary [S_0 D ... S_{R-1} D] (fp16, scaled, M*R rows,
 // angle-major), i.e. steps (a) and (b) of OMP (Sec. II-C) over the augmented
 // dictionary of Fig. "code", the two linear maps folded into one.  Per CTA
 // (persistent, one per SM) and pair of 128-patch tiles:
 //   * warp 8 (one lane) loads the two residual tiles and streams the steered
 //     dictionary in 128-row chunks through a 3-stage shared-memory ring with
 //     TMA (128-byte swizzle);
-//   * warp 9 (one lane) issues tcgen05.mma (M = 128, N = 128, K = 16, bf16 in,
+//   * warp 9 (one lane) issues tcgen05.mma (M = 128, N = 128, K = 16, fp16 in,
 //     f32 out) for both tiles into one of two TMEM accumulator buffers per
 //     tile, and tcgen05.commit's the stage, the buffer and the A tiles back;
 //   * warps 0-7 (one thread per patch, TMEM lane = patch) read each buffer
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr uint32_t kCols = kSTiles * 2 * kTcBN;  // 512
-  constexpr uint32_t kIdesc = tc::idesc_bf16_f32(128, kTcBN);
+  constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, kTcBN);
 
   if (tid == 0) {
     tc::mbar_init(bar(kBarAFull), 1);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
             const uint32_t d = tmem + (uint32_t)(t * 2 + b) * kTcBN;
             for (int ks = 0; ks < a.ksteps; ++ks) {
               const uint32_t off = (ks >> 2) * kSBlk + (ks & 3) * 32;
-              tc::mma_bf16(d, tc::smem_desc_sw128(a0 + t * kSTileBytes + off),
+              tc::mma_f16(d, tc::smem_desc_sw128(a0 + t * kSTileBytes + off),
                            tc::smem_desc_sw128(b0 + off), kIdesc, ks > 0 ? 1u : 0u);
             }
           }

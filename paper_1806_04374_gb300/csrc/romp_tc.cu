@@ -1,4 +1,4 @@
-// romp_tc.cu -- rotational OMP with a BF16 tensor-core (tcgen05) scoring pass.
+// romp_tc.cu -- rotational OMP with an FP16 tensor-core (tcgen05) scoring pass.
 //
 // The scores of one greedy step, score(p, m, r) = <S_r d_m, r_p> (OMP of
 // Sec. II-C over the augmented dictionary of Fig. "code"), are steps (a) and
@@ -6,11 +6,11 @@
 // the angle transform sum_k e^{ik 2 pi r/R} G_k.  Both are linear, so their
 // product is one dense contraction of the packed residual with the steered
 // dictionary [S_0 D ... S_{R-1} D] (built once per dictionary by the host in
-// FP64 and stored in bf16).  This kernel runs that contraction on the 5th
+// FP64 and stored in fp16, scaled by kDictScale).  This kernel runs that contraction on the 5th
 // generation tensor cores:
 //
 //   * a CTA owns TILES tiles of 128 patches; a tile's packed residuals are
-//     the A operand (bf16, 128 x 112, 128-byte swizzled K-major in shared
+//     the A operand (fp16, 128 x 112, 128-byte swizzled K-major in shared
 //     memory) and every TMEM lane holds one patch;
 //   * the steered dictionary streams through a ring of shared-memory stages
 //     in chunks of 128 steered atoms, loaded by TMA (one thread issues the
@@ -19,15 +19,16 @@
 //   * epilogue (c): every thread reads its patch's scores with tcgen05.ld and
 //     keeps the 8 largest block maxima of |score| and the largest value it
 //     discarded;
-//   * per patch, every candidate within 2E of the best (E bounds the bf16
+//   * per patch, every candidate within 2E of the best (E bounds the fp16
 //     error of a score) is re-scored exactly in double-float as
 //     <A_c, x> - sum_i a_i <A_c, A_i>, the Gram entries coming from the
 //     per-harmonic cross-Gram table; if the window holds more candidates
 //     than were kept, the patch is handed to the FP32 path instead;
 //   * (e) the Gram row and right-hand side of the winner in double-float,
 //     the Cholesky row and solve in FP64, per thread;
-//   * (d) the new residual in FP32, rounded to bf16 into the A tile.
-#include <cuda_bf16.h>
+//   * (d) the new residual in FP32, scaled by a power of two chosen from the
+//     previous norm (rsc_internal.h) and rounded to fp16 into the A tile.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "df.cuh"
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(TILES * 128, 1)
   const uint32_t full_bar0 = tc::smem_u32(bars);
   const uint32_t done_bar0 = tc::smem_u32(bars + kStages);
   constexpr uint32_t kCols = TILES * 2 * kTcBN;
-  constexpr uint32_t kIdesc = tc::idesc_bf16_f32(128, kTcBN);
+  constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, kTcBN);
 
   // ---- set-up: tables, barriers, TMEM
   for (int i = tid; i < 4 * H * R; i += blockDim.x) {
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(TILES * 128, 1)
       for (int ks = 0; ks < a.ksteps; ++ks) {
         const uint32_t off = (ks >> 2) * kBlkA + (ks & 3) * 32;
         const uint32_t boff = (ks >> 2) * kBlkB + (ks & 3) * 32;
-        tc::mma_bf16(d, tc::smem_desc_sw128(a0 + tl * 2 * kBlkA + off),
+        tc::mma_f16(d, tc::smem_desc_sw128(a0 + tl * 2 * kBlkA + off),
                      tc::smem_desc_sw128(b0 + boff), kIdesc, ks > 0 ? 1u : 0u);
       }
     }
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(TILES * 128, 1)
     int t = 0;
     bool active = valid, redo = false;
     float xnorm = 0.0f, rnorm = 0.0f, dr = 0.0f;
+    int escale = 0;  // the A row holds the residual times 2^(kRowLog2 - escale)
     if (valid) {
       df acc = df_make(0.0f);
       for (int e = 0; e < HJ; ++e) {
@@ -180,7 +182,9 @@ __global__ void __launch_bounds__(TILES * 128, 1)
         acc = df_add(acc, e < J ? q : df_mul_f(q, 2.0f));
       }
       xnorm = sqrtf(fmaxf(acc.hi + acc.lo, 0.0f));
-      rnorm = sqrtf(write_residual<KK>(SmemRow{myA, row}, xp, a.d, J, HJ, a.n, 0, S, tw));
+      escale = rsc_row_exponent(xnorm);
+      rnorm = sqrtf(write_residual<KK>(SmemRow{myA, row}, ldexpf(1.0f, kRowLog2 - escale), xp,
+                                       a.d, J, HJ, a.n, 0, S, tw));
       dr = 2.0f * kU32 * xnorm;
     } else {
       // rows of absent patches: zeros
@@ -284,9 +288,19 @@ __global__ void __launch_bounds__(TILES * 128, 1)
 
       // ---- per patch: certify, re-score, least squares, residual
       if (active) {
+        // accumulator scores are 2^(16 - escale) times the true scores
+        const float unscale = ldexpf(1.0f, escale - 16);
+#pragma unroll
+        for (int q = 0; q < kTop; ++q) tv[q] *= unscale;
+        disc *= unscale;
         const float s1 = tv[0];
-        const float E = 1.25f * (3.90625e-3f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f) *
-                            rnorm + 2.0f * dr;
+        // fp16 error of a score (both operands, second order, accumulation,
+        // subnormal rounding of dictionary and row entries), times 1.25, plus
+        // the FP32 residual's own error
+        const float E = 1.25f * (9.765625e-4f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f +
+                                 11.0f * 1.16415321826934814e-10f) *
+                            rnorm +
+                        1.25f * 11.0f * ldexpf(1.0f, escale - 33) + 2.0f * dr;
         if (!(s1 + E > stop_level)) {
           active = false;
         } else {
@@ -370,7 +384,9 @@ __global__ void __launch_bounds__(TILES * 128, 1)
 #pragma unroll
                 for (int i = 0; i < KK; ++i)
                   if (i < t) asum += fabsf(S.ahi[i]);
-                rnorm = sqrtf(write_residual<KK>(SmemRow{myA, row}, xp, a.d, J, HJ, a.n, t, S, tw));
+                escale = rsc_row_exponent(rnorm);
+                rnorm = sqrtf(write_residual<KK>(SmemRow{myA, row}, ldexpf(1.0f, kRowLog2 - escale),
+                                                 xp, a.d, J, HJ, a.n, t, S, tw));
                 dr = 2.0f * (t + 6) * kU32 * (xnorm + 1.5f * asum);
               }
             }

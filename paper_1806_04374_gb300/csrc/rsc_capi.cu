@@ -5,7 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <mutex>
 #include <vector>
@@ -73,14 +73,15 @@ void free_dict(rsc_dict *d) {
   cudaFree(d->tw);
   cudaFree(d->err);
   cudaFree(d->fallbacks);
-  cudaFree(d->steered_bf16);
+  cudaFree(d->steered_f16);
   cudaFree(d->xgram);
   cudaFree(d->anorm);
   delete d;
 }
 
-uint16_t bf16_bits(double v) {
-  const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+// fp16 bits of kDictScale * v (rounded once, from double)
+uint16_t f16_bits(double v) {
+  const __half b = __double2half(v * (double)kDictScale);
   return *reinterpret_cast<const uint16_t *>(&b);
 }
 
@@ -89,7 +90,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// TMA map of a row-major bf16 matrix [rows][kTcKst]: box 64 columns x kTcBN
+// TMA map of a row-major fp16 matrix [rows][kTcKst]: box 64 columns x kTcBN
 // rows, 128-byte swizzle, zero fill outside (columns kTcKst..127, rows >= rows).
 int encode_rows_map(CUtensorMap *map, void *base, size_t rows) {
   static EncodeTiledFn fn = nullptr;
@@ -107,7 +108,7 @@ int encode_rows_map(CUtensorMap *map, void *base, size_t rows) {
   const cuuint64_t gstride[1] = {(cuuint64_t)kTcKst * 2};
   const cuuint32_t box[2] = {64, (cuuint32_t)kTcBN};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult cr = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr,
+  CUresult cr = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, gdim, gstride, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) {
@@ -117,8 +118,8 @@ int encode_rows_map(CUtensorMap *map, void *base, size_t rows) {
   return RSC_OK;
 }
 
-// Tables of the tensor-core path: the packed steered dictionary (bf16, row
-// r*M + m = S_r d_m, angle-major so that 32 consecutive rows hold different
+// Tables of the tensor-core path: the packed steered dictionary (fp16 of
+// kDictScale times the entries, row r*M + m = S_r d_m, angle-major so that 32 consecutive rows hold different
 // atoms; the packed layout described in rsc_internal.h), the
 // per-harmonic cross-Gram table H_k(a, b) in double-float and the TMA map.
 // Returns RSC_OK also when the sizes are outside the path (tables left null).
@@ -142,11 +143,11 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
           const double dim = k ? h[((size_t)m * HJ + k * J + j) * 2 + 1] : 0.0;
           const double re = c * dre + s * dim, im = c * dim - s * dre;
           if (k == 0) {
-            row[j] = bf16_bits(re);
+            row[j] = f16_bits(re);
           } else {
             const int q = J + 2 * ((k - 1) * J + j);
-            row[q] = bf16_bits(M_SQRT2 * re);
-            row[q + 1] = bf16_bits(M_SQRT2 * im);
+            row[q] = f16_bits(M_SQRT2 * re);
+            row[q + 1] = f16_bits(M_SQRT2 * im);
           }
         }
       }
@@ -180,7 +181,7 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
     const float hi = (float)n2;
     NA[m] = make_float2(hi, (float)(n2 - (double)hi));
   }
-  cudaError_t e = cudaMalloc(&d->steered_bf16, B.size() * 2);
+  cudaError_t e = cudaMalloc(&d->steered_f16, B.size() * 2);
   if (e == cudaSuccess) e = cudaMalloc(&d->xgram, X.size() * sizeof(float4));
   if (e == cudaSuccess) e = cudaMalloc(&d->anorm, NA.size() * sizeof(float2));
   if (e == cudaErrorMemoryAllocation) {
@@ -188,7 +189,7 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
     return RSC_ERR_OOM;
   }
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d->steered_bf16, B.data(), B.size() * 2, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(d->steered_f16, B.data(), B.size() * 2, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d->xgram, X.data(), X.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -197,7 +198,7 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
 
-  return encode_rows_map(&d->tmap_b, d->steered_bf16, rows);
+  return encode_rows_map(&d->tmap_b, d->steered_f16, rows);
 }
 
 int check_device(const rsc_dict *d) {
@@ -341,7 +342,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
                int32_t *atom, int32_t *angle_idx, float *angle, double *coef, float *resid_norm2,
                void *stream) {
   if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
-  if (prec != RSC_FP32 && prec != RSC_BF16_RESCORE) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
   if (P == 0) return RSC_OK;
   if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
   if (!aligned16(x) || !aligned_as<int32_t>(atom) || !aligned_as<int32_t>(angle_idx) ||
@@ -377,11 +378,11 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
     return rc;
   }
 
-  // BF16 tensor-core path, split per greedy step into a scoring kernel and a
+  // FP16 tensor-core path, split per greedy step into a scoring kernel and a
   // per-patch refine kernel; patches it hands back are coded by the FP32 path
-  if (!dict->steered_bf16 || K > kTcMaxK || P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
+  if (!dict->steered_f16 || K > kTcMaxK || P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
   int nD = 0, nF = 0, nI = 0;
-  rsc_state_layout(K, &nD, &nF, &nI);
+  const int cap = rsc_state_layout(K, &nD, &nF, &nI);
   auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const size_t bA = al256((size_t)P * kTcKst * 2), bCI = al256((size_t)P * kTcTop * 4),
                bCV = bCI, bCD = al256((size_t)P * 4), bSt = bCD, bD = al256((size_t)nD * P * 8),
@@ -465,6 +466,9 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   if (rc == RSC_OK) {
     a.redo_count = ra.redo_count;
     a.redo_list = ra.redo_list;
+    a.resume_sI = ra.sI;
+    a.resume_P = P;
+    a.resume_cap = cap;
     a.fallbacks = nullptr;
     const int slot = timing_begin(dict, 1, st);
     rc = rsc_launch_f32(a, st);
@@ -479,7 +483,7 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
                     int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
                     float *resid_norm2) {
   if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
-  if (prec != RSC_FP32 && prec != RSC_BF16_RESCORE) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
   if (P == 0) return RSC_OK;
   if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
   int rc = check_device(dict);

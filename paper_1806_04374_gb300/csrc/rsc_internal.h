@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "rsc.h"
@@ -27,24 +28,38 @@ struct rsc_dict {
   unsigned long long *fallbacks;  // device counter of exact re-scans
   // tensor-core path: steered dictionary and cross-Gram table (null when the
   // sizes are outside what the path handles)
-  void *steered_bf16;    // [R*M][kTcKst] bf16, row r*M + m = packed S_r d_m
+  void *steered_f16;     // [R*M][kTcKst] fp16 of kDictScale x packed S_r d_m (row r*M + m)
   float4 *xgram;         // [M][M][H] double-float complex H_k(a,b) = sum_j conj(d_a) d_b
   float2 *anorm;         // [M] ||d_m||^2 in double-float
   int n;                 // packed real length J (2 kmax + 1)
   // per-phase timing (diagnostic): event pairs recorded around launches
   int timing;
   void *timing_state;    // owned std::vector of recorded pairs, see rsc_capi.cu
-  CUtensorMap tmap_b;    // TMA map of steered_bf16, box 64 x kTcBN, 128B swizzle
+  CUtensorMap tmap_b;    // TMA map of steered_f16, box 64 x kTcBN, 128B swizzle
 };
 
 // Packed real coordinates of a half spectrum, shared by the tensor-core
 // operands: slot q < J is Re c[j=q, k=0]; slot J + 2 ((k-1) J + j) + c holds
 // sqrt(2) Re (c = 0) or sqrt(2) Im (c = 1) of c[j, k], k >= 1.  The Euclidean
 // dot product of two packed vectors is the coefficient inner product.
-constexpr int kTcKst = 112;  // stored row length of the steered dictionary (bf16)
+constexpr int kTcKst = 112;  // stored row length of the steered dictionary (fp16)
 constexpr int kTcMaxN = 112; // packed lengths the tensor-core path handles
 constexpr int kTcBN = 128;   // steered atoms per MMA (N) and per TMA box
 constexpr int kTcMaxK = 8;   // greedy steps the tensor-core path handles
+
+// fp16 operand scaling of the tensor-core path.  The steered dictionary holds
+// kDictScale * entries (unit atoms: |entries| <= 256); a residual row is
+// stored times 2^(kRowLog2 - e), e = rsc_row_exponent(bound) for a bound >= the
+// row's norm, so its entries are below 2^kRowLog2 and far from fp16's
+// subnormal range.  A score read from the accumulator is therefore
+// 2^(16 - e) times the true score; both scales are powers of two (exact).
+constexpr float kDictScale = 256.0f;
+constexpr int kRowLog2 = 8;
+__host__ __device__ inline int rsc_row_exponent(float bound) {
+  int e = 0;
+  (void)frexpf(bound, &e);  // bound = f 2^e, f in [0.5, 1); 0 for bound = 0
+  return e < -100 ? -100 : (e > 126 ? 126 : e);
+}
 
 struct TcArgs {
   const float *x;
@@ -65,7 +80,7 @@ struct TcArgs {
   unsigned long long *fallbacks;
 };
 
-// BF16 tensor-core scoring path fused with the per-patch steps in one
+// FP16 tensor-core scoring path fused with the per-patch steps in one
 // persistent kernel (romp_tc.cu; used by rsc_encode_noalloc); patches whose
 // candidates overflow are appended to redo_list for the FP32 path.
 int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream);
@@ -73,7 +88,7 @@ int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream)
 // Block maxima kept per patch and greedy step by the tensor-core scoring.
 constexpr int kTcTop = 8;
 
-// One scoring pass of the split BF16 path (romp_score.cu): packed bf16
+// One scoring pass of the split FP16 path (romp_score.cu): packed fp16
 // residual rows (TMA map tmA: [P][kTcKst]) times the steered dictionary
 // (tmB) -> per patch the kTcTop largest block maxima of |score| with their
 // rows (r*M + m) and the largest value left out.
@@ -89,7 +104,7 @@ struct ScoreArgs {
 int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
                      cudaStream_t stream);
 
-// Per-patch steps of the split BF16 path (romp_refine.cu): init (packed x,
+// Per-patch steps of the split FP16 path (romp_refine.cu): init (packed x,
 // state) or one refine (certify, re-score, Cholesky, residual).
 struct RefineArgs {
   const float *x;
@@ -99,7 +114,7 @@ struct RefineArgs {
   const float *tw;       // [4][H][R]
   const float4 *xgram;
   const float2 *anorm;   // [M] ||d_m||^2 in double-float
-  unsigned char *A;      // [P][kTcKst] bf16 packed residual rows
+  unsigned char *A;      // [P][kTcKst] fp16 packed residual rows, scaled (see below)
   const int *cand_idx;
   const float *cand_val;
   const float *cand_disc;
@@ -139,6 +154,12 @@ struct RompArgs {
   // when set, code only patches redo_list[0 .. *redo_count) (device memory)
   const int *redo_list = nullptr;
   const int *redo_count = nullptr;
+  // when set, patch p resumes from the steps the FP16 path already certified:
+  // t0 = sI[2 cap * sP + p] steps with atoms sI[i * sP + p] and angles
+  // sI[(cap + i) * sP + p], i < t0 (the refine kernel's state layout)
+  const int *resume_sI = nullptr;
+  int64_t resume_P = 0;
+  int resume_cap = 0;
 };
 
 // FP32 CUDA-core scoring path (romp_f32.cu).

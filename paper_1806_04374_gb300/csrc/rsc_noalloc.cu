@@ -1,7 +1,7 @@
-// rsc_noalloc.cu -- rsc_encode_noalloc: the BF16 tensor-core coding path
+// rsc_noalloc.cu -- rsc_encode_noalloc: the FP16 tensor-core coding path
 // without any device allocation.
 //
-// rsc_encode's BF16 path needs one scratch buffer per call: the list of
+// rsc_encode's FP16 path needs one scratch buffer per call: the list of
 // patches the tensor-core kernel hands to the FP32 kernel, plus its counter.
 // It takes that buffer from the stream-ordered allocator (cudaMallocAsync).
 // Some callers cannot allocate while they code: a serving process that
@@ -61,7 +61,7 @@ extern "C" int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   if (dev != dict->device) return RSC_ERR_INVALID;
-  if (!dict->steered_bf16 || K > kTcMaxK) return RSC_ERR_UNSUPPORTED;
+  if (!dict->steered_f16 || K > kTcMaxK) return RSC_ERR_UNSUPPORTED;
   int *scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != RSC_OK) return rc;

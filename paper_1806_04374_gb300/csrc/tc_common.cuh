@@ -4,7 +4,7 @@
 // screen, the candidate list of block maxima, and the packed residual.
 #pragma once
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "df.cuh"
@@ -225,12 +225,13 @@ struct CholAt<KK, KK> {
 };
 
 // Produces this thread's packed residual x - sum_i a_i S_{r_i} d_{m_i} (FP32,
-// rounded to bf16) as 16-byte chunks sink(chunk index, 8 bf16) in packed
-// order, zero-padded to a multiple of 16 slots; returns ||r||^2.
+// times `scale`, rounded to fp16) as 16-byte chunks sink(chunk index, 8 fp16)
+// in packed order, zero-padded to a multiple of 16 slots; returns ||r||^2
+// (unscaled).
 // Entries are visited in packed order; a k >= 1 entry yields its two slots
 // (sqrt(2) Re, sqrt(2) Im) from one pass over the selected atoms.
 template <int KK, class Sink>
-__device__ float write_residual(Sink &&sink, const float *__restrict__ xp,
+__device__ float write_residual(Sink &&sink, float scale, const float *__restrict__ xp,
                                 const float *__restrict__ d, int J, int HJ, int n, int t,
                                 const Ls<KK> &S, const TwS &tw) {
   float n2 = 0.0f;
@@ -240,10 +241,10 @@ __device__ float write_residual(Sink &&sink, const float *__restrict__ xp,
   int kcur = -1;
   auto flush = [&]() {
     uint4 pk;
-    __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]);
-    __nv_bfloat162 b1 = __floats2bfloat162_rn(v[2], v[3]);
-    __nv_bfloat162 b2 = __floats2bfloat162_rn(v[4], v[5]);
-    __nv_bfloat162 b3 = __floats2bfloat162_rn(v[6], v[7]);
+    __half2 b0 = __floats2half2_rn(v[0] * scale, v[1] * scale);
+    __half2 b1 = __floats2half2_rn(v[2] * scale, v[3] * scale);
+    __half2 b2 = __floats2half2_rn(v[4] * scale, v[5] * scale);
+    __half2 b3 = __floats2half2_rn(v[6] * scale, v[7] * scale);
     pk.x = *reinterpret_cast<uint32_t *>(&b0);
     pk.y = *reinterpret_cast<uint32_t *>(&b1);
     pk.z = *reinterpret_cast<uint32_t *>(&b2);

@@ -11,7 +11,7 @@ import numpy as np
 from . import Dictionary, encode, ksvd_update
 
 
-def learn(x, d0, R: int, K: int, iters: int, precision: str = "bf16", callback=None):
+def learn(x, d0, R: int, K: int, iters: int, precision: str = "f16", callback=None):
     """x: CUDA float32 [P, kmax+1, J, 2] patches; d0: CUDA float32 initial
     unit-norm atoms [M, kmax+1, J, 2].  Returns (d, codes, history) with
     history[i] = {"iter", "mse", "unused"} where mse is the mean squared

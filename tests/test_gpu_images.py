@@ -47,7 +47,7 @@ def test_project_matches_oracle(rsc, shape):
     b.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
 def test_encode_uneven_images(rsc, precision):
     """Images of different sizes (one smaller than a window) coded in one
     call; windows are compared with the oracle run on the oracle's own

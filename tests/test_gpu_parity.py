@@ -14,7 +14,7 @@ from parity import check
 
 pytestmark = pytest.mark.gpu
 
-COEF_TOL = {"fp32": 1e-5, "bf16": 1e-3}
+COEF_TOL = {"fp32": 1e-5, "f16": 1e-3}
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +38,7 @@ def run_gpu(rsc, x, d, R, K, precision="fp32"):
     return res
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
 def test_small_workload_full(rsc, precision):
     """1000 patches, M=16, R=32, K=3, sigma 0.05 (plus 3 ragged extra)."""
     d, x, _, wl = synth.workload_inputs("omp_small")
@@ -50,7 +50,7 @@ def test_small_workload_full(rsc, precision):
     print(precision, s, "fallbacks", g["fallbacks"])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
 def test_1m_workload_sampled(rsc, precision):
     """The 1,000,000-patch workload (M=64, R=64, K=5) coded in one launch as
     the benchmark does; 768 sampled patches (incl. the first and last) are
@@ -79,6 +79,9 @@ CASES = [
     ("kmax12_J10", 32, 10, 12, 64, 4, 40, 3, 0.05),
     ("kmax16_J4", 16, 4, 16, 64, 3, 40, 3, 0.05),
     ("kmax0_rotation_invariant", 8, 6, 0, 16, 3, 30, 3, 0.05),
+    # the image workload's coder sizes: 21x21 patches, J=10, kmax=12 (n=250),
+    # M=256, R=128, K=8 (outside the tensor-core path: FP32 only)
+    ("c2_sizes_n250_M256_R128_K8", 256, 10, 12, 128, 8, 24, 4, 0.05),
 ]
 
 
@@ -88,13 +91,13 @@ def tc_supported(J, kmax, K):
     return J * (2 * kmax + 1) <= 112 and K <= 8
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_edge_shapes(rsc, case, precision):
     name, M, J, kmax, R, K, P, n_terms, sigma = case
     d = synth.make_dictionary(M, J, kmax, 1000 + M + R)
     x, _ = synth.make_patches(d, P, n_terms, sigma, 2000 + R)
-    if precision == "bf16" and not tc_supported(J, kmax, K):
+    if precision == "f16" and not tc_supported(J, kmax, K):
         with pytest.raises(rsc.RscError) as ei:
             run_gpu(rsc, x, d, R, K, precision)
         assert ei.value.status == rsc.RSC_ERR_UNSUPPORTED
@@ -104,7 +107,7 @@ def test_edge_shapes(rsc, case, precision):
     print(name, precision, s, "fallbacks", g["fallbacks"])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
 def test_degenerate_patches(rsc, precision):
     """Zero patch (no step), exactly one steered atom on the grid (one step,
     then stop), and an exactly sparse patch recovered with zero residual."""
@@ -122,7 +125,22 @@ def test_degenerate_patches(rsc, precision):
     check(x, d, R, 3, g, COEF_TOL[precision])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
+@pytest.mark.parametrize("scale", [1e-12, 1e12])
+def test_patch_scale(rsc, precision, scale):
+    """Selections and weights scale with the patch: the FP16 path stores each
+    residual row times a power of two chosen from its norm bound, so patches
+    far outside fp16's range (1e-12, 1e12 times the unit-scale workload) are
+    coded like the oracle codes them."""
+    d, x, _, wl = synth.workload_inputs("omp_small", P=300)
+    xs = (x.astype(np.float64) * scale).astype(np.float32)
+    g = run_gpu(rsc, xs, d, wl.R, wl.K, precision)
+    s = check(xs, d, wl.R, wl.K, g, COEF_TOL[precision])
+    assert s["pinned_steps"] > 0.98 * xs.shape[0] * wl.K - 20
+    print(precision, scale, s, "fallbacks", g["fallbacks"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
 def test_rotation_covariance_gpu(rsc, precision):
     """Rotating every patch by s grid steps shifts every GPU-selected angle by
     s (Eq. 3) wherever the oracle's margins pin the selections."""
@@ -173,7 +191,7 @@ def test_empty_and_errors(rsc):
         rsc.Dictionary(torch.from_numpy(d).cuda(), 129)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
 def test_host_entry_point_matches_device(rsc, precision):
     """rsc_encode_host (chunked copies + coding on two streams) returns the
     same codes as rsc_encode on device buffers."""
@@ -188,17 +206,17 @@ def test_host_entry_point_matches_device(rsc, precision):
         assert np.array_equal(a[k].cpu().numpy(), b[k].numpy()), k
 
 
-def test_bf16_and_fp32_paths_agree(rsc):
+def test_f16_and_fp32_paths_agree(rsc):
     """Both scoring paths certify their picks against exact re-scoring, so on
     the 1M workload they return the same selections wherever the oracle's
     margin pins them; compared here on every patch of the first 200k, with
     the weights equal to ~1e-12 relative (both solve the same FP64 system)."""
     d, x, _, wl = synth.workload_inputs("omp_1m", P=200_000)
     g32 = run_gpu(rsc, x, d, wl.R, wl.K, "fp32")
-    g16 = run_gpu(rsc, x, d, wl.R, wl.K, "bf16")
+    g16 = run_gpu(rsc, x, d, wl.R, wl.K, "f16")
     same = np.all((g32["atom"] == g16["atom"]) & (g32["angle_idx"] == g16["angle_idx"]), axis=1)
     assert same.mean() > 0.9999, same.mean()
     rel = np.abs(g32["coef"][same] - g16["coef"][same]).max() / np.abs(g32["coef"]).max()
     assert rel < 1e-9, rel
     print("identical patches", same.sum(), "of", same.size, "max rel coef diff", rel,
-          "bf16 handed to fp32:", g16["fallbacks"])
+          "f16 handed to fp32:", g16["fallbacks"])

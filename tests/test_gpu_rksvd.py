@@ -20,7 +20,7 @@ def test_recovers_planted_atoms(cuda_ok):
     x, _ = synth.make_patches(d_true, 6000, 2, 0.02, 902)
     d0 = synth.make_dictionary(M, 6, 8, 903)
     d, codes, hist = rksvd.learn(torch.from_numpy(x).cuda(), torch.from_numpy(d0).cuda(), R, K,
-                                 iters=15, precision="bf16")
+                                 iters=15, precision="f16")
     mse = [h["mse"] for h in hist]
     assert mse[-1] < 0.5 * mse[0]
     rec = bench.recovery(d.cpu().numpy(), d_true, R)

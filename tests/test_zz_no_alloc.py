@@ -1,7 +1,7 @@
-"""rsc_encode_noalloc: the BF16 coding path for callers that cannot allocate
+"""rsc_encode_noalloc: the FP16 coding path for callers that cannot allocate
 device memory while they code (its scratch list lives in a fixed device
 array inside the library).  Called through the C ABI and compared with
-rsc_encode (RSC_BF16_RESCORE) on the same inputs, twice in a row, since every
+rsc_encode (RSC_F16_RESCORE) on the same inputs, twice in a row, since every
 call reuses the same array.  Collected last on purpose."""
 import numpy as np
 import pytest
@@ -35,7 +35,7 @@ def test_noalloc_matches_encode_twice(cuda_ok):
     P, K = x.shape[0], wl.K
     dic = rsc.Dictionary(torch.from_numpy(d).cuda(), wl.R)
     xd = torch.from_numpy(x).cuda()
-    ref = rsc.encode(dic, xd, K, "bf16")
+    ref = rsc.encode(dic, xd, K, "f16")
     torch.cuda.synchronize()
     stream = int(torch.cuda.current_stream().cuda_stream)
     outs = [_outputs(torch, P, K) for _ in range(3)]
