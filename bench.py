@@ -256,6 +256,166 @@ def run_reference(args) -> None:
     print(json.dumps(line))
 
 
+def measure_projection(rsc, torch, dev, stream, reps: int = 5) -> dict:
+    """rsc_project over one 2048 x 2048 image (4.15 M windows of 11 x 11,
+    n = 102): windows/s from CUDA events on the launching stream, against
+    the CUDA-core FP32 roofline of its contraction (2 x 97 x 108 flops per
+    window; the 432-byte output per window is the HBM side)."""
+    N, J, kmax = 11, 6, 8
+    basis = rsc.Basis(N, J, kmax)
+    rng = np.random.default_rng(20180614)
+    img = torch.from_numpy(rng.standard_normal((2048, 2048)).astype(np.float32)).to(dev)
+    with torch.cuda.stream(stream):
+        out = rsc.project(basis, img, stream=stream)  # warm-up (and output size)
+        del out
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            out = rsc.project(basis, img, stream=stream)
+            del out
+        ev[1].record(stream)
+        stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    P = (2048 - N + 1) ** 2
+    nout = (kmax + 1) * J * 2
+    flops = 2.0 * basis.npix * nout * P
+    basis.close()
+    return {"windows": P, "ms_per_call": ms, "windows_per_s": P / (ms / 1e3),
+            "achieved_tflops": flops / (ms / 1e3) / 1e12, "bound": "alu (FP32 FMA)",
+            "write_gbs": P * nout * 4 / (ms / 1e3) / 1e9,
+            "config": "one 2048x2048 image, N=11 (97 px), J=6, kmax=8, stride 1"}
+
+
+def measure_images_c2(rsc, torch, dev) -> dict:
+    """rsc_encode_images at the image workload's coder sizes: 21 x 21 patches
+    (349 px), J = 10, kmax = 12 (n = 250, outside the tensor-core path, so
+    the FP32 path), M = 256, R = 128, K = 8, on 4 seeded N(0,1) images of
+    sides 96, 160, 224, 288 (every stride-1 window).  Host clock around the
+    blocking call (projection + coding), after one warm-up call."""
+    N, J, kmax, M, R, K = 21, 10, 12, 256, 128, 8
+    rng = np.random.default_rng(20180617)
+    imgs = [torch.from_numpy(rng.standard_normal((s_, s_)).astype(np.float32)).to(dev)
+            for s_ in (96, 160, 224, 288)]
+    basis = rsc.Basis(N, J, kmax)
+    dic = rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180618)).to(dev), R)
+    rsc.encode_images(dic, basis, imgs[:1], K, "fp32")
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    out = rsc.encode_images(dic, basis, imgs, K, "fp32")
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    P = int(out["atom"].shape[0])
+    dic.close()
+    basis.close()
+    return {"patches": P, "s": dt, "patches_per_s": P / dt, "precision": "fp32",
+            "config": "N=21 (349 px), J=10, kmax=12 (n=250), M=256, R=128, K=8; "
+                      "4 images, sides 96/160/224/288, projection included"}
+
+
+def measure_rksvd(rsc, torch, dev, iters: int = 20) -> dict:
+    """Rotational K-SVD on 200,000 patches drawn from 64 planted atoms
+    (3 terms, noise 0.05): learn M = 128 atoms, R = 64, K = 5, from the first
+    128 patches normalised; reports seconds per iteration, the MSE trajectory
+    and the fraction of planted atoms recovered (|<S_theta d_m, t>| >= 0.99)."""
+    from paper_1806_04374_gb300 import rksvd
+    R, K, M, P = 64, 5, 128, 200_000
+    d_true = synth.make_dictionary(64, 6, 8, 20180615)
+    x, _ = synth.make_patches(d_true, P, 3, 0.05, 20180616)
+    d0 = x[:M].astype(np.float64)
+    d0[:, 0, :, 1] = 0.0
+    d0 /= np.sqrt(synth.coef_norm2(d0))[:, None, None, None]
+    xd = torch.from_numpy(x).to(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    d, _, hist = rksvd.learn(xd, torch.from_numpy(d0.astype(np.float32)).to(dev), R, K,
+                             iters=iters, precision="f16")
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    mse = [h["mse"] for h in hist]
+    return {"patches": P, "atoms_learned": M, "atoms_planted": 64, "R": R, "K": K,
+            "iterations": iters, "s_per_iteration": dt / (iters + 1),
+            "mse_first": mse[0], "mse_last": mse[-1],
+            "recovery_0.99": recovery(d.cpu().numpy(), d_true, R),
+            "timing": "host clock around the whole loop (encode + update + sync per iteration)"}
+
+
+def run_serving(args) -> None:
+    """Serving loop of the request workload: images of side ~ U{128..1024}
+    (square, seeded N(0,1) pixels: the coder's cost does not depend on the
+    content), 11 x 11 patches, M = 128 resident atoms, R = 64, K = 5, FP16
+    path; requests arrive as a Poisson process; the server takes every
+    request that has arrived (up to `--serve-batch` patches) into one
+    rsc_encode_images call and copies the codes back to the host.  Latency =
+    host-visible completion - arrival.  Runs: all requests at t = 0
+    (capacity), then Poisson arrivals at each rate of `--rates`."""
+    import torch
+    import paper_1806_04374_gb300 as rsc
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rsc.load_library()
+    N, J, kmax, M, R, K = 11, 6, 8, 128, 64, 5
+    basis = rsc.Basis(N, J, kmax)
+    dic = rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180619)).to(dev), R)
+    rng = np.random.default_rng(20180620)
+    sides = rng.integers(128, 1025, size=64)
+    pool = [torch.from_numpy(rng.standard_normal((int(s_), int(s_))).astype(np.float32)).to(dev)
+            for s_ in sides]
+    windows = [(int(s_) - N + 1) ** 2 for s_ in sides]
+
+    def serve(arrivals, which):
+        n = len(arrivals)
+        lat = np.zeros(n)
+        i, t0 = 0, time.perf_counter()
+        calls = 0
+        while i < n:
+            now = time.perf_counter() - t0
+            if arrivals[i] > now:
+                time.sleep(min(arrivals[i] - now, 0.01))
+                continue
+            j, P = i, 0
+            while j < n and arrivals[j] <= now and (P == 0 or P + windows[which[j]] <= args.serve_batch):
+                P += windows[which[j]]
+                j += 1
+            out = rsc.encode_images(dic, basis, [pool[q] for q in which[i:j]], K, "f16")
+            host = {k: v.cpu() for k, v in out.items()}
+            del host, out
+            done = time.perf_counter() - t0
+            lat[i:j] = done - arrivals[i:j]
+            calls += 1
+            i = j
+        total = sum(windows[q] for q in which)
+        return {"requests": n, "patches": int(total), "calls": calls,
+                "wall_s": done, "patches_per_s": total / done,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+
+    # warm-up
+    serve(np.zeros(4), rng.integers(0, 64, size=4))
+    runs = []
+    nreq = max(16, int(args.serve_requests))
+    which = rng.integers(0, 64, size=nreq)
+    cap = serve(np.zeros(nreq), which)
+    cap["arrivals"] = "all at t = 0 (capacity)"
+    runs.append(cap)
+    mean_windows = float(np.mean(windows))
+    for rate in args.rates:
+        n = max(16, int(rate * args.serve_seconds))
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        r = serve(arr, rng.integers(0, 64, size=n))
+        r["arrivals"] = f"Poisson {rate:g} req/s for {args.serve_seconds:g} s"
+        r["offered_patches_per_s"] = rate * mean_windows
+        runs.append(r)
+    dic.close()
+    basis.close()
+    print(json.dumps({
+        "metric": "request latency p50/p99 and sustained patches/s (serving loop)",
+        "unit": "ms / patches/s", "n_gpus": 1, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": "images side U{128..1024}, 11x11 patches (97 px), J=6, kmax=8, "
+                               "M=128, R=64, K=5; codes copied to the host",
+                   "batch_cap_patches": args.serve_batch},
+        "runs": runs}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,7 +427,18 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--patches", type=int, default=None, help="override P (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the projection and rotational K-SVD measurements")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the request-serving loop instead of the throughput bench")
+    ap.add_argument("--rates", type=float, nargs="*", default=[200.0, 50.0])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-batch", type=int, default=4_000_000)
     args = ap.parse_args()
+    if args.serve:
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -462,6 +633,10 @@ def main():
             line["fp32_path"] = {"value": v32, "unit": "patches/s",
                                  "ms_per_step": cmp_run["total_ms"] / args.steps,
                                  "speedup_of_headline": value / v32}
+        if not args.no_extras and world == 1:
+            line["projection"] = measure_projection(rsc, torch, dev, stream)
+            line["rksvd"] = measure_rksvd(rsc, torch, dev)
+            line["images_c2_sizes"] = measure_images_c2(rsc, torch, dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(d, x, wl)
         print(json.dumps(line))
