@@ -210,6 +210,27 @@ __device__ __forceinline__ float residual_q(uint4 *row, float scale, const float
   return n2;
 }
 
+// Error bound of one fp16 score of a row, times 1.25, without the key term:
+// 2^-10 ||r|| (both operands rounded, unit atoms) + 2^-18 ||r|| (second
+// order) + 112 * 2^-21 ||r|| (the accumulation, at 4x unit roundoff) +
+// 11 * 2^-33 ||r|| and 11 * 2^(e-33) (subnormal rounding of a dictionary
+// entry, <= 2^-25 / kDictScale, and of a row entry, <= 2^-25 / row scale, over
+// sqrt(112) < 11 entries); plus the FP32 residual's own error 2 dr.
+__device__ __forceinline__ float score_err_base(float rnorm, float dr, int e) {
+  return 1.25f * (9.765625e-4f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f +
+                  11.0f * 1.16415321826934814e-10f) *
+             rnorm +
+         1.25f * 11.0f * ldexpf(1.0f, e - 33) + 2.0f * dr;
+}
+
+// The scoring pass's window for a row: 2.02 E in accumulator units
+// (2^(16 - e) times true scores), with the key term 2^-16 s1 bounded through
+// s1 <= 1.01 ||r|| (Cauchy-Schwarz over unit atoms plus the score error).
+__device__ __forceinline__ float score_window(float rnorm, float dr, int e) {
+  return 2.02f * (score_err_base(rnorm, dr, e) + 1.52587890625e-5f * 1.01f * rnorm) *
+         ldexpf(1.0f, 16 - e);
+}
+
 template <int KK>
 __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
   using I = StateIdx<KK>;
@@ -237,6 +258,7 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
     a.sF[I::fX * a.P + p] = xnorm;
     a.sF[I::fR * a.P + p] = rn;
     a.sF[I::fDr * a.P + p] = 2.0f * kU32 * xnorm;
+    a.win[p] = score_window(rn, 2.0f * kU32 * xnorm, e);
     a.status[p] = 1;
   }
 }
@@ -269,18 +291,9 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
     const float disc = a.cand_disc[p] * unscale;
     const float stop_level = 1e-10f * xnorm;
     const float s1 = tv[0];
-    // fp16 error of a score, times 1.25: 2^-10 ||r|| (both operands rounded,
-    // unit atoms) + 2^-18 ||r|| (second order) + 112 * 2^-21 ||r|| (the
-    // accumulation, at 4x unit roundoff) + 11 * 2^-33 ||r|| and 11 * 2^(e-33)
-    // (subnormal rounding of a dictionary entry, <= 2^-25 / kDictScale, and of
-    // a row entry, <= 2^-25 / row scale, over sqrt(112) < 11 entries); plus the
-    // FP32 residual's own error, plus 2^-16 s1 for the low mantissa bits the
-    // scoring kernel replaces by a column index
-    const float E = 1.25f * (9.765625e-4f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f +
-                             11.0f * 1.16415321826934814e-10f) *
-                        rnorm +
-                    1.25f * 11.0f * ldexpf(1.0f, e - 33) + 2.0f * dr +
-                    1.52587890625e-5f * fabsf(s1);
+    // fp16 error of a score (score_err_base) plus 2^-16 s1 for the low
+    // mantissa bits the scoring kernel replaces by a column index
+    const float E = score_err_base(rnorm, dr, e) + 1.52587890625e-5f * fabsf(s1);
     int outcome = 0;  // 0 continue, 1 finished/stopped, 2 hand-off
     bool have_factor = false;
     if (!(s1 + E > stop_level)) {
@@ -385,6 +398,7 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
                                            ldexpf(1.0f, kRowLog2 - en), xp, a.d, HJ, a.n, t, S,
                                            tw, qtab));
               store_state<KK>(a, p, S, t, en, rnorm, dr);
+              a.win[p] = score_window(rnorm, dr, en);
             }
           }
         }

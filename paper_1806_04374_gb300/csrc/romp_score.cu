@@ -14,9 +14,12 @@
 //     f32 out) for both tiles into one of two TMEM accumulator buffers per
 //     tile, and tcgen05.commit's the stage, the buffer and the A tiles back;
 //   * warps 0-7 (one thread per patch, TMEM lane = patch) read each buffer
-//     back with tcgen05.ld and keep the 8 largest block maxima of |score|
+//     back with tcgen05.ld and keep the kTcTop (4) largest block maxima of |score|
 //     (block = 32 rows = 32 atoms at one angle) with their rows, plus the
-//     largest value left out (disc), then hand the buffer back.
+//     largest value left out (disc), then hand the buffer back.  A block whose
+//     maximum is more than the patch's window (>= 2 E, from the refine pass)
+//     below the running best can neither win nor fall inside the final
+//     window, so it is neither kept nor needs its second maximum.
 // All hand-offs are mbarriers; every wait is bounded (2 s of globaltimer) and
 // a failed wait records RSC_ERR_TIMEOUT, stops the CTA's loops, drains the
 // copies and MMAs it issued, and frees its TMEM.
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
     for (int64_t pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
       const int64_t p = (pair * kSTiles + tile) * kSTile + row;
       const bool act = p < a.P && a.status[p] > 0;
+      const float win = act ? a.win[p] : 0.0f;
       float tv[kTop];
       int ti[kTop];
 #pragma unroll
@@ -235,7 +239,9 @@ __global__ void __launch_bounds__(kSThreads, 1)
             float m1 = -1.0f;
 #pragma unroll
             for (int u = 0; u < 32; u += 2) m1 = fmax3(m1, key[u], key[u + 1]);
-            if (m1 >= 0.0f && m1 > tv[kTop - 1]) {
+            // kept: the block maximum beats the last kept one and is not below
+            // the window under the running best (NaN-safe form)
+            if (m1 >= 0.0f && m1 > tv[kTop - 1] && !(m1 < tv[0] - win)) {
               const int us = __float_as_int(m1) & 31;
               float m2 = -1.0f;
 #pragma unroll

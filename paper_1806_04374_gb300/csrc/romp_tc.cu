@@ -17,7 +17,7 @@
 //     loads and the MMAs); each chunk is multiplied into one of two TMEM
 //     accumulator buffers per tile while the other buffer is read back;
 //   * epilogue (c): every thread reads its patch's scores with tcgen05.ld and
-//     keeps the 8 largest block maxima of |score| and the largest value it
+//     keeps the kTcTop (4) largest block maxima of |score| and the largest value it
 //     discarded;
 //   * per patch, every candidate within 2E of the best (E bounds the fp16
 //     error of a score) is re-scored exactly in double-float as

@@ -387,8 +387,8 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   const size_t bA = al256((size_t)P * kTcKst * 2), bCI = al256((size_t)P * kTcTop * 4),
                bCV = bCI, bCD = al256((size_t)P * 4), bSt = bCD, bD = al256((size_t)nD * P * 8),
                bF = al256((size_t)nF * P * 4), bI = al256((size_t)nI * P * 4),
-               bR = al256((size_t)(P + 4) * 4);
-  const size_t total = bA + bCI + bCV + bCD + bSt + bD + bF + bI + bR;
+               bR = al256((size_t)(P + 4) * 4), bW = bCD;
+  const size_t total = bA + bCI + bCV + bCD + bSt + bD + bF + bI + bR + bW;
   unsigned char *scratch = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
   if (e == cudaErrorMemoryAllocation) {
@@ -427,6 +427,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   int *redo = reinterpret_cast<int *>(take(bR));
   ra.redo_count = redo;
   ra.redo_list = redo + 4;
+  ra.win = reinterpret_cast<float *>(take(bW));
   ra.atom = atom;
   ra.angle_idx = angle_idx;
   ra.angle = angle;
@@ -442,6 +443,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   sa.cand_idx = const_cast<int *>(ra.cand_idx);
   sa.cand_val = const_cast<float *>(ra.cand_val);
   sa.cand_disc = const_cast<float *>(ra.cand_disc);
+  sa.win = ra.win;
   sa.err = dict->err;
   CUtensorMap tmA;
   rc = encode_rows_map(&tmA, ra.A, (size_t)P);

@@ -86,7 +86,7 @@ struct TcArgs {
 int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream);
 
 // Block maxima kept per patch and greedy step by the tensor-core scoring.
-constexpr int kTcTop = 8;
+constexpr int kTcTop = 4;
 
 // One scoring pass of the split FP16 path (romp_score.cu): packed fp16
 // residual rows (TMA map tmA: [P][kTcKst]) times the steered dictionary
@@ -99,6 +99,10 @@ struct ScoreArgs {
   int *cand_idx;      // [P][kTcTop]
   float *cand_val;    // [P][kTcTop]
   float *cand_disc;   // [P]
+  // [P] per-patch certification window in accumulator units (written by the
+  // refine pass with the row): a block maximum more than `win` below the
+  // running best can neither win nor reach the window, so it is not kept
+  const float *win;
   int *err;
 };
 int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
@@ -118,6 +122,7 @@ struct RefineArgs {
   const int *cand_idx;
   const float *cand_val;
   const float *cand_disc;
+  float *win;            // [P] window of the next scoring pass (see ScoreArgs)
   int *status;           // 1 active, 0 done, -1 handed to the FP32 path
   double *sD;            // state, structure of arrays
   float *sF;
