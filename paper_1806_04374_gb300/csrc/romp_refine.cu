@@ -123,27 +123,16 @@ __device__ void write_outputs(const RefineArgs &a, int64_t p, const Ls<KK> &S, i
 }
 
 // Shared memory of the init/refine kernels: the steering-factor table
-// [4][H][R], then the packed-slot table qtab[q] = (e << 8) | (k << 1) | c
-// (slot q holds Re (c = 0) or Im (c = 1) of entry e = k*J + j).
+// [4][H][R], then the packed-slot table qtab[q] = rsc_slot_code (slot q holds
+// Re (c = 0) or Im (c = 1) of entry e = k*J + j, or zero for -1) of the
+// plain or paired row layout.
 __device__ __forceinline__ TwS load_tw(const RefineArgs &a, const int *&qtab) {
   extern __shared__ __align__(16) float tws[];
   const int n = 4 * a.H * a.R;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = a.tw[i];
   int *qt = reinterpret_cast<int *>(tws + ((n + 3) & ~3));
-  for (int q = threadIdx.x; q < a.n; q += blockDim.x) {
-    int e, k, c;
-    if (q < a.J) {
-      e = q;
-      k = 0;
-      c = 0;
-    } else {
-      const int qq = q - a.J;
-      e = a.J + (qq >> 1);
-      k = e / a.J;
-      c = qq & 1;
-    }
-    qt[q] = (e << 8) | (k << 1) | c;
-  }
+  for (int q = threadIdx.x; q < kTcKst; q += blockDim.x)
+    qt[q] = rsc_slot_code(q, a.J, a.kmax, a.paired != 0);
   __syncthreads();
   qtab = qt;
   return TwS{tws, a.H, a.R};
@@ -155,7 +144,7 @@ __device__ __forceinline__ TwS load_tw(const RefineArgs &a, const int *&qtab) {
 // computed with its Re slot.  Returns ||r||^2 (unscaled).
 template <int KK>
 __device__ __forceinline__ float residual_q(uint4 *row, float scale, const float *__restrict__ xp,
-                                            const float *__restrict__ d, int HJ, int n, int t,
+                                            const float *__restrict__ d, int HJ, int t,
                                             const Ls<KK> &S, const TwS &tw, const int *qtab) {
   float n2 = 0.0f, pend = 0.0f;
 #pragma unroll 1
@@ -163,10 +152,9 @@ __device__ __forceinline__ float residual_q(uint4 *row, float scale, const float
     float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int q = cq * 8 + u;
+      const int code = qtab[cq * 8 + u];
       float val = 0.0f;
-      if (q < n) {
-        const int code = qtab[q];
+      if (code >= 0) {
         const int e = code >> 8, k = (code >> 1) & 127;
         if (code & 1) {
           val = pend;
@@ -251,7 +239,7 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
     Ls<KK> S;
     const int e = rsc_row_exponent(xnorm);
     const float rn = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes),
-                                          ldexpf(1.0f, kRowLog2 - e), xp, a.d, HJ, a.n, 0, S, tw,
+                                          ldexpf(1.0f, kRowLog2 - e), xp, a.d, HJ, 0, S, tw,
                                           qtab));
     a.sI[I::iT * a.P + p] = 0;
     a.sI[I::iE * a.P + p] = e;
@@ -263,7 +251,7 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
   }
 }
 
-template <int KK>
+template <int KK, bool PAIRED>
 __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a) {
   const int H = a.H, J = a.J, R = a.R, M = a.M, HJ = H * J;
   const int *qtab;
@@ -308,61 +296,103 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
         for (int i = 0; i < KK; ++i)
           if (i < t) asum += fabsf(S.ahi[i]);
         const float E32 = 256.0f * kU32 * (xnorm + asum);
-        float fs[kTop];
+        // a candidate unit is one steered atom (row r*M + m), or in the
+        // paired layout the two angles r and r + R/2 of atom m (row r*M + m,
+        // r < R/2, scored by max(|s(r)|, |s(r + R/2)|))
+        constexpr int NP = PAIRED ? 2 : 1;
+        const int Rh = R / 2;
+        float fs[kTop][NP];
         float fbest = -1.0f;
         int nwin = 0;
 #pragma unroll
         for (int q = 0; q < kTop; ++q) nwin += (ti[q] >= 0 && tv[q] >= thr) ? 1 : 0;
-        // a single candidate in the certified window is the winner: no screen
+        // a single unit in the certified window holds the winner: no screen
 #pragma unroll
         for (int q = 0; q < kTop; ++q) {
-          fs[q] = -1.0f;
+#pragma unroll
+          for (int h = 0; h < NP; ++h) fs[q][h] = -1.0f;
           if (ti[q] >= 0 && tv[q] >= thr) {
             if (nwin > 1) {
               const int m = ti[q] % M, r = ti[q] / M;
-              fs[q] = fabsf(score32<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H, R, m, r,
-                                        t, S, tw));
+              if (PAIRED) {
+                const float2 f = score32_pair<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H,
+                                                  R, m, r, t, S, tw);
+                fs[q][0] = fabsf(f.x);
+                fs[q][NP - 1] = fabsf(f.y);
+              } else {
+                fs[q][0] = fabsf(score32<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H, R,
+                                             m, r, t, S, tw));
+              }
             } else {
-              fs[q] = 0.0f;
+#pragma unroll
+              for (int h = 0; h < NP; ++h) fs[q][h] = 0.0f;
             }
-            fbest = fmaxf(fbest, fs[q]);
+#pragma unroll
+            for (int h = 0; h < NP; ++h) fbest = fmaxf(fbest, fs[q][h]);
           }
         }
         df best = df_make(0.0f), best_ax = df_make(0.0f);
         df bg[KK];
 #pragma unroll
         for (int i = 0; i < KK; ++i) bg[i] = df_make(0.0f);
-        int bc = -1, bflat = 0;
+        int bm = -1, br = 0, bflat = 0;
 #pragma unroll
         for (int q = 0; q < kTop; ++q) {
-          if (fs[q] >= 0.0f && fs[q] >= fbest - 2.0f * E32) {
+          bool live[NP], any = false;
+#pragma unroll
+          for (int h = 0; h < NP; ++h) {
+            live[h] = fs[q][h] >= 0.0f && fs[q][h] >= fbest - 2.0f * E32;
+            any = any || live[h];
+          }
+          if (any) {
             const int m = ti[q] % M, r = ti[q] / M;
-            const df ax = score_x(a.d + (size_t)m * HJ * 2, xp, J, H, r, tw);
-            df sc = ax;
-            df gq[KK];
+            df ax[NP], sc[NP], gq[NP][KK];
+            if (PAIRED) {
+              const DF2 x2 = score_x_pair(a.d + (size_t)m * HJ * 2, xp, J, H, r, tw);
+              ax[0] = x2.a;
+              ax[NP - 1] = x2.b;
+            } else {
+              ax[0] = score_x(a.d + (size_t)m * HJ * 2, xp, J, H, r, tw);
+            }
+#pragma unroll
+            for (int h = 0; h < NP; ++h) sc[h] = ax[h];
 #pragma unroll
             for (int i = 0; i < KK; ++i) {
-              gq[i] = df_make(0.0f);
+#pragma unroll
+              for (int h = 0; h < NP; ++h) gq[h][i] = df_make(0.0f);
               if (i < t) {
-                gq[i] = gram_entry(a.xgram, M, H, R, m, r, S.m[i], S.r[i], tw);
-                sc = df_sub(sc, df_mul(df{S.ahi[i], S.alo[i]}, gq[i]));
+                if (PAIRED) {
+                  const DF2 g2 = gram_entry_pair(a.xgram, M, H, R, m, r, S.m[i], S.r[i], tw);
+                  gq[0][i] = g2.a;
+                  gq[NP - 1][i] = g2.b;
+                } else {
+                  gq[0][i] = gram_entry(a.xgram, M, H, R, m, r, S.m[i], S.r[i], tw);
+                }
+#pragma unroll
+                for (int h = 0; h < NP; ++h)
+                  sc[h] = df_sub(sc[h], df_mul(df{S.ahi[i], S.alo[i]}, gq[h][i]));
               }
             }
-            const int flat = m * R + r;
-            if (bc < 0 || df_abs_gt(sc, best) || (df_abs_eq(sc, best) && flat < bflat)) {
-              best = sc;
-              bc = ti[q];
-              bflat = flat;
-              best_ax = ax;
 #pragma unroll
-              for (int i = 0; i < KK; ++i) bg[i] = gq[i];
+            for (int h = 0; h < NP; ++h) {
+              const int rr = r + h * Rh, flat = m * R + rr;
+              if (live[h] &&
+                  (bm < 0 || df_abs_gt(sc[h], best) || (df_abs_eq(sc[h], best) && flat < bflat))) {
+                best = sc[h];
+                bm = m;
+                br = rr;
+                bflat = flat;
+                best_ax = ax[h];
+#pragma unroll
+                for (int i = 0; i < KK; ++i) bg[i] = gq[h][i];
+              }
             }
           }
         }
-        if (bc < 0 || !(fabsf(best.hi) > stop_level)) {
+        if (bm < 0 || !(fabsf(best.hi) > stop_level)) {
           outcome = 1;
         } else {
-          const int mb = bc % M, rb = bc / M;
+          const int mb = bm, rb = br;
           double gr[KK];
 #pragma unroll
           for (int i = 0; i < KK; ++i) gr[i] = (i < t) ? df_to_d(bg[i]) : 0.0;
@@ -389,13 +419,13 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
             if (t >= a.K) {
               outcome = 1;
               // final residual norm in FP32 (the fp16 row is not needed any more)
-              rnorm = sqrtf(residual_q<KK>(nullptr, 1.0f, xp, a.d, HJ, a.n, t, S, tw, qtab));
+              rnorm = sqrtf(residual_q<KK>(nullptr, 1.0f, xp, a.d, HJ, t, S, tw, qtab));
             } else {
               // the previous residual's norm bounds the new one (least squares
               // over a larger support)
               const int en = rsc_row_exponent(rnorm);
               rnorm = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes),
-                                           ldexpf(1.0f, kRowLog2 - en), xp, a.d, HJ, a.n, t, S,
+                                           ldexpf(1.0f, kRowLog2 - en), xp, a.d, HJ, t, S,
                                            tw, qtab));
               store_state<KK>(a, p, S, t, en, rnorm, dr);
               a.win[p] = score_window(rnorm, dr, en);
@@ -430,11 +460,13 @@ int launch_refine_t(const RefineArgs &a, bool init, cudaStream_t stream) {
   const int64_t blocks = (a.P + 127) / 128;
   const int64_t cap = (int64_t)nsm * 32;
   const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
-  const size_t shm = (size_t)((4 * a.H * a.R + 3) & ~3) * 4 + (size_t)kTcMaxN * 4;
+  const size_t shm = (size_t)((4 * a.H * a.R + 3) & ~3) * 4 + (size_t)kTcKst * 4;
   if (init)
     romp_init_kernel<KK><<<grid, 128, shm, stream>>>(a);
+  else if (a.paired)
+    romp_refine_kernel<KK, true><<<grid, 128, shm, stream>>>(a);
   else
-    romp_refine_kernel<KK><<<grid, 128, shm, stream>>>(a);
+    romp_refine_kernel<KK, false><<<grid, 128, shm, stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return RSC_OK;

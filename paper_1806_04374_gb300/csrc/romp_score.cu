@@ -57,9 +57,13 @@ enum : int {
   kBarCount = 6 + 2 * kSStages,
 };
 
+template <bool PAIRED>
 __global__ void __launch_bounds__(kSThreads, 1)
     romp_score_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const ScoreArgs a) {
+  // B rows per chunk and the byte offset of a chunk's second 64-column block
+  constexpr int BR = PAIRED ? kTcBP : kTcBN;
+  constexpr uint32_t kBBlk = (uint32_t)BR * 128;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr uint32_t kCols = kSTiles * 2 * kTcBN;  // 512
-  constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, kTcBN);
+  constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, PAIRED ? kTcBN / 2 : kTcBN);
 
   if (tid == 0) {
     tc::mbar_init(bar(kBarAFull), 1);
@@ -128,9 +132,9 @@ __global__ void __launch_bounds__(kSThreads, 1)
             break;
           }
           const uint32_t dst = tc::smem_u32(sB + s * kSTileBytes);
-          tc::mbar_arrive_expect_tx(bar(kBarBFull + s), kSTileBytes);
-          tc::tma_load_2d(dst, &tmB, bar(kBarBFull + s), 0, c * kTcBN);
-          tc::tma_load_2d(dst + kSBlk, &tmB, bar(kBarBFull + s), 64, c * kTcBN);
+          tc::mbar_arrive_expect_tx(bar(kBarBFull + s), 2 * kBBlk);
+          tc::tma_load_2d(dst, &tmB, bar(kBarBFull + s), 0, c * BR);
+          tc::tma_load_2d(dst + kBBlk, &tmB, bar(kBarBFull + s), 64, c * BR);
           ++issuedB;
         }
       }
@@ -165,10 +169,21 @@ __global__ void __launch_bounds__(kSThreads, 1)
 #pragma unroll
           for (int t = 0; t < kSTiles; ++t) {
             const uint32_t d = tmem + (uint32_t)(t * 2 + b) * kTcBN;
-            for (int ks = 0; ks < a.ksteps; ++ks) {
-              const uint32_t off = (ks >> 2) * kSBlk + (ks & 3) * 32;
-              tc::mma_f16(d, tc::smem_desc_sw128(a0 + t * kSTileBytes + off),
-                           tc::smem_desc_sw128(b0 + off), kIdesc, ks > 0 ? 1u : 0u);
+            const uint32_t at = a0 + t * kSTileBytes;
+            if (PAIRED) {
+              // even half (A and B block 0) -> columns 0..63, odd half
+              // (block 1) -> columns 64..127 of the buffer
+              for (int ks = 0; ks < a.ke; ++ks)
+                tc::mma_f16(d, tc::smem_desc_sw128(at + ks * 32), tc::smem_desc_sw128(b0 + ks * 32),
+                            kIdesc, ks > 0 ? 1u : 0u);
+              for (int ks = 0; ks < a.ko; ++ks)
+                tc::mma_f16(d + kTcBN / 2, tc::smem_desc_sw128(at + kSBlk + ks * 32),
+                            tc::smem_desc_sw128(b0 + kBBlk + ks * 32), kIdesc, ks > 0 ? 1u : 0u);
+            } else {
+              for (int ks = 0; ks < a.ksteps; ++ks)
+                tc::mma_f16(d, tc::smem_desc_sw128(at + (ks >> 2) * kSBlk + (ks & 3) * 32),
+                            tc::smem_desc_sw128(b0 + (ks >> 2) * kBBlk + (ks & 3) * 32), kIdesc,
+                            ks > 0 ? 1u : 0u);
             }
           }
           tc::mma_commit(bar(kBarBEmpty + s));
@@ -213,19 +228,29 @@ __global__ void __launch_bounds__(kSThreads, 1)
         }
         tc::fence_after_sync();
         const uint32_t taddr = tmem + lane_base + (uint32_t)(tile * 2 + b) * kTcBN;
-        const int nvalid = min(kTcBN, a.MR - c * kTcBN);
+        const int nvalid = min(BR, a.MR - c * BR);
 #pragma unroll 1
-        for (int piece = 0; piece < kTcBN / 32; ++piece) {
+        for (int piece = 0; piece < BR / 32; ++piece) {
           uint32_t v[32];
           tc::tmem_ld32(taddr + piece * 32, v);
-          tc::tmem_wait_ld();
+          if (PAIRED) {
+            // pair value |E| + |O| = max(|score(r)|, |score(r + R/2)|)
+            uint32_t o[32];
+            tc::tmem_ld32(taddr + kTcBN / 2 + piece * 32, o);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 32; ++u)
+              v[u] = __float_as_uint(fabsf(__uint_as_float(v[u])) + fabsf(__uint_as_float(o[u])));
+          } else {
+            tc::tmem_wait_ld();
+          }
           if (act) {
             // keys: |score| with the low 5 mantissa bits replaced by the
             // column within the block; non-negative floats order like their
             // bits, so one max gives the block maximum and its column (the
             // truncation is < 2^-18 relative and covered by the refine's
             // error bound)
-            const int base = c * kTcBN + piece * 32;
+            const int base = c * BR + piece * 32;
             const int nv = nvalid - piece * 32;
             float key[32];
 #pragma unroll
@@ -247,7 +272,17 @@ __global__ void __launch_bounds__(kSThreads, 1)
 #pragma unroll
               for (int u = 0; u < 32; ++u) m2 = fmaxf(m2, key[u] < m1 ? key[u] : -1.0f);
               topn_insert(tv, ti, disc, m1, base + us);
-              disc = fmaxf(disc, m2);
+              if (m2 >= 0.0f && !(m2 < tv[0] - win)) {
+                // the block's second value may lie in the window too: keep it
+                // as a candidate and bound the rest by the third value
+                float m3 = -1.0f;
+#pragma unroll
+                for (int u = 0; u < 32; ++u) m3 = fmaxf(m3, key[u] < m2 ? key[u] : -1.0f);
+                topn_insert(tv, ti, disc, m2, base + (__float_as_int(m2) & 31));
+                disc = fmaxf(disc, m3);
+              } else {
+                disc = fmaxf(disc, m2);
+              }
             } else {
               disc = fmaxf(disc, m1);
             }
@@ -290,11 +325,12 @@ int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorM
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   constexpr SLayout L = s_layout();
   if (L.total > max_optin) return RSC_ERR_UNSUPPORTED;
-  e = cudaFuncSetAttribute(romp_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+  auto kern = a.paired ? romp_score_kernel<true> : romp_score_kernel<false>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   const int64_t pairs = (a.P + kSTiles * kSTile - 1) / (kSTiles * kSTile);
   const int64_t grid = pairs < nsm ? pairs : nsm;
-  romp_score_kernel<<<(unsigned)grid, kSThreads, L.total, stream>>>(tmA, tmB, a);
+  kern<<<(unsigned)grid, kSThreads, L.total, stream>>>(tmA, tmB, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return RSC_OK;

@@ -74,6 +74,7 @@ void free_dict(rsc_dict *d) {
   cudaFree(d->err);
   cudaFree(d->fallbacks);
   cudaFree(d->steered_f16);
+  cudaFree(d->paired_f16);
   cudaFree(d->xgram);
   cudaFree(d->anorm);
   delete d;
@@ -90,9 +91,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// TMA map of a row-major fp16 matrix [rows][kTcKst]: box 64 columns x kTcBN
-// rows, 128-byte swizzle, zero fill outside (columns kTcKst..127, rows >= rows).
-int encode_rows_map(CUtensorMap *map, void *base, size_t rows) {
+// TMA map of a row-major fp16 matrix [rows][kTcKst]: box 64 columns x
+// box_rows rows, 128-byte swizzle, zero fill outside (columns kTcKst..127,
+// rows >= rows).
+int encode_rows_map(CUtensorMap *map, void *base, size_t rows, int box_rows) {
   static EncodeTiledFn fn = nullptr;
   static cudaError_t fn_err = cudaSuccess;
   static std::once_flag once;
@@ -106,7 +108,7 @@ int encode_rows_map(CUtensorMap *map, void *base, size_t rows) {
   if (!fn) return rsc_cuda_fail(fn_err != cudaSuccess ? fn_err : cudaErrorNotSupported);
   const cuuint64_t gdim[2] = {(cuuint64_t)kTcKst, (cuuint64_t)rows};
   const cuuint64_t gstride[1] = {(cuuint64_t)kTcKst * 2};
-  const cuuint32_t box[2] = {64, (cuuint32_t)kTcBN};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult cr = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, gdim, gstride, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -131,27 +133,34 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   if (n > kTcMaxN || rows * kTcKst * 2 > ((size_t)1 << 30) ||
       (size_t)M * M * H * 16 > ((size_t)1 << 28))
     return RSC_OK;
+  // packed steered rows: slot q of row (r, m) from rsc_slot_code
+  auto fill_row = [&](uint16_t *row, int m, int r, bool paired) {
+    for (int q = 0; q < kTcKst; ++q) {
+      const int code = rsc_slot_code(q, J, d->kmax, paired);
+      if (code < 0) continue;
+      const int e = code >> 8, k = (code >> 1) & 127, c = code & 1;
+      const double th = 2.0 * M_PI * (double)(((int64_t)k * r) % R) / (double)R;
+      const double co = cos(th), si = sin(th);
+      const double dre = h[((size_t)m * HJ + e) * 2];
+      const double dim = k ? h[((size_t)m * HJ + e) * 2 + 1] : 0.0;
+      const double re = co * dre + si * dim, im = co * dim - si * dre;  // e^{-ik theta} d
+      row[q] = f16_bits(k == 0 ? re : M_SQRT2 * (c ? im : re));
+    }
+  };
   std::vector<uint16_t> B(rows * kTcKst, 0);
   for (int m = 0; m < M; ++m)
-    for (int r = 0; r < R; ++r) {
-      uint16_t *row = &B[((size_t)r * M + m) * kTcKst];  // angle-major rows
-      for (int k = 0; k < H; ++k) {
-        const double th = 2.0 * M_PI * (double)(((int64_t)k * r) % R) / (double)R;
-        const double c = cos(th), s = sin(th);
-        for (int j = 0; j < J; ++j) {
-          const double dre = h[((size_t)m * HJ + k * J + j) * 2];
-          const double dim = k ? h[((size_t)m * HJ + k * J + j) * 2 + 1] : 0.0;
-          const double re = c * dre + s * dim, im = c * dim - s * dre;
-          if (k == 0) {
-            row[j] = f16_bits(re);
-          } else {
-            const int q = J + 2 * ((k - 1) * J + j);
-            row[q] = f16_bits(M_SQRT2 * re);
-            row[q + 1] = f16_bits(M_SQRT2 * im);
-          }
-        }
-      }
-    }
+    for (int r = 0; r < R; ++r) fill_row(&B[((size_t)r * M + m) * kTcKst], m, r, false);
+  const bool paired = rsc_paired_ok(J, d->kmax, R);
+  std::vector<uint16_t> BP;
+  if (paired) {
+    int ne, no;
+    rsc_paired_counts(J, d->kmax, &ne, &no);
+    d->ke = (ne + 15) / 16;
+    d->ko = (no + 15) / 16;
+    BP.assign(rows / 2 * kTcKst, 0);
+    for (int m = 0; m < M; ++m)
+      for (int r = 0; r < R / 2; ++r) fill_row(&BP[((size_t)r * M + m) * kTcKst], m, r, true);
+  }
   std::vector<float4> X((size_t)M * M * H);
   for (int ma = 0; ma < M; ++ma)
     for (int mb = 0; mb < M; ++mb)
@@ -182,6 +191,7 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
     NA[m] = make_float2(hi, (float)(n2 - (double)hi));
   }
   cudaError_t e = cudaMalloc(&d->steered_f16, B.size() * 2);
+  if (e == cudaSuccess && paired) e = cudaMalloc(&d->paired_f16, BP.size() * 2);
   if (e == cudaSuccess) e = cudaMalloc(&d->xgram, X.size() * sizeof(float4));
   if (e == cudaSuccess) e = cudaMalloc(&d->anorm, NA.size() * sizeof(float2));
   if (e == cudaErrorMemoryAllocation) {
@@ -190,6 +200,8 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d->steered_f16, B.data(), B.size() * 2, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && paired)
+    e = cudaMemcpyAsync(d->paired_f16, BP.data(), BP.size() * 2, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d->xgram, X.data(), X.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -198,7 +210,9 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
 
-  return encode_rows_map(&d->tmap_b, d->steered_f16, rows);
+  int rc = encode_rows_map(&d->tmap_b, d->steered_f16, rows, kTcBN);
+  if (rc == RSC_OK && paired) rc = encode_rows_map(&d->tmap_bp, d->paired_f16, rows / 2, kTcBP);
+  return rc;
 }
 
 int check_device(const rsc_dict *d) {
@@ -428,6 +442,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   ra.redo_count = redo;
   ra.redo_list = redo + 4;
   ra.win = reinterpret_cast<float *>(take(bW));
+  ra.paired = dict->paired_f16 != nullptr ? 1 : 0;
   ra.atom = atom;
   ra.angle_idx = angle_idx;
   ra.angle = angle;
@@ -437,8 +452,11 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   ScoreArgs sa;
   sa.P = P;
   sa.ksteps = (dict->n + 15) / 16;
-  sa.MR = dict->M * dict->R;
-  sa.nchunks = (sa.MR + kTcBN - 1) / kTcBN;
+  sa.paired = ra.paired;
+  sa.ke = dict->ke;
+  sa.ko = dict->ko;
+  sa.MR = sa.paired ? dict->M * (dict->R / 2) : dict->M * dict->R;
+  sa.nchunks = sa.paired ? (sa.MR + kTcBP - 1) / kTcBP : (sa.MR + kTcBN - 1) / kTcBN;
   sa.status = ra.status;
   sa.cand_idx = const_cast<int *>(ra.cand_idx);
   sa.cand_val = const_cast<float *>(ra.cand_val);
@@ -446,7 +464,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   sa.win = ra.win;
   sa.err = dict->err;
   CUtensorMap tmA;
-  rc = encode_rows_map(&tmA, ra.A, (size_t)P);
+  rc = encode_rows_map(&tmA, ra.A, (size_t)P, kTcBN);
   if (rc == RSC_OK) {
     e = cudaMemsetAsync(redo, 0, sizeof(int), st);
     if (e != cudaSuccess) rc = rsc_cuda_fail(e);
@@ -458,7 +476,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   }
   for (int step = 0; step < K && rc == RSC_OK; ++step) {
     int slot = timing_begin(dict, 0, st);
-    rc = rsc_launch_score(sa, tmA, dict->tmap_b, st);
+    rc = rsc_launch_score(sa, tmA, sa.paired ? dict->tmap_bp : dict->tmap_b, st);
     timing_end(dict, slot, st);
     if (rc != RSC_OK) break;
     slot = timing_begin(dict, 2, st);

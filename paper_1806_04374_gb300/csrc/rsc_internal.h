@@ -29,6 +29,10 @@ struct rsc_dict {
   // tensor-core path: steered dictionary and cross-Gram table (null when the
   // sizes are outside what the path handles)
   void *steered_f16;     // [R*M][kTcKst] fp16 of kDictScale x packed S_r d_m (row r*M + m)
+  // paired layout (even R): rows r*M + m for r < R/2, slots split by the
+  // parity of k (rsc_slot_code); null when the sizes do not allow it
+  void *paired_f16;
+  int ke, ko;            // paired: MMA K-steps (16 slots) of the even / odd halves
   float4 *xgram;         // [M][M][H] double-float complex H_k(a,b) = sum_j conj(d_a) d_b
   float2 *anorm;         // [M] ||d_m||^2 in double-float
   int n;                 // packed real length J (2 kmax + 1)
@@ -36,6 +40,7 @@ struct rsc_dict {
   int timing;
   void *timing_state;    // owned std::vector of recorded pairs, see rsc_capi.cu
   CUtensorMap tmap_b;    // TMA map of steered_f16, box 64 x kTcBN, 128B swizzle
+  CUtensorMap tmap_bp;   // TMA map of paired_f16, box 64 x kTcBP, 128B swizzle
 };
 
 // Packed real coordinates of a half spectrum, shared by the tensor-core
@@ -43,9 +48,56 @@ struct rsc_dict {
 // sqrt(2) Re (c = 0) or sqrt(2) Im (c = 1) of c[j, k], k >= 1.  The Euclidean
 // dot product of two packed vectors is the coefficient inner product.
 constexpr int kTcKst = 112;  // stored row length of the steered dictionary (fp16)
+constexpr int kTcOdd = 64;   // first slot of the odd harmonics in the paired layout
 constexpr int kTcMaxN = 112; // packed lengths the tensor-core path handles
 constexpr int kTcBN = 128;   // steered atoms per MMA (N) and per TMA box
 constexpr int kTcMaxK = 8;   // greedy steps the tensor-core path handles
+
+constexpr int kTcBP = 64;   // steered-atom pairs per MMA chunk, paired layout
+
+// Slot layouts of a packed row (kTcKst fp16 slots) of the tensor-core path;
+// returns (e << 8) | (k << 1) | c for slot q holding Re (c = 0) or Im (c = 1)
+// of entry e = k J + j (weight sqrt(2) for k >= 1), or -1 for a zero slot.
+// Plain: the order described above, zeros from slot n.  Paired: the even
+// harmonics (k = 0, then k = 2, 4, ... in (Re, Im) pairs) from slot 0 and
+// the odd harmonics (k = 1, 3, ...) from slot kTcOdd.  Steering by half a
+// turn multiplies harmonic k by (-1)^k (Eq. (Sr)), so with E and O the even
+// and odd parts of <S_r d, x>, <S_{r + R/2} d, x> = E - O and
+// max(|E + O|, |E - O|) = |E| + |O|: one contraction scores both angles.
+__host__ __device__ inline int rsc_paired_counts(int J, int kmax, int *ne, int *no) {
+  *ne = J + 2 * J * (kmax / 2);
+  *no = 2 * J * ((kmax + 1) / 2);
+  return 0;
+}
+__host__ __device__ inline bool rsc_paired_ok(int J, int kmax, int R) {
+  int ne, no;
+  rsc_paired_counts(J, kmax, &ne, &no);
+  return R >= 2 && (R % 2) == 0 && kmax >= 1 && ne <= kTcOdd && no <= kTcKst - kTcOdd;
+}
+__host__ __device__ inline int rsc_slot_code(int q, int J, int kmax, bool paired) {
+  if (!paired) {
+    const int n = J + 2 * kmax * J;
+    if (q < J) return q << 8;
+    if (q >= n) return -1;
+    const int qq = q - J, e = J + (qq >> 1);
+    return (e << 8) | ((e / J) << 1) | (qq & 1);
+  }
+  int ne, no;
+  rsc_paired_counts(J, kmax, &ne, &no);
+  if (q < J) return q << 8;
+  int qq, k0;
+  if (q < ne) {
+    qq = q - J;
+    k0 = 2;
+  } else if (q >= kTcOdd && q < kTcOdd + no) {
+    qq = q - kTcOdd;
+    k0 = 1;
+  } else {
+    return -1;
+  }
+  const int idx = qq >> 1, k = k0 + 2 * (idx / J), e = k * J + idx % J;
+  return (e << 8) | (k << 1) | (qq & 1);
+}
 
 // fp16 operand scaling of the tensor-core path.  The steered dictionary holds
 // kDictScale * entries (unit atoms: |entries| <= 256); a residual row is
@@ -95,6 +147,9 @@ constexpr int kTcTop = 4;
 struct ScoreArgs {
   int64_t P;
   int ksteps, MR, nchunks;
+  // paired layout (rsc_slot_code): B rows are steered-atom pairs (r < R/2),
+  // MR counts pairs, and the MMAs run ke / ko K-steps on the even / odd halves
+  int paired, ke, ko;
   const int *status;  // > 0: patch still being coded
   int *cand_idx;      // [P][kTcTop]
   float *cand_val;    // [P][kTcTop]
@@ -123,6 +178,7 @@ struct RefineArgs {
   const float *cand_val;
   const float *cand_disc;
   float *win;            // [P] window of the next scoring pass (see ScoreArgs)
+  int paired;            // rows and candidates in the paired layout (rsc_slot_code)
   int *status;           // 1 active, 0 done, -1 handed to the FP32 path
   double *sD;            // state, structure of arrays
   float *sF;

@@ -171,6 +171,105 @@ __device__ df gram_entry(const float4 *__restrict__ xg, int M, int H, int R, int
   return acc;
 }
 
+// Paired forms (even R): the same quantities for the two angles r and
+// r + R/2 at once.  Half a turn multiplies harmonic k by (-1)^k (Eq. (Sr)), so
+// with the even-k and odd-k parts of a sum, value(r) = even + odd and
+// value(r + R/2) = even - odd.
+struct DF2 {
+  df a, b;
+};
+
+// score32 for (m, r) and (m, r + R/2).
+template <int KK>
+__device__ float2 score32_pair(const float *__restrict__ dm, const float *__restrict__ xp,
+                               const float4 *__restrict__ xg, int M, int J, int H, int R, int m,
+                               int r, int t, const Ls<KK> &S, const TwS &tw) {
+  float ev = 0.0f, od = 0.0f;
+  for (int k = 0; k < H; ++k) {
+    float qr = 0.f, qi = 0.f;
+    const float2 *d2 = reinterpret_cast<const float2 *>(dm) + k * J;
+    const float2 *x2 = reinterpret_cast<const float2 *>(xp) + k * J;
+    for (int j = 0; j < J; ++j) {
+      const float2 dv = __ldg(d2 + j), xv = __ldg(x2 + j);
+      const float dim = k ? dv.y : 0.0f, xim = k ? xv.y : 0.0f;
+      qr = fmaf(dv.x, xv.x, fmaf(dim, xim, qr));
+      qi = fmaf(dv.x, xim, fmaf(-dim, xv.x, qi));
+    }
+    const float term = fmaf(tw.cos32(k, r), qr, -tw.sin32(k, r) * qi);
+    if (k & 1)
+      od = fmaf(2.0f, term, od);
+    else
+      ev = fmaf(k ? 2.0f : 1.0f, term, ev);
+  }
+  float sa = ev + od, sb = ev - od;
+#pragma unroll
+  for (int i = 0; i < KK; ++i) {
+    if (i < t) {
+      int dr = r - S.r[i];
+      if (dr < 0) dr += R;
+      const float4 *h = xg + ((size_t)m * M + S.m[i]) * H;
+      float ge = 0.0f, go = 0.0f;
+      for (int k = 0; k < H; ++k) {
+        const float4 v = __ldg(h + k);
+        const float term = fmaf(tw.cos32(k, dr), v.x, -tw.sin32(k, dr) * v.z);
+        if (k & 1)
+          go = fmaf(2.0f, term, go);
+        else
+          ge = fmaf(k ? 2.0f : 1.0f, term, ge);
+      }
+      sa = fmaf(-S.ahi[i], ge + go, sa);
+      sb = fmaf(-S.ahi[i], ge - go, sb);
+    }
+  }
+  return make_float2(sa, sb);
+}
+
+// score_x for (m, r) and (m, r + R/2), double-float.
+__device__ DF2 score_x_pair(const float *__restrict__ dm, const float *__restrict__ xp, int J,
+                            int H, int r, const TwS &tw) {
+  df ev = df_make(0.0f), od = df_make(0.0f);
+  for (int k = 0; k < H; ++k) {
+    float qr = 0.f, qrc = 0.f, qi = 0.f, qic = 0.f;
+    const float2 *d2 = reinterpret_cast<const float2 *>(dm) + k * J;
+    const float2 *x2 = reinterpret_cast<const float2 *>(xp) + k * J;
+    for (int j = 0; j < J; ++j) {
+      const float2 dv = __ldg(d2 + j);
+      const float2 xv = __ldg(x2 + j);
+      const float dim = k ? dv.y : 0.0f, xim = k ? xv.y : 0.0f;
+      dot2_acc(qr, qrc, dv.x, xv.x);
+      dot2_acc(qr, qrc, dim, xim);
+      dot2_acc(qi, qic, dv.x, xim);
+      dot2_acc(qi, qic, -dim, xv.x);
+    }
+    const df Qr = fast_two_sum(qr, qrc), Qi = fast_two_sum(qi, qic);
+    const df term = df_sub(df_mul(tw.cosv(k, r), Qr), df_mul(tw.sinv(k, r), Qi));
+    if (k & 1)
+      od = df_add(od, df_mul_f(term, 2.0f));
+    else
+      ev = df_add(ev, k ? df_mul_f(term, 2.0f) : term);
+  }
+  return DF2{df_add(ev, od), df_sub(ev, od)};
+}
+
+// gram_entry for (ma, ra) and (ma, ra + R/2) against (mb, rb), double-float.
+__device__ DF2 gram_entry_pair(const float4 *__restrict__ xg, int M, int H, int R, int ma, int ra,
+                               int mb, int rb, const TwS &tw) {
+  int dr = ra - rb;
+  if (dr < 0) dr += R;
+  const float4 *h = xg + ((size_t)ma * M + mb) * H;
+  df ev = df_make(0.0f), od = df_make(0.0f);
+  for (int k = 0; k < H; ++k) {
+    const float4 v = __ldg(h + k);
+    const df term =
+        df_sub(df_mul(tw.cosv(k, dr), df{v.x, v.y}), df_mul(tw.sinv(k, dr), df{v.z, v.w}));
+    if (k & 1)
+      od = df_add(od, df_mul_f(term, 2.0f));
+    else
+      ev = df_add(ev, k ? df_mul_f(term, 2.0f) : term);
+  }
+  return DF2{df_add(ev, od), df_sub(ev, od)};
+}
+
 // New Cholesky row TT (compile-time) and the solve of all TT+1 weights, FP64.
 template <int KK, int TT>
 __device__ __forceinline__ bool chol_add(Ls<KK> &S, const double (&g)[KK], double diag,
