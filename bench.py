@@ -45,10 +45,17 @@ def algorithmic_flops_per_patch(wl) -> dict:
 
 
 def mma_flops_per_patch(wl) -> int:
-    """Dense flops the tensor-core path executes per patch: K steps x
-    2 x (padded depth 112) x (M R steered atoms)."""
+    """Dense flops the tensor-core path executes per patch.  Plain layout:
+    K steps x 2 x (depth rounded up to 16) x (M R steered atoms).  Paired
+    layout (even R, even harmonics in <= 64 slots, odd ones in <= 48): the
+    even and odd halves, each rounded up to 16, against M R / 2 atom pairs."""
+    ne = wl.J + 2 * wl.J * (wl.kmax // 2)
+    no = 2 * wl.J * ((wl.kmax + 1) // 2)
+    up = lambda v: ((v + 15) // 16) * 16  # noqa: E731
+    if wl.R % 2 == 0 and wl.kmax >= 1 and ne <= 64 and no <= 48:
+        return wl.K * 2 * (up(ne) + up(no)) * wl.M * (wl.R // 2)
     n = wl.J * (2 * wl.kmax + 1)
-    return wl.K * 2 * (((n + 15) // 16) * 16) * wl.M * wl.R
+    return wl.K * 2 * up(n) * wl.M * wl.R
 
 
 def algorithmic_bytes_per_patch(wl) -> int:
