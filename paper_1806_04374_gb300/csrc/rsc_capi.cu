@@ -222,6 +222,118 @@ int check_device(const rsc_dict *d) {
   return dev == d->device ? RSC_OK : RSC_ERR_INVALID;
 }
 
+// Patches per group below which rsc_encode does not split the FP16 path.
+constexpr int64_t kGroupMin = 65536;
+
+// Scratch of the FP16 path for P patches and K steps (256-byte aligned parts).
+size_t f16_scratch_bytes(int64_t P, int K) {
+  int nD = 0, nF = 0, nI = 0;
+  rsc_state_layout(K, &nD, &nF, &nI);
+  auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  return al256((size_t)P * kTcKst * 2) + 2 * al256((size_t)P * kTcTop * 4) +
+         3 * al256((size_t)P * 4) + al256((size_t)nD * P * 8) + al256((size_t)nF * P * 4) +
+         al256((size_t)nI * P * 4) + al256((size_t)(P + 4) * 4);
+}
+
+// Enqueues the FP16 path for the patches of `a` on `st`: init, K x (scoring,
+// refine), then the FP32 hand-off of the patches the path gives back, with the
+// scratch (f16_scratch_bytes) at `scratch`.
+int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *scratch,
+                     cudaStream_t st) {
+  const int64_t P = base.P;
+  const int K = base.K;
+  if (P == 0) return RSC_OK;
+  int nD = 0, nF = 0, nI = 0;
+  const int cap = rsc_state_layout(K, &nD, &nF, &nI);
+  auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  unsigned char *q = scratch;
+  auto take = [&](size_t b) {
+    unsigned char *r = q;
+    q += al256(b);
+    return r;
+  };
+  RefineArgs ra;
+  ra.x = base.x;
+  ra.P = P;
+  ra.K = K;
+  ra.M = dict->M;
+  ra.J = dict->J;
+  ra.kmax = dict->kmax;
+  ra.R = dict->R;
+  ra.H = dict->H;
+  ra.n = dict->n;
+  ra.d = dict->d;
+  ra.tw = dict->tw;
+  ra.xgram = dict->xgram;
+  ra.anorm = dict->anorm;
+  ra.A = take((size_t)P * kTcKst * 2);
+  ra.cand_idx = reinterpret_cast<int *>(take((size_t)P * kTcTop * 4));
+  ra.cand_val = reinterpret_cast<float *>(take((size_t)P * kTcTop * 4));
+  ra.cand_disc = reinterpret_cast<float *>(take((size_t)P * 4));
+  ra.status = reinterpret_cast<int *>(take((size_t)P * 4));
+  ra.win = reinterpret_cast<float *>(take((size_t)P * 4));
+  ra.sD = reinterpret_cast<double *>(take((size_t)nD * P * 8));
+  ra.sF = reinterpret_cast<float *>(take((size_t)nF * P * 4));
+  ra.sI = reinterpret_cast<int *>(take((size_t)nI * P * 4));
+  int *redo = reinterpret_cast<int *>(take((size_t)(P + 4) * 4));
+  ra.redo_count = redo;
+  ra.redo_list = redo + 4;
+  ra.paired = dict->paired_f16 != nullptr ? 1 : 0;
+  ra.atom = base.atom;
+  ra.angle_idx = base.angle_idx;
+  ra.angle = base.angle;
+  ra.coef = base.coef;
+  ra.resid_norm2 = base.resid_norm2;
+  ra.fallbacks = dict->fallbacks;
+  ScoreArgs sa;
+  sa.P = P;
+  sa.ksteps = (dict->n + 15) / 16;
+  sa.paired = ra.paired;
+  sa.ke = dict->ke;
+  sa.ko = dict->ko;
+  sa.MR = sa.paired ? dict->M * (dict->R / 2) : dict->M * dict->R;
+  sa.nchunks = sa.paired ? (sa.MR + kTcBP - 1) / kTcBP : (sa.MR + kTcBN - 1) / kTcBN;
+  sa.status = ra.status;
+  sa.cand_idx = const_cast<int *>(ra.cand_idx);
+  sa.cand_val = const_cast<float *>(ra.cand_val);
+  sa.cand_disc = const_cast<float *>(ra.cand_disc);
+  sa.win = ra.win;
+  sa.err = dict->err;
+  CUtensorMap tmA;
+  int rc = encode_rows_map(&tmA, ra.A, (size_t)P, kTcBN);
+  if (rc == RSC_OK) {
+    const cudaError_t e = cudaMemsetAsync(redo, 0, sizeof(int), st);
+    if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+  }
+  if (rc == RSC_OK) {
+    const int slot = timing_begin(dict, 2, st);
+    rc = rsc_launch_refine(ra, true, st);
+    timing_end(dict, slot, st);
+  }
+  for (int step = 0; step < K && rc == RSC_OK; ++step) {
+    int slot = timing_begin(dict, 0, st);
+    rc = rsc_launch_score(sa, tmA, sa.paired ? dict->tmap_bp : dict->tmap_b, st);
+    timing_end(dict, slot, st);
+    if (rc != RSC_OK) break;
+    slot = timing_begin(dict, 2, st);
+    rc = rsc_launch_refine(ra, false, st);
+    timing_end(dict, slot, st);
+  }
+  if (rc == RSC_OK) {
+    RompArgs a = base;
+    a.redo_count = ra.redo_count;
+    a.redo_list = ra.redo_list;
+    a.resume_sI = ra.sI;
+    a.resume_P = P;
+    a.resume_cap = cap;
+    a.fallbacks = nullptr;
+    const int slot = timing_begin(dict, 1, st);
+    rc = rsc_launch_f32(a, st);
+    timing_end(dict, slot, st);
+  }
+  return rc;
+}
+
 }  // namespace
 
 int rsc_cuda_fail(cudaError_t e) {
@@ -395,104 +507,54 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   // FP16 tensor-core path, split per greedy step into a scoring kernel and a
   // per-patch refine kernel; patches it hands back are coded by the FP32 path
   if (!dict->steered_f16 || K > kTcMaxK || P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
-  int nD = 0, nF = 0, nI = 0;
-  const int cap = rsc_state_layout(K, &nD, &nF, &nI);
-  auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t bA = al256((size_t)P * kTcKst * 2), bCI = al256((size_t)P * kTcTop * 4),
-               bCV = bCI, bCD = al256((size_t)P * 4), bSt = bCD, bD = al256((size_t)nD * P * 8),
-               bF = al256((size_t)nF * P * 4), bI = al256((size_t)nI * P * 4),
-               bR = al256((size_t)(P + 4) * 4), bW = bCD;
-  const size_t total = bA + bCI + bCV + bCD + bSt + bD + bF + bI + bR + bW;
+  // Two independent halves on two streams: the scoring pass of one half
+  // (tensor and ALU pipes, one CTA per SM) runs beside the refine pass of the
+  // other (latency-bound), so each hides part of the other.
+  const int G = P >= 2 * kGroupMin ? 2 : 1;
+  int64_t Pg[2] = {P, 0};
+  if (G == 2) {
+    Pg[0] = (P / 2 + 255) & ~(int64_t)255;
+    Pg[1] = P - Pg[0];
+  }
+  size_t bytes[2] = {f16_scratch_bytes(Pg[0], K), G == 2 ? f16_scratch_bytes(Pg[1], K) : 0};
   unsigned char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bytes[0] + bytes[1], st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
   }
   if (e != cudaSuccess) return rsc_cuda_fail(e);
-  unsigned char *q = scratch;
-  auto take = [&](size_t b) {
-    unsigned char *r = q;
-    q += b;
-    return r;
-  };
-  RefineArgs ra;
-  ra.x = x;
-  ra.P = P;
-  ra.K = K;
-  ra.M = dict->M;
-  ra.J = dict->J;
-  ra.kmax = dict->kmax;
-  ra.R = dict->R;
-  ra.H = dict->H;
-  ra.n = dict->n;
-  ra.d = dict->d;
-  ra.tw = dict->tw;
-  ra.xgram = dict->xgram;
-  ra.anorm = dict->anorm;
-  ra.A = take(bA);
-  ra.cand_idx = reinterpret_cast<int *>(take(bCI));
-  ra.cand_val = reinterpret_cast<float *>(take(bCV));
-  ra.cand_disc = reinterpret_cast<float *>(take(bCD));
-  ra.status = reinterpret_cast<int *>(take(bSt));
-  ra.sD = reinterpret_cast<double *>(take(bD));
-  ra.sF = reinterpret_cast<float *>(take(bF));
-  ra.sI = reinterpret_cast<int *>(take(bI));
-  int *redo = reinterpret_cast<int *>(take(bR));
-  ra.redo_count = redo;
-  ra.redo_list = redo + 4;
-  ra.win = reinterpret_cast<float *>(take(bW));
-  ra.paired = dict->paired_f16 != nullptr ? 1 : 0;
-  ra.atom = atom;
-  ra.angle_idx = angle_idx;
-  ra.angle = angle;
-  ra.coef = coef;
-  ra.resid_norm2 = resid_norm2;
-  ra.fallbacks = dict->fallbacks;
-  ScoreArgs sa;
-  sa.P = P;
-  sa.ksteps = (dict->n + 15) / 16;
-  sa.paired = ra.paired;
-  sa.ke = dict->ke;
-  sa.ko = dict->ko;
-  sa.MR = sa.paired ? dict->M * (dict->R / 2) : dict->M * dict->R;
-  sa.nchunks = sa.paired ? (sa.MR + kTcBP - 1) / kTcBP : (sa.MR + kTcBN - 1) / kTcBN;
-  sa.status = ra.status;
-  sa.cand_idx = const_cast<int *>(ra.cand_idx);
-  sa.cand_val = const_cast<float *>(ra.cand_val);
-  sa.cand_disc = const_cast<float *>(ra.cand_disc);
-  sa.win = ra.win;
-  sa.err = dict->err;
-  CUtensorMap tmA;
-  rc = encode_rows_map(&tmA, ra.A, (size_t)P, kTcBN);
-  if (rc == RSC_OK) {
-    e = cudaMemsetAsync(redo, 0, sizeof(int), st);
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (G == 2) {
+    e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st2, fork, 0);
     if (e != cudaSuccess) rc = rsc_cuda_fail(e);
   }
-  if (rc == RSC_OK) {
-    const int slot = timing_begin(dict, 2, st);
-    rc = rsc_launch_refine(ra, true, st);
-    timing_end(dict, slot, st);
+  int64_t off = 0;
+  for (int g = 0; g < G && rc == RSC_OK; ++g) {
+    RompArgs ag = a;
+    ag.x = x + off * dict->H * dict->J * 2;
+    ag.P = Pg[g];
+    ag.atom = atom + off * K;
+    ag.angle_idx = angle_idx + off * K;
+    ag.angle = angle ? angle + off * K : nullptr;
+    ag.coef = coef + off * K;
+    ag.resid_norm2 = resid_norm2 ? resid_norm2 + off : nullptr;
+    rc = encode_f16_group(dict, ag, scratch + (g ? bytes[0] : 0), g ? st2 : st);
+    off += Pg[g];
   }
-  for (int step = 0; step < K && rc == RSC_OK; ++step) {
-    int slot = timing_begin(dict, 0, st);
-    rc = rsc_launch_score(sa, tmA, sa.paired ? dict->tmap_bp : dict->tmap_b, st);
-    timing_end(dict, slot, st);
-    if (rc != RSC_OK) break;
-    slot = timing_begin(dict, 2, st);
-    rc = rsc_launch_refine(ra, false, st);
-    timing_end(dict, slot, st);
-  }
-  if (rc == RSC_OK) {
-    a.redo_count = ra.redo_count;
-    a.redo_list = ra.redo_list;
-    a.resume_sI = ra.sI;
-    a.resume_P = P;
-    a.resume_cap = cap;
-    a.fallbacks = nullptr;
-    const int slot = timing_begin(dict, 1, st);
-    rc = rsc_launch_f32(a, st);
-    timing_end(dict, slot, st);
+  if (G == 2) {
+    // join (also after a failed launch, so that the scratch is released last)
+    e = cudaEventRecord(join, st2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
+    if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (st2) cudaStreamDestroy(st2);
   }
   e = cudaFreeAsync(scratch, st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
