@@ -12,8 +12,7 @@
 //     error); every row with |score| >= s1 - 2E is in the list unless the
 //     largest value left out (disc) is >= s1 - 2E, in which case the patch is
 //     handed to the FP32 path;
-//   * screens the candidates with an FP32 score whose error is bounded, and
-//     re-scores the survivors exactly in double-float as
+//   * re-scores every candidate in the window exactly in double-float as
 //     <A_c, x> - sum_i a_i <A_c, A_i> (ties: smallest m*R + r);
 //   * adds the Cholesky row of the winner (Gram entries and right-hand side
 //     in double-float, factor and solve in FP64) and writes the new residual.
@@ -291,46 +290,13 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
       if (disc >= thr) {
         outcome = 2;
       } else {
-        float asum = 0.0f;
-#pragma unroll
-        for (int i = 0; i < KK; ++i)
-          if (i < t) asum += fabsf(S.ahi[i]);
-        const float E32 = 256.0f * kU32 * (xnorm + asum);
         // a candidate unit is one steered atom (row r*M + m), or in the
         // paired layout the two angles r and r + R/2 of atom m (row r*M + m,
-        // r < R/2, scored by max(|s(r)|, |s(r + R/2)|))
+        // r < R/2, scored by max(|s(r)|, |s(r + R/2)|)); every unit in the
+        // certified window is re-scored exactly (the window holds 1.1 units
+        // on average, so no cheaper screen pays for its divergence)
         constexpr int NP = PAIRED ? 2 : 1;
         const int Rh = R / 2;
-        float fs[kTop][NP];
-        float fbest = -1.0f;
-        int nwin = 0;
-#pragma unroll
-        for (int q = 0; q < kTop; ++q) nwin += (ti[q] >= 0 && tv[q] >= thr) ? 1 : 0;
-        // a single unit in the certified window holds the winner: no screen
-#pragma unroll
-        for (int q = 0; q < kTop; ++q) {
-#pragma unroll
-          for (int h = 0; h < NP; ++h) fs[q][h] = -1.0f;
-          if (ti[q] >= 0 && tv[q] >= thr) {
-            if (nwin > 1) {
-              const int m = ti[q] % M, r = ti[q] / M;
-              if (PAIRED) {
-                const float2 f = score32_pair<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H,
-                                                  R, m, r, t, S, tw);
-                fs[q][0] = fabsf(f.x);
-                fs[q][NP - 1] = fabsf(f.y);
-              } else {
-                fs[q][0] = fabsf(score32<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H, R,
-                                             m, r, t, S, tw));
-              }
-            } else {
-#pragma unroll
-              for (int h = 0; h < NP; ++h) fs[q][h] = 0.0f;
-            }
-#pragma unroll
-            for (int h = 0; h < NP; ++h) fbest = fmaxf(fbest, fs[q][h]);
-          }
-        }
         df best = df_make(0.0f), best_ax = df_make(0.0f);
         df bg[KK];
 #pragma unroll
@@ -338,12 +304,7 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
         int bm = -1, br = 0, bflat = 0;
 #pragma unroll
         for (int q = 0; q < kTop; ++q) {
-          bool live[NP], any = false;
-#pragma unroll
-          for (int h = 0; h < NP; ++h) {
-            live[h] = fs[q][h] >= 0.0f && fs[q][h] >= fbest - 2.0f * E32;
-            any = any || live[h];
-          }
+          const bool any = ti[q] >= 0 && tv[q] >= thr;
           if (any) {
             const int m = ti[q] % M, r = ti[q] / M;
             df ax[NP], sc[NP], gq[NP][KK];
@@ -376,8 +337,7 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
 #pragma unroll
             for (int h = 0; h < NP; ++h) {
               const int rr = r + h * Rh, flat = m * R + rr;
-              if (live[h] &&
-                  (bm < 0 || df_abs_gt(sc[h], best) || (df_abs_eq(sc[h], best) && flat < bflat))) {
+              if (bm < 0 || df_abs_gt(sc[h], best) || (df_abs_eq(sc[h], best) && flat < bflat)) {
                 best = sc[h];
                 bm = m;
                 br = rr;
@@ -411,7 +371,7 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
                 S.r[i] = rb;
               }
             ++t;
-            asum = 0.0f;
+            float asum = 0.0f;
 #pragma unroll
             for (int i = 0; i < KK; ++i)
               if (i < t) asum += fabsf(S.ahi[i]);

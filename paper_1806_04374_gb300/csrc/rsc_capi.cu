@@ -222,7 +222,9 @@ int check_device(const rsc_dict *d) {
   return dev == d->device ? RSC_OK : RSC_ERR_INVALID;
 }
 
-// Patches per group below which rsc_encode does not split the FP16 path.
+// The FP16 path splits its patches into at most kMaxGroups groups of at
+// least kGroupMin patches, one stream each.
+constexpr int kMaxGroups = 2;
 constexpr int64_t kGroupMin = 65536;
 
 // Scratch of the FP16 path for P patches and K steps (256-byte aligned parts).
@@ -507,34 +509,45 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   // FP16 tensor-core path, split per greedy step into a scoring kernel and a
   // per-patch refine kernel; patches it hands back are coded by the FP32 path
   if (!dict->steered_f16 || K > kTcMaxK || P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
-  // Two independent halves on two streams: the scoring pass of one half
-  // (tensor and ALU pipes, one CTA per SM) runs beside the refine pass of the
-  // other (latency-bound), so each hides part of the other.
-  const int G = P >= 2 * kGroupMin ? 2 : 1;
-  int64_t Pg[2] = {P, 0};
-  if (G == 2) {
-    Pg[0] = (P / 2 + 255) & ~(int64_t)255;
-    Pg[1] = P - Pg[0];
+  // Independent groups of patches on their own streams: the scoring pass of
+  // one group (tensor and ALU pipes, one CTA per SM) runs beside the refine
+  // pass of another (latency-bound), so each hides part of the other.
+  int G = (int)(P / kGroupMin);
+  G = G < 1 ? 1 : (G > kMaxGroups ? kMaxGroups : G);
+  int64_t Pg[kMaxGroups] = {};
+  size_t bytes[kMaxGroups] = {}, total = 0;
+  for (int g = 0, left = G; g < G; ++g, --left) {
+    const int64_t done = [&] {
+      int64_t v = 0;
+      for (int h = 0; h < g; ++h) v += Pg[h];
+      return v;
+    }();
+    Pg[g] = left == 1 ? P - done : (((P - done) / left + 255) & ~(int64_t)255);
+    bytes[g] = f16_scratch_bytes(Pg[g], K);
+    total += bytes[g];
   }
-  size_t bytes[2] = {f16_scratch_bytes(Pg[0], K), G == 2 ? f16_scratch_bytes(Pg[1], K) : 0};
   unsigned char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bytes[0] + bytes[1], st);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
   }
   if (e != cudaSuccess) return rsc_cuda_fail(e);
-  cudaStream_t st2 = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  if (G == 2) {
-    e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+  cudaStream_t sg[kMaxGroups] = {};
+  cudaEvent_t fork = nullptr, join[kMaxGroups] = {};
+  sg[0] = st;
+  if (G > 1) {
+    e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(fork, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st2, fork, 0);
+    for (int g = 1; g < G && e == cudaSuccess; ++g) {
+      e = cudaStreamCreateWithFlags(&sg[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[g], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(sg[g], fork, 0);
+    }
     if (e != cudaSuccess) rc = rsc_cuda_fail(e);
   }
   int64_t off = 0;
+  size_t soff = 0;
   for (int g = 0; g < G && rc == RSC_OK; ++g) {
     RompArgs ag = a;
     ag.x = x + off * dict->H * dict->J * 2;
@@ -544,17 +557,22 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
     ag.angle = angle ? angle + off * K : nullptr;
     ag.coef = coef + off * K;
     ag.resid_norm2 = resid_norm2 ? resid_norm2 + off : nullptr;
-    rc = encode_f16_group(dict, ag, scratch + (g ? bytes[0] : 0), g ? st2 : st);
+    rc = encode_f16_group(dict, ag, scratch + soff, sg[g]);
     off += Pg[g];
+    soff += bytes[g];
   }
-  if (G == 2) {
-    // join (also after a failed launch, so that the scratch is released last)
-    e = cudaEventRecord(join, st2);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
+  // join every side stream (also after a failed launch, so that the scratch
+  // is released after all work that uses it)
+  for (int g = 1; g < G; ++g) {
+    if (!sg[g] || !join[g]) continue;
+    e = cudaEventRecord(join[g], sg[g]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join[g], 0);
     if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    if (st2) cudaStreamDestroy(st2);
+  }
+  if (fork) cudaEventDestroy(fork);
+  for (int g = 1; g < G; ++g) {
+    if (join[g]) cudaEventDestroy(join[g]);
+    if (sg[g]) cudaStreamDestroy(sg[g]);
   }
   e = cudaFreeAsync(scratch, st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
