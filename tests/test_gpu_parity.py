@@ -79,6 +79,10 @@ CASES = [
     ("kmax12_J10", 32, 10, 12, 64, 4, 40, 3, 0.05),
     ("kmax16_J4", 16, 4, 16, 64, 3, 40, 3, 0.05),
     ("kmax0_rotation_invariant", 8, 6, 0, 16, 3, 30, 3, 0.05),
+    # even R codes atom pairs (r, r + R/2) in one unit: the smallest pairs
+    ("R2_one_pair_per_atom", 9, 6, 8, 2, 3, 60, 2, 0.05),
+    ("R4_two_pairs", 11, 6, 8, 4, 3, 60, 3, 0.05),
+    ("kmax1_minimal_odd_half", 12, 6, 1, 16, 3, 60, 2, 0.05),
     # the image workload's coder sizes: 21x21 patches, J=10, kmax=12 (n=250),
     # M=256, R=128, K=8 (outside the tensor-core path: FP32 only)
     ("c2_sizes_n250_M256_R128_K8", 256, 10, 12, 128, 8, 24, 4, 0.05),
@@ -123,6 +127,27 @@ def test_degenerate_patches(rsc, precision):
     assert g["atom"][2, 0] == 1 and g["angle_idx"][2, 0] == 2 and np.all(g["atom"][2, 1:] == -1)
     assert abs(g["coef"][1, 0] - 1.0) < 1e-9 and abs(g["coef"][2, 0] - 1.0) < 1e-9
     check(x, d, R, 3, g, COEF_TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
+def test_half_turn_ties_take_the_smaller_angle(rsc, precision):
+    """Atoms with even harmonics only score the same at r and r + R/2 (half a
+    turn multiplies harmonic k by (-1)^k, Eq. (Sr)): the tie must go to the
+    smaller flat index, i.e. the angle below R/2, as the oracle's rule says."""
+    M, J, kmax, R = 6, 6, 8, 16
+    d = synth.make_dictionary(M, J, kmax, 4242).astype(np.float64)
+    d[:, 1::2] = 0.0
+    d /= np.sqrt(synth.coef_norm2(d))[:, None, None, None]
+    d = d.astype(np.float32)
+    xs = []
+    for m, r0 in [(0, 3), (2, 11), (5, 0), (4, 7)]:  # 11 = 3 + R/2: ties with 3
+        xs.append(oracle.steer(d[m].astype(np.float64), 2 * np.pi * r0 / R).astype(np.float32))
+    x = np.stack(xs)
+    g = run_gpu(rsc, x, d, R, 1, precision)
+    o = oracle.romp(x, d, R, 1)
+    assert np.array_equal(g["atom"][:, 0], [0, 2, 5, 4])
+    assert np.array_equal(g["angle_idx"][:, 0], [3, 3, 0, 7])
+    assert np.array_equal(g["angle_idx"][:, 0], o["angle"][:, 0])
 
 
 @pytest.mark.parametrize("precision", ["fp32", "f16"])
