@@ -102,7 +102,10 @@ int rsc_dict_dims(const rsc_dict *dict, rsc_dims *dims);
  *   x         : device, P x (kmax+1) x J x 2 floats.
  *   P         : patches, >= 0 (0 is a no-op).
  *   K         : greedy steps, 1 <= K <= 16.
- *   prec      : RSC_FP32 or RSC_F16_RESCORE.
+ *   prec      : RSC_FP32 or RSC_F16_RESCORE.  RSC_F16_RESCORE takes packed
+ *               lengths J (2 kmax + 1) <= 256 and K <= 8 (RSC_ERR_UNSUPPORTED
+ *               otherwise); the dictionary's tables for it are built by
+ *               rsc_dict_create when the sizes allow.
  *   atom      : device int32 [P x K], atom index m per step, -1 if none.
  *   angle_idx : device int32 [P x K], angle index r in [0, R), -1 if none.
  *   angle     : device float [P x K] or NULL, the angle 2*pi*r/R in radians.

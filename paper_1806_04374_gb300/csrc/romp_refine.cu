@@ -23,7 +23,6 @@
 
 namespace {
 
-constexpr int kRowBytes = kTcKst * 2;  // packed fp16 residual row
 
 // State arrays (each of length P, element i of patch p at [field * P + p]).
 template <int KK>
@@ -130,7 +129,7 @@ __device__ __forceinline__ TwS load_tw(const RefineArgs &a, const int *&qtab) {
   const int n = 4 * a.H * a.R;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = a.tw[i];
   int *qt = reinterpret_cast<int *>(tws + ((n + 3) & ~3));
-  for (int q = threadIdx.x; q < kTcKst; q += blockDim.x)
+  for (int q = threadIdx.x; q < a.L; q += blockDim.x)
     qt[q] = rsc_slot_code(q, a.J, a.kmax, a.paired != 0);
   __syncthreads();
   qtab = qt;
@@ -138,16 +137,17 @@ __device__ __forceinline__ TwS load_tw(const RefineArgs &a, const int *&qtab) {
 }
 
 // Packed residual x - sum_i a_i S_{r_i} d_{m_i} of this thread's patch (FP32)
-// written times `scale` as fp16 (kTcKst slots, zero-padded) to `row` if not
+// written times `scale` as fp16 (L slots, zero-padded) to `row` if not
 // null, slot by slot in packed order; the Im slot of an entry reuses the value
 // computed with its Re slot.  Returns ||r||^2 (unscaled).
 template <int KK>
-__device__ __forceinline__ float residual_q(uint4 *row, float scale, const float *__restrict__ xp,
+__device__ __forceinline__ float residual_q(uint4 *row, int L, float scale,
+                                            const float *__restrict__ xp,
                                             const float *__restrict__ d, int HJ, int t,
                                             const Ls<KK> &S, const TwS &tw, const int *qtab) {
   float n2 = 0.0f, pend = 0.0f;
 #pragma unroll 1
-  for (int cq = 0; cq < kTcKst / 8; ++cq) {
+  for (int cq = 0; cq < L / 8; ++cq) {
     float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -197,24 +197,26 @@ __device__ __forceinline__ float residual_q(uint4 *row, float scale, const float
   return n2;
 }
 
-// Error bound of one fp16 score of a row, times 1.25, without the key term:
-// 2^-10 ||r|| (both operands rounded, unit atoms) + 2^-18 ||r|| (second
-// order) + 112 * 2^-21 ||r|| (the accumulation, at 4x unit roundoff) +
-// 11 * 2^-33 ||r|| and 11 * 2^(e-33) (subnormal rounding of a dictionary
-// entry, <= 2^-25 / kDictScale, and of a row entry, <= 2^-25 / row scale, over
-// sqrt(112) < 11 entries); plus the FP32 residual's own error 2 dr.
-__device__ __forceinline__ float score_err_base(float rnorm, float dr, int e) {
-  return 1.25f * (9.765625e-4f + 3.814697265625e-6f + 112.0f * 4.76837158203125e-7f +
-                  11.0f * 1.16415321826934814e-10f) *
+// Error bound of one fp16 score of a row of L slots, times 1.25, without the
+// key term: 2^-10 ||r|| (both operands rounded, unit atoms) + 2^-18 ||r||
+// (second order) + L 2^-21 ||r|| (the accumulation, at 4x unit roundoff) +
+// s 2^-33 ||r|| and s 2^(e-33) (subnormal rounding of a dictionary entry,
+// <= 2^-25 / kDictScale, and of a row entry, <= 2^-25 / row scale, over
+// sqrt(L) <= s entries: s = 11 for 112 slots, 16 for 256); plus the FP32
+// residual's own error 2 dr.
+__device__ __forceinline__ float score_err_base(float rnorm, float dr, int e, int L) {
+  const float sq = L <= kTcKst ? 11.0f : 16.0f;
+  return 1.25f * (9.765625e-4f + 3.814697265625e-6f + (float)L * 4.76837158203125e-7f +
+                  sq * 1.16415321826934814e-10f) *
              rnorm +
-         1.25f * 11.0f * ldexpf(1.0f, e - 33) + 2.0f * dr;
+         1.25f * sq * ldexpf(1.0f, e - 33) + 2.0f * dr;
 }
 
 // The scoring pass's window for a row: 2.02 E in accumulator units
 // (2^(16 - e) times true scores), with the key term 2^-16 s1 bounded through
 // s1 <= 1.01 ||r|| (Cauchy-Schwarz over unit atoms plus the score error).
-__device__ __forceinline__ float score_window(float rnorm, float dr, int e) {
-  return 2.02f * (score_err_base(rnorm, dr, e) + 1.52587890625e-5f * 1.01f * rnorm) *
+__device__ __forceinline__ float score_window(float rnorm, float dr, int e, int L) {
+  return 2.02f * (score_err_base(rnorm, dr, e, L) + 1.52587890625e-5f * 1.01f * rnorm) *
          ldexpf(1.0f, 16 - e);
 }
 
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
     const float xnorm = sqrtf(fmaxf(acc.hi + acc.lo, 0.0f));
     Ls<KK> S;
     const int e = rsc_row_exponent(xnorm);
-    const float rn = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes),
+    const float rn = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * (a.L * 2)), a.L,
                                           ldexpf(1.0f, kRowLog2 - e), xp, a.d, HJ, 0, S, tw,
                                           qtab));
     a.sI[I::iT * a.P + p] = 0;
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
     a.sF[I::fX * a.P + p] = xnorm;
     a.sF[I::fR * a.P + p] = rn;
     a.sF[I::fDr * a.P + p] = 2.0f * kU32 * xnorm;
-    a.win[p] = score_window(rn, 2.0f * kU32 * xnorm, e);
+    a.win[p] = score_window(rn, 2.0f * kU32 * xnorm, e, a.L);
     a.status[p] = 1;
   }
 }
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
     const float s1 = tv[0];
     // fp16 error of a score (score_err_base) plus 2^-16 s1 for the low
     // mantissa bits the scoring kernel replaces by a column index
-    const float E = score_err_base(rnorm, dr, e) + 1.52587890625e-5f * fabsf(s1);
+    const float E = score_err_base(rnorm, dr, e, a.L) + 1.52587890625e-5f * fabsf(s1);
     int outcome = 0;  // 0 continue, 1 finished/stopped, 2 hand-off
     bool have_factor = false;
     if (!(s1 + E > stop_level)) {
@@ -379,16 +381,16 @@ __global__ void __launch_bounds__(128, 5) romp_refine_kernel(const RefineArgs a)
             if (t >= a.K) {
               outcome = 1;
               // final residual norm in FP32 (the fp16 row is not needed any more)
-              rnorm = sqrtf(residual_q<KK>(nullptr, 1.0f, xp, a.d, HJ, t, S, tw, qtab));
+              rnorm = sqrtf(residual_q<KK>(nullptr, a.L, 1.0f, xp, a.d, HJ, t, S, tw, qtab));
             } else {
               // the previous residual's norm bounds the new one (least squares
               // over a larger support)
               const int en = rsc_row_exponent(rnorm);
-              rnorm = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * kRowBytes),
+              rnorm = sqrtf(residual_q<KK>(reinterpret_cast<uint4 *>(a.A + p * (a.L * 2)), a.L,
                                            ldexpf(1.0f, kRowLog2 - en), xp, a.d, HJ, t, S,
                                            tw, qtab));
               store_state<KK>(a, p, S, t, en, rnorm, dr);
-              a.win[p] = score_window(rnorm, dr, en);
+              a.win[p] = score_window(rnorm, dr, en, a.L);
             }
           }
         }
@@ -420,7 +422,7 @@ int launch_refine_t(const RefineArgs &a, bool init, cudaStream_t stream) {
   const int64_t blocks = (a.P + 127) / 128;
   const int64_t cap = (int64_t)nsm * 32;
   const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
-  const size_t shm = (size_t)((4 * a.H * a.R + 3) & ~3) * 4 + (size_t)kTcKst * 4;
+  const size_t shm = (size_t)((4 * a.H * a.R + 3) & ~3) * 4 + (size_t)a.L * 4;
   if (init)
     romp_init_kernel<KK><<<grid, 128, shm, stream>>>(a);
   else if (a.paired)

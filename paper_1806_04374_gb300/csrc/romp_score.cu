@@ -33,18 +33,24 @@ constexpr int kSTile = 128;
 constexpr int kSTiles = 2;
 constexpr int kSStages = 3;
 constexpr int kSBlk = 128 * 128;       // one 64-column block of 128 rows (bytes)
-constexpr int kSTileBytes = 2 * kSBlk; // A tile / B stage: two blocks
 constexpr int kSThreads = 320;         // 8 epilogue warps + TMA warp + MMA warp
 constexpr uint64_t kSWaitNs = 2000000000ull;
 
-struct SLayout {
-  int a_off, b_off, bar_off, total;
+// Shape of one instantiation: NB 64-column blocks per packed row (2 for rows
+// of kTcKst, 4 for kTcKstLong), BR dictionary rows (atoms or atom pairs) per
+// chunk, BUFC accumulator columns per TMEM buffer.
+template <bool PAIRED, int NB>
+struct SShape {
+  static constexpr int BR = (PAIRED || NB > 2) ? kTcBP : kTcBN;
+  static constexpr int BUFC = PAIRED ? 2 * kTcBP : BR;
+  static constexpr uint32_t kCols = kSTiles * 2 * BUFC;  // 512 or 256
+  static constexpr int kATile = NB * kSBlk;               // one A tile (bytes)
+  static constexpr int kBBlk = BR * 128;                  // one 64-column block of a B stage
+  static constexpr int kBStage = NB * kBBlk;
+  static constexpr int a_off = 0, b_off = kSTiles * kATile;
+  static constexpr int bar_off = b_off + kSStages * kBStage;
+  static constexpr int total = bar_off + 256 + 1024;  // barriers + alignment slack
 };
-
-__host__ __device__ constexpr SLayout s_layout() {
-  return SLayout{0, kSTiles * kSTileBytes, kSTiles * kSTileBytes + kSStages * kSTileBytes,
-                 kSTiles * kSTileBytes + kSStages * kSTileBytes + 256 + 1024};
-}
 
 // barrier slots (8 bytes each)
 enum : int {
@@ -57,17 +63,17 @@ enum : int {
   kBarCount = 6 + 2 * kSStages,
 };
 
-template <bool PAIRED>
+template <bool PAIRED, int NB>
 __global__ void __launch_bounds__(kSThreads, 1)
     romp_score_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const ScoreArgs a) {
-  // B rows per chunk and the byte offset of a chunk's second 64-column block
-  constexpr int BR = PAIRED ? kTcBP : kTcBN;
-  constexpr uint32_t kBBlk = (uint32_t)BR * 128;
+  using Sh = SShape<PAIRED, NB>;
+  constexpr int BR = Sh::BR;
+  constexpr uint32_t kBBlk = (uint32_t)Sh::kBBlk;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  constexpr SLayout Lo = s_layout();
+  constexpr Sh Lo{};
   unsigned char *sA = smem + Lo.a_off;
   unsigned char *sB = smem + Lo.b_off;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bar_off);
@@ -77,8 +83,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
   auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr uint32_t kCols = kSTiles * 2 * kTcBN;  // 512
-  constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, PAIRED ? kTcBN / 2 : kTcBN);
+  constexpr uint32_t kCols = Sh::kCols;
+  constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, PAIRED ? kTcBP : BR);
 
   if (tid == 0) {
     tc::mbar_init(bar(kBarAFull), 1);
@@ -116,12 +122,12 @@ __global__ void __launch_bounds__(kSThreads, 1)
           fail();
           break;
         }
-        tc::mbar_arrive_expect_tx(bar(kBarAFull), kSTiles * kSTileBytes);
+        tc::mbar_arrive_expect_tx(bar(kBarAFull), kSTiles * Sh::kATile);
         for (int t = 0; t < kSTiles; ++t) {
           const int y = (int)((pair * kSTiles + t) * kSTile);
-          const uint32_t dst = tc::smem_u32(sA + t * kSTileBytes);
-          tc::tma_load_2d(dst, &tmA, bar(kBarAFull), 0, y);
-          tc::tma_load_2d(dst + kSBlk, &tmA, bar(kBarAFull), 64, y);
+          const uint32_t dst = tc::smem_u32(sA + t * Sh::kATile);
+#pragma unroll
+          for (int j = 0; j < NB; ++j) tc::tma_load_2d(dst + j * kSBlk, &tmA, bar(kBarAFull), 64 * j, y);
         }
         ++issuedA;
         for (int c = 0; c < nch; ++c, ++gB) {
@@ -131,10 +137,11 @@ __global__ void __launch_bounds__(kSThreads, 1)
             fail();
             break;
           }
-          const uint32_t dst = tc::smem_u32(sB + s * kSTileBytes);
-          tc::mbar_arrive_expect_tx(bar(kBarBFull + s), 2 * kBBlk);
-          tc::tma_load_2d(dst, &tmB, bar(kBarBFull + s), 0, c * BR);
-          tc::tma_load_2d(dst + kBBlk, &tmB, bar(kBarBFull + s), 64, c * BR);
+          const uint32_t dst = tc::smem_u32(sB + s * Sh::kBStage);
+          tc::mbar_arrive_expect_tx(bar(kBarBFull + s), Sh::kBStage);
+#pragma unroll
+          for (int j = 0; j < NB; ++j)
+            tc::tma_load_2d(dst + j * kBBlk, &tmB, bar(kBarBFull + s), 64 * j, c * BR);
           ++issuedB;
         }
       }
@@ -165,11 +172,11 @@ __global__ void __launch_bounds__(kSThreads, 1)
             break;
           }
           tc::fence_after_sync();
-          const uint32_t b0 = tc::smem_u32(sB + s * kSTileBytes);
+          const uint32_t b0 = tc::smem_u32(sB + s * Sh::kBStage);
 #pragma unroll
           for (int t = 0; t < kSTiles; ++t) {
-            const uint32_t d = tmem + (uint32_t)(t * 2 + b) * kTcBN;
-            const uint32_t at = a0 + t * kSTileBytes;
+            const uint32_t d = tmem + (uint32_t)(t * 2 + b) * Sh::BUFC;
+            const uint32_t at = a0 + t * Sh::kATile;
             if (PAIRED) {
               // even half (A and B block 0) -> columns 0..63, odd half
               // (block 1) -> columns 64..127 of the buffer
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
                 tc::mma_f16(d, tc::smem_desc_sw128(at + ks * 32), tc::smem_desc_sw128(b0 + ks * 32),
                             kIdesc, ks > 0 ? 1u : 0u);
               for (int ks = 0; ks < a.ko; ++ks)
-                tc::mma_f16(d + kTcBN / 2, tc::smem_desc_sw128(at + kSBlk + ks * 32),
+                tc::mma_f16(d + kTcBP, tc::smem_desc_sw128(at + kSBlk + ks * 32),
                             tc::smem_desc_sw128(b0 + kBBlk + ks * 32), kIdesc, ks > 0 ? 1u : 0u);
             } else {
               for (int ks = 0; ks < a.ksteps; ++ks)
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
           break;
         }
         tc::fence_after_sync();
-        const uint32_t taddr = tmem + lane_base + (uint32_t)(tile * 2 + b) * kTcBN;
+        const uint32_t taddr = tmem + lane_base + (uint32_t)(tile * 2 + b) * Sh::BUFC;
         const int nvalid = min(BR, a.MR - c * BR);
 #pragma unroll 1
         for (int piece = 0; piece < BR / 32; ++piece) {
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
           if (PAIRED) {
             // pair value |E| + |O| = max(|score(r)|, |score(r + R/2)|)
             uint32_t o[32];
-            tc::tmem_ld32(taddr + kTcBN / 2 + piece * 32, o);
+            tc::tmem_ld32(taddr + kTcBP + piece * 32, o);
             tc::tmem_wait_ld();
 #pragma unroll
             for (int u = 0; u < 32; ++u)
@@ -314,24 +321,36 @@ __global__ void __launch_bounds__(kSThreads, 1)
 
 }  // namespace
 
-int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
-                     cudaStream_t stream) {
-  if (a.P == 0) return RSC_OK;
+namespace {
+template <bool PAIRED, int NB>
+int launch_score_t(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
+                   cudaStream_t stream) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   int max_optin = 0, nsm = 0;
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  constexpr SLayout L = s_layout();
-  if (L.total > max_optin) return RSC_ERR_UNSUPPORTED;
-  auto kern = a.paired ? romp_score_kernel<true> : romp_score_kernel<false>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+  constexpr int total = SShape<PAIRED, NB>::total;
+  if (total > max_optin) return RSC_ERR_UNSUPPORTED;
+  auto kern = romp_score_kernel<PAIRED, NB>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, total);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   const int64_t pairs = (a.P + kSTiles * kSTile - 1) / (kSTiles * kSTile);
   const int64_t grid = pairs < nsm ? pairs : nsm;
-  kern<<<(unsigned)grid, kSThreads, L.total, stream>>>(tmA, tmB, a);
+  kern<<<(unsigned)grid, kSThreads, total, stream>>>(tmA, tmB, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return RSC_OK;
+}
+}  // namespace
+
+int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
+                     cudaStream_t stream) {
+  if (a.P == 0) return RSC_OK;
+  if (a.L == kTcKst)
+    return a.paired ? launch_score_t<true, 2>(a, tmA, tmB, stream)
+                    : launch_score_t<false, 2>(a, tmA, tmB, stream);
+  if (a.L == kTcKstLong && !a.paired) return launch_score_t<false, 4>(a, tmA, tmB, stream);
+  return RSC_ERR_UNSUPPORTED;
 }

@@ -94,7 +94,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // TMA map of a row-major fp16 matrix [rows][kTcKst]: box 64 columns x
 // box_rows rows, 128-byte swizzle, zero fill outside (columns kTcKst..127,
 // rows >= rows).
-int encode_rows_map(CUtensorMap *map, void *base, size_t rows, int box_rows) {
+int encode_rows_map(CUtensorMap *map, void *base, size_t rows, int box_rows, int row_len) {
   static EncodeTiledFn fn = nullptr;
   static cudaError_t fn_err = cudaSuccess;
   static std::once_flag once;
@@ -106,8 +106,8 @@ int encode_rows_map(CUtensorMap *map, void *base, size_t rows, int box_rows) {
     if (fn_err == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = (EncodeTiledFn)f;
   });
   if (!fn) return rsc_cuda_fail(fn_err != cudaSuccess ? fn_err : cudaErrorNotSupported);
-  const cuuint64_t gdim[2] = {(cuuint64_t)kTcKst, (cuuint64_t)rows};
-  const cuuint64_t gstride[1] = {(cuuint64_t)kTcKst * 2};
+  const cuuint64_t gdim[2] = {(cuuint64_t)row_len, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)row_len * 2};
   const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult cr = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, gdim, gstride, box, estr,
@@ -130,12 +130,14 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   const int n = J + 2 * d->kmax * J;
   d->n = n;
   const size_t rows = (size_t)M * R;
-  if (n > kTcMaxN || rows * kTcKst * 2 > ((size_t)1 << 30) ||
+  const int L = n <= kTcKst ? kTcKst : kTcKstLong;
+  d->row_len = L;
+  if (n > kTcMaxN || rows * L * 2 > ((size_t)1 << 30) ||
       (size_t)M * M * H * 16 > ((size_t)1 << 28))
     return RSC_OK;
   // packed steered rows: slot q of row (r, m) from rsc_slot_code
   auto fill_row = [&](uint16_t *row, int m, int r, bool paired) {
-    for (int q = 0; q < kTcKst; ++q) {
+    for (int q = 0; q < L; ++q) {
       const int code = rsc_slot_code(q, J, d->kmax, paired);
       if (code < 0) continue;
       const int e = code >> 8, k = (code >> 1) & 127, c = code & 1;
@@ -147,10 +149,10 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
       row[q] = f16_bits(k == 0 ? re : M_SQRT2 * (c ? im : re));
     }
   };
-  std::vector<uint16_t> B(rows * kTcKst, 0);
+  std::vector<uint16_t> B(rows * L, 0);
   for (int m = 0; m < M; ++m)
-    for (int r = 0; r < R; ++r) fill_row(&B[((size_t)r * M + m) * kTcKst], m, r, false);
-  const bool paired = rsc_paired_ok(J, d->kmax, R);
+    for (int r = 0; r < R; ++r) fill_row(&B[((size_t)r * M + m) * L], m, r, false);
+  const bool paired = L == kTcKst && rsc_paired_ok(J, d->kmax, R);
   std::vector<uint16_t> BP;
   if (paired) {
     int ne, no;
@@ -210,8 +212,9 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
 
-  int rc = encode_rows_map(&d->tmap_b, d->steered_f16, rows, kTcBN);
-  if (rc == RSC_OK && paired) rc = encode_rows_map(&d->tmap_bp, d->paired_f16, rows / 2, kTcBP);
+  int rc = encode_rows_map(&d->tmap_b, d->steered_f16, rows, L == kTcKst ? kTcBN : kTcBP, L);
+  if (rc == RSC_OK && paired)
+    rc = encode_rows_map(&d->tmap_bp, d->paired_f16, rows / 2, kTcBP, kTcKst);
   return rc;
 }
 
@@ -228,11 +231,11 @@ constexpr int kMaxGroups = 2;
 constexpr int64_t kGroupMin = 65536;
 
 // Scratch of the FP16 path for P patches and K steps (256-byte aligned parts).
-size_t f16_scratch_bytes(int64_t P, int K) {
+size_t f16_scratch_bytes(int64_t P, int K, int L) {
   int nD = 0, nF = 0, nI = 0;
   rsc_state_layout(K, &nD, &nF, &nI);
   auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  return al256((size_t)P * kTcKst * 2) + 2 * al256((size_t)P * kTcTop * 4) +
+  return al256((size_t)P * L * 2) + 2 * al256((size_t)P * kTcTop * 4) +
          3 * al256((size_t)P * 4) + al256((size_t)nD * P * 8) + al256((size_t)nF * P * 4) +
          al256((size_t)nI * P * 4) + al256((size_t)(P + 4) * 4);
 }
@@ -268,7 +271,8 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   ra.tw = dict->tw;
   ra.xgram = dict->xgram;
   ra.anorm = dict->anorm;
-  ra.A = take((size_t)P * kTcKst * 2);
+  ra.L = dict->row_len;
+  ra.A = take((size_t)P * ra.L * 2);
   ra.cand_idx = reinterpret_cast<int *>(take((size_t)P * kTcTop * 4));
   ra.cand_val = reinterpret_cast<float *>(take((size_t)P * kTcTop * 4));
   ra.cand_disc = reinterpret_cast<float *>(take((size_t)P * 4));
@@ -290,11 +294,14 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   ScoreArgs sa;
   sa.P = P;
   sa.ksteps = (dict->n + 15) / 16;
+  sa.L = ra.L;
   sa.paired = ra.paired;
   sa.ke = dict->ke;
   sa.ko = dict->ko;
   sa.MR = sa.paired ? dict->M * (dict->R / 2) : dict->M * dict->R;
-  sa.nchunks = sa.paired ? (sa.MR + kTcBP - 1) / kTcBP : (sa.MR + kTcBN - 1) / kTcBN;
+  // B rows per chunk: 128 (short plain rows) or 64 (paired, long rows)
+  const int br = (sa.paired || sa.L != kTcKst) ? kTcBP : kTcBN;
+  sa.nchunks = (sa.MR + br - 1) / br;
   sa.status = ra.status;
   sa.cand_idx = const_cast<int *>(ra.cand_idx);
   sa.cand_val = const_cast<float *>(ra.cand_val);
@@ -302,7 +309,7 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   sa.win = ra.win;
   sa.err = dict->err;
   CUtensorMap tmA;
-  int rc = encode_rows_map(&tmA, ra.A, (size_t)P, kTcBN);
+  int rc = encode_rows_map(&tmA, ra.A, (size_t)P, kTcBN, ra.L);
   if (rc == RSC_OK) {
     const cudaError_t e = cudaMemsetAsync(redo, 0, sizeof(int), st);
     if (e != cudaSuccess) rc = rsc_cuda_fail(e);
@@ -523,7 +530,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
       return v;
     }();
     Pg[g] = left == 1 ? P - done : (((P - done) / left + 255) & ~(int64_t)255);
-    bytes[g] = f16_scratch_bytes(Pg[g], K);
+    bytes[g] = f16_scratch_bytes(Pg[g], K, dict->row_len);
     total += bytes[g];
   }
   unsigned char *scratch = nullptr;

@@ -28,7 +28,8 @@ struct rsc_dict {
   unsigned long long *fallbacks;  // device counter of exact re-scans
   // tensor-core path: steered dictionary and cross-Gram table (null when the
   // sizes are outside what the path handles)
-  void *steered_f16;     // [R*M][kTcKst] fp16 of kDictScale x packed S_r d_m (row r*M + m)
+  void *steered_f16;     // [R*M][row_len] fp16 of kDictScale x packed S_r d_m (row r*M + m)
+  int row_len;           // packed row length of the tensor-core operands: kTcKst or kTcKstLong
   // paired layout (even R): rows r*M + m for r < R/2, slots split by the
   // parity of k (rsc_slot_code); null when the sizes do not allow it
   void *paired_f16;
@@ -48,8 +49,9 @@ struct rsc_dict {
 // sqrt(2) Re (c = 0) or sqrt(2) Im (c = 1) of c[j, k], k >= 1.  The Euclidean
 // dot product of two packed vectors is the coefficient inner product.
 constexpr int kTcKst = 112;  // stored row length of the steered dictionary (fp16)
+constexpr int kTcKstLong = 256;  // row length for packed lengths 113..256 (plain layout only)
 constexpr int kTcOdd = 64;   // first slot of the odd harmonics in the paired layout
-constexpr int kTcMaxN = 112; // packed lengths the tensor-core path handles
+constexpr int kTcMaxN = 256; // packed lengths the tensor-core path handles
 constexpr int kTcBN = 128;   // steered atoms per MMA (N) and per TMA box
 constexpr int kTcMaxK = 8;   // greedy steps the tensor-core path handles
 
@@ -150,6 +152,7 @@ struct ScoreArgs {
   // paired layout (rsc_slot_code): B rows are steered-atom pairs (r < R/2),
   // MR counts pairs, and the MMAs run ke / ko K-steps on the even / odd halves
   int paired, ke, ko;
+  int L;  // packed row length (kTcKst or kTcKstLong; the latter plain only)
   const int *status;  // > 0: patch still being coded
   int *cand_idx;      // [P][kTcTop]
   float *cand_val;    // [P][kTcTop]
@@ -173,7 +176,8 @@ struct RefineArgs {
   const float *tw;       // [4][H][R]
   const float4 *xgram;
   const float2 *anorm;   // [M] ||d_m||^2 in double-float
-  unsigned char *A;      // [P][kTcKst] fp16 packed residual rows, scaled (see below)
+  unsigned char *A;      // [P][L] fp16 packed residual rows, scaled (see below)
+  int L;                 // packed row length (kTcKst or kTcKstLong)
   const int *cand_idx;
   const float *cand_val;
   const float *cand_disc;

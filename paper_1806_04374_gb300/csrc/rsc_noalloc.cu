@@ -61,7 +61,7 @@ extern "C" int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   if (dev != dict->device) return RSC_ERR_INVALID;
-  if (!dict->steered_f16 || K > kTcMaxK) return RSC_ERR_UNSUPPORTED;
+  if (!dict->steered_f16 || dict->row_len != kTcKst || K > kTcMaxK) return RSC_ERR_UNSUPPORTED;
   int *scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != RSC_OK) return rc;

@@ -84,15 +84,15 @@ CASES = [
     ("R4_two_pairs", 11, 6, 8, 4, 3, 60, 3, 0.05),
     ("kmax1_minimal_odd_half", 12, 6, 1, 16, 3, 60, 2, 0.05),
     # the image workload's coder sizes: 21x21 patches, J=10, kmax=12 (n=250),
-    # M=256, R=128, K=8 (outside the tensor-core path: FP32 only)
+    # M=256, R=128, K=8 (tensor-core rows of 256 slots)
     ("c2_sizes_n250_M256_R128_K8", 256, 10, 12, 128, 8, 24, 4, 0.05),
 ]
 
 
 def tc_supported(J, kmax, K):
-    """Shapes the tensor-core path handles: packed length J(2 kmax + 1) <= 112
+    """Shapes the tensor-core path handles: packed length J(2 kmax + 1) <= 256
     and K <= 8."""
-    return J * (2 * kmax + 1) <= 112 and K <= 8
+    return J * (2 * kmax + 1) <= 256 and K <= 8
 
 
 @pytest.mark.parametrize("precision", ["fp32", "f16"])
