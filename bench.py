@@ -295,28 +295,33 @@ def measure_projection(rsc, torch, dev, stream, reps: int = 5) -> dict:
 
 def measure_images_c2(rsc, torch, dev) -> dict:
     """rsc_encode_images at the image workload's coder sizes: 21 x 21 patches
-    (349 px), J = 10, kmax = 12 (n = 250, outside the tensor-core path, so
-    the FP32 path), M = 256, R = 128, K = 8, on 4 seeded N(0,1) images of
-    sides 96, 160, 224, 288 (every stride-1 window).  Host clock around the
-    blocking call (projection + coding), after one warm-up call."""
+    (349 px), J = 10, kmax = 12 (n = 250: tensor-core rows of 256 slots),
+    M = 256, R = 128, K = 8, on 4 seeded N(0,1) images of sides 96, 160, 224,
+    288 (line textures, synth.make_line_image, 0.01 lines per pixel), FP16
+    path and FP32 path.  Host clock around the blocking call (projection +
+    coding), after one warm-up call each; hand-offs of the FP16 path counted."""
     N, J, kmax, M, R, K = 21, 10, 12, 256, 128, 8
-    rng = np.random.default_rng(20180617)
-    imgs = [torch.from_numpy(rng.standard_normal((s_, s_)).astype(np.float32)).to(dev)
+    imgs = [torch.from_numpy(synth.make_line_image(s_, s_, 0.01, 20180617 + s_)).to(dev)
             for s_ in (96, 160, 224, 288)]
     basis = rsc.Basis(N, J, kmax)
     dic = rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180618)).to(dev), R)
-    rsc.encode_images(dic, basis, imgs[:1], K, "fp32")
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    out = rsc.encode_images(dic, basis, imgs, K, "fp32")
-    torch.cuda.synchronize(dev)
-    dt = time.perf_counter() - t0
-    P = int(out["atom"].shape[0])
+    res = {"config": "N=21 (349 px), J=10, kmax=12 (n=250), M=256, R=128, K=8; "
+                     "4 images, sides 96/160/224/288, projection included"}
+    for prec in ("f16", "fp32"):
+        rsc.encode_images(dic, basis, imgs[:1], K, prec)
+        torch.cuda.synchronize(dev)
+        rsc.rsc_dict_fallback_count(dic.handle)
+        t0 = time.perf_counter()
+        out = rsc.encode_images(dic, basis, imgs, K, prec)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        P = int(out["atom"].shape[0])
+        res["patches"] = P
+        res[prec] = {"s": dt, "patches_per_s": P / dt,
+                     "handoffs": rsc.rsc_dict_fallback_count(dic.handle)}
     dic.close()
     basis.close()
-    return {"patches": P, "s": dt, "patches_per_s": P / dt, "precision": "fp32",
-            "config": "N=21 (349 px), J=10, kmax=12 (n=250), M=256, R=128, K=8; "
-                      "4 images, sides 96/160/224/288, projection included"}
+    return res
 
 
 def measure_rksvd(rsc, torch, dev, iters: int = 20) -> dict:
@@ -346,13 +351,53 @@ def measure_rksvd(rsc, torch, dev, iters: int = 20) -> dict:
             "timing": "host clock around the whole loop (encode + update + sync per iteration)"}
 
 
+def run_c2(args) -> None:
+    """The 21 x 21-patch image workload at full size: 512 images of side
+    U{64..512} (square line textures, synth.make_line_image, 0.01 lines per
+    pixel, standing in for the rendered texture images), every
+    stride-1 window (about 4.5 x 10^7 patches) projected (N = 21, J = 10,
+    kmax = 12, n = 250) and coded (M = 256, R = 128, K = 8) in one
+    rsc_encode_images call on the FP16 path.  Host clock around the call,
+    after a warm-up call on two images."""
+    import torch
+    import paper_1806_04374_gb300 as rsc
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rsc.load_library()
+    N, J, kmax, M, R, K = 21, 10, 12, 256, 128, 8
+    rng = np.random.default_rng(20180621)
+    sides = rng.integers(64, 513, size=512)
+    imgs = [torch.from_numpy(synth.make_line_image(int(s_), int(s_), 0.01, 20180621 + i)).to(dev)
+            for i, s_ in enumerate(sides)]
+    basis = rsc.Basis(N, J, kmax)
+    dic = rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180622)).to(dev), R)
+    out = rsc.encode_images(dic, basis, imgs[:2], K, args.precision)
+    del out
+    torch.cuda.synchronize(dev)
+    rsc.rsc_dict_fallback_count(dic.handle)
+    t0 = time.perf_counter()
+    out = rsc.encode_images(dic, basis, imgs, K, args.precision)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    P = int(out["atom"].shape[0])
+    steps = float((out["atom"] >= 0).sum().item()) / P
+    print(json.dumps({
+        "metric": "image workload patches/s (projection + coding, one call)", "value": P / dt,
+        "unit": "patches/s", "n_gpus": 1, "dtype": "f16" if args.precision == "f16" else "f32",
+        "data": "synthetic", "s": dt, "patches": P, "mean_steps_taken": steps,
+        "handoffs": rsc.rsc_dict_fallback_count(dic.handle),
+        "config": {"workload": "512 images, side U{64..512}, N=21 (349 px), J=10, kmax=12 "
+                               "(n=250), M=256, R=128, K=8"}}))
+    dic.close()
+    basis.close()
+
+
 def run_serving(args) -> None:
     """Serving loop of the request workload: images of side ~ U{128..1024}
-    (square, seeded N(0,1) pixels: the coder's cost does not depend on the
-    content), 11 x 11 patches, M = 128 resident atoms, R = 64, K = 5, FP16
-    path; requests arrive as a Poisson process; the server takes every
-    request that has arrived (up to `--serve-batch` patches) into one
-    rsc_encode_images call and copies the codes back to the host.  Latency =
+    (square line textures, synth.make_line_image), 11 x 11 patches, M = 128
+    resident atoms, R = 64, K = 5, FP16 path; requests arrive as a Poisson
+    process; the server takes every request that has arrived (up to
+    `--serve-batch` patches) into one rsc_encode_images call and copies the codes back to the host.  Latency =
     host-visible completion - arrival.  Runs: all requests at t = 0
     (capacity), then Poisson arrivals at each rate of `--rates`."""
     import torch
@@ -365,8 +410,8 @@ def run_serving(args) -> None:
     dic = rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180619)).to(dev), R)
     rng = np.random.default_rng(20180620)
     sides = rng.integers(128, 1025, size=64)
-    pool = [torch.from_numpy(rng.standard_normal((int(s_), int(s_))).astype(np.float32)).to(dev)
-            for s_ in sides]
+    pool = [torch.from_numpy(synth.make_line_image(int(s_), int(s_), 0.01, 20180620 + i)).to(dev)
+            for i, s_ in enumerate(sides)]
     windows = [(int(s_) - N + 1) ** 2 for s_ in sides]
 
     def serve(arrivals, which):
@@ -392,12 +437,14 @@ def run_serving(args) -> None:
             i = j
         total = sum(windows[q] for q in which)
         return {"requests": n, "patches": int(total), "calls": calls,
+                "handoffs": rsc.rsc_dict_fallback_count(dic.handle),
                 "wall_s": done, "patches_per_s": total / done,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99))}
 
     # warm-up
     serve(np.zeros(4), rng.integers(0, 64, size=4))
+    rsc.rsc_dict_fallback_count(dic.handle)
     runs = []
     nreq = max(16, int(args.serve_requests))
     which = rng.integers(0, 64, size=nreq)
@@ -442,7 +489,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-batch", type=int, default=4_000_000)
+    ap.add_argument("--c2", action="store_true",
+                    help="code the full 21x21-patch image workload once instead")
     args = ap.parse_args()
+    if args.c2:
+        run_c2(args)
+        return
     if args.serve:
         run_serving(args)
         return

@@ -129,3 +129,31 @@ def workload_inputs(name: str, P: int | None = None):
     P = wl.P if P is None else P
     x, truth = make_patches(d, P, wl.n_terms, wl.sigma, wl.seed + 1)
     return d, x, truth, wl
+
+
+def make_line_image(h: int, w: int, density: float, seed: int, noise: float = 0.1,
+                    width: float = 1.0, length: float = 9.0) -> np.ndarray:
+    """A pixel image for the image workloads: background N(0, noise^2) plus
+    randomly placed and oriented line segments (Poisson count density * h * w,
+    centres uniform, angles U[0, pi), weights N(0, 1)) with a Gaussian cross
+    profile of the given width and a soft end taper, i.e. rotated copies of
+    one line template, the structure of the paper's toy example (Fig. 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    img = rng.normal(0.0, noise, (h, w))
+    n = rng.poisson(density * h * w)
+    ys, xs = np.mgrid[0:h, 0:w].astype(np.float64)
+    cy = rng.uniform(0, h, n)
+    cx = rng.uniform(0, w, n)
+    th = rng.uniform(0, np.pi, n)
+    wt = rng.standard_normal(n)
+    half = length / 2.0
+    reach = int(np.ceil(half + 3 * width)) + 1
+    for i in range(n):
+        y0, y1 = max(0, int(cy[i]) - reach), min(h, int(cy[i]) + reach + 1)
+        x0, x1 = max(0, int(cx[i]) - reach), min(w, int(cx[i]) + reach + 1)
+        dy, dx = ys[y0:y1, x0:x1] - cy[i], xs[y0:y1, x0:x1] - cx[i]
+        along = dx * np.cos(th[i]) + dy * np.sin(th[i])
+        across = -dx * np.sin(th[i]) + dy * np.cos(th[i])
+        taper = np.clip(half + 1.0 - np.abs(along), 0.0, 1.0)
+        img[y0:y1, x0:x1] += wt[i] * taper * np.exp(-0.5 * (across / width) ** 2)
+    return img.astype(np.float32)
