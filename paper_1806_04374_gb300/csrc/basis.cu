@@ -26,12 +26,21 @@
 #include <vector>
 
 #include "rsc_internal.h"
+#include "tc_ptx.cuh"
+
+#include <cuda_fp16.h>
 
 struct rsc_basis {
   int N, J, kmax, H, npix, n, nout, nout_pad;
   int device;
   int2 *offs;    // device [npix] (dy, dx) of each masked pixel, row-major
   float *Po;     // device [npix][nout_pad]: half-spectrum outputs per pixel
+  // tensor-core projection (npix <= 128, nout <= 128; null otherwise): the
+  // operator transposed to [NP outputs][KP pixels] fp16, times 2^sb, as a hi
+  // part and the lo part of what hi leaves
+  uint16_t *Bt;  // device [2][NP][KP]
+  int KP, NP, sb;
+  int *err;      // device error word of the projection kernels (bounded waits)
 };
 
 namespace {
@@ -183,11 +192,220 @@ __global__ void project_kernel(const ImageItem *items, int n_items, int64_t P_to
   }
 }
 
+// Projection on the tensor cores: a tile of 128 windows (one per TMEM lane)
+// times the operator, coef = A Po with A the gathered window pixels.  fp16
+// keeps 11 bits, so both operands are split, x = hi + lo (hi = fp16(x), lo =
+// fp16(x - hi)), and the three products hi*hi + hi*lo + lo*hi are summed in the
+// FP32 accumulator: about 2^-21 relative, FP32 accuracy for the coder.  Each
+// window's pixels are scaled by a power of two 2^sa with max |x| 2^sa in
+// [2^13, 2^14) and the operator by 2^sb, far from fp16's range limits; the
+// result is multiplied back by 2^-(sa + sb) (exact).  Two groups of 128
+// threads per CTA each own a tile, an A area and 128 TMEM columns; a group
+// gathers its windows into 128-byte-swizzled K-major rows, one thread issues
+// the 3 x KP/16 MMAs (M = 128, N = NP) and commits them to the group's
+// mbarrier (bounded wait), and every thread reads its window's row back with
+// tcgen05.ld and writes the half spectrum.
+constexpr int kPjThreads = 256;
+constexpr int kPjRows = 128;
+constexpr int kPjBlkA = kPjRows * 128;  // one 64-pixel block of a 128-window tile
+constexpr uint64_t kPjWaitNs = 2000000000ull;
+
+struct PjLayout {
+  int b_off, a_off, bar_off, total;
+};
+__host__ __device__ inline PjLayout pj_layout(int NP) {
+  const int bblk = NP * 128;                   // one 64-pixel block of the operator
+  const int b_bytes = 2 * 2 * bblk;            // hi, lo; two blocks each
+  const int a_bytes = 2 * 2 * 2 * kPjBlkA;     // two groups; hi, lo; two blocks
+  return PjLayout{0, b_bytes, b_bytes + a_bytes, b_bytes + a_bytes + 64 + 1024};
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kPjRows) : "memory");
+}
+
+__global__ void __launch_bounds__(kPjThreads, 1)
+    project_tc_kernel(const ImageItem *items, int n_items, int64_t P_total, int N, int npix,
+                      const int2 *offs, const uint16_t *Bt, int KP, int NP, int sb, int nout,
+                      float *coef, int *err) {
+  extern __shared__ unsigned char pj_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(pj_raw) + 1023) & ~uintptr_t(1023));
+  const PjLayout Lo = pj_layout(NP);
+  const int bblk = NP * 128;
+  unsigned char *sB = smem + Lo.b_off;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bar_off);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 2);
+  volatile int *s_ok = reinterpret_cast<volatile int *>(bars + 2) + 1;  // [2]
+  const int tid = threadIdx.x, warp = tid >> 5, g = tid >> 7, row = tid & 127;
+  const int kchunks = KP / 8;  // 16-byte chunks of a row
+
+  // operator hi / lo -> swizzled K-major tiles (row = output, 8 pixels a chunk)
+  for (int i = tid; i < 2 * NP * kchunks; i += kPjThreads) {
+    const int part = i / (NP * kchunks), rem = i - part * NP * kchunks;
+    const int r = rem / kchunks, c = rem - r * kchunks;
+    const uint4 v = *reinterpret_cast<const uint4 *>(Bt + ((size_t)part * NP + r) * KP + c * 8);
+    *reinterpret_cast<uint4 *>(sB + part * 2 * bblk + (c >> 3) * bblk + r * 128 +
+                               (((c & 7) ^ (r & 7)) << 4)) = v;
+  }
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_u32(bars), 1);
+    tc::mbar_init(tc::smem_u32(bars + 1), 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), 2 * kPjRows);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t bar = tc::smem_u32(bars + g);
+  unsigned char *sA = smem + Lo.a_off + g * (2 * 2 * kPjBlkA);  // hi blocks, then lo blocks
+  const uint32_t a_hi = tc::smem_u32(sA), a_lo = a_hi + 2 * kPjBlkA;
+  const uint32_t b_hi = tc::smem_u32(sB), b_lo = b_hi + 2 * bblk;
+  const uint32_t idesc = tc::idesc_f16_f32(kPjRows, NP);
+  const uint32_t dcol = tmem + (uint32_t)(g * kPjRows);
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const int64_t ntiles = (P_total + kPjRows - 1) / kPjRows;
+  uint32_t iter = 0;
+  bool alive = true;
+  for (int64_t t = (int64_t)blockIdx.x * 2 + g; t < ntiles && alive;
+       t += (int64_t)gridDim.x * 2, ++iter) {
+    // ---- gather this thread's window, scale, split, write its A rows
+    const int64_t p = t * kPjRows + row;
+    const float *base = nullptr;
+    int w = 0;
+    float amax = 0.0f;
+    if (p < P_total) {
+      int lo = 0, hi = n_items - 1;  // last item with first <= p
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].first <= p) lo = mid; else hi = mid - 1;
+      }
+      const ImageItem it = items[lo];
+      const int64_t local = p - it.first;
+      const int nw = it.w - N + 1;
+      const int r0 = (int)(local / nw), c0 = (int)(local - (int64_t)r0 * nw);
+      base = it.img + (int64_t)r0 * it.w + c0;
+      w = it.w;
+      for (int q = 0; q < npix; ++q) {
+        const int2 o = __ldg(offs + q);
+        amax = fmaxf(amax, fabsf(__ldg(base + (int64_t)o.x * w + o.y)));
+      }
+    }
+    int ea = 0;
+    (void)frexpf(amax, &ea);
+    const int sa = 14 - (ea < -100 ? -100 : (ea > 127 ? 127 : ea));  // max |x| 2^sa < 2^14
+    const float scale = ldexpf(1.0f, sa);
+    for (int c = 0; c < kchunks; ++c) {
+      uint32_t hv[4], lv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float x2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = c * 8 + 2 * u + h;
+          float x = 0.0f;
+          if (base && q < npix) {
+            const int2 o = __ldg(offs + q);
+            x = __ldg(base + (int64_t)o.x * w + o.y) * scale;
+          }
+          x2[h] = x;
+        }
+        const __half2 hh = __floats2half2_rn(x2[0], x2[1]);
+        const float2 hf = __half22float2(hh);
+        const __half2 ll = __floats2half2_rn(x2[0] - hf.x, x2[1] - hf.y);
+        hv[u] = *reinterpret_cast<const uint32_t *>(&hh);
+        lv[u] = *reinterpret_cast<const uint32_t *>(&ll);
+      }
+      const int off = (c >> 3) * kPjBlkA + row * 128 + (((c & 7) ^ (row & 7)) << 4);
+      *reinterpret_cast<uint4 *>(sA + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+      *reinterpret_cast<uint4 *>(sA + 2 * kPjBlkA + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    group_sync(g);
+    tc::fence_after_sync();
+    // ---- MMAs: hi*hi + hi*lo + lo*hi into the group's accumulator
+    if (row == 0) {
+      const int ks_n = KP / 16;
+      for (int prod = 0; prod < 3; ++prod) {
+        const uint32_t aa = prod == 2 ? a_lo : a_hi, bb = prod == 1 ? b_lo : b_hi;
+        for (int ks = 0; ks < ks_n; ++ks) {
+          const uint32_t ao = (ks >> 2) * kPjBlkA + (ks & 3) * 32;
+          const uint32_t bo = (ks >> 2) * bblk + (ks & 3) * 32;
+          tc::mma_f16(dcol, tc::smem_desc_sw128(aa + ao), tc::smem_desc_sw128(bb + bo), idesc,
+                      (prod | ks) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(bar);
+      const bool done = tc::mbar_wait_bounded(bar, iter & 1, kPjWaitNs);
+      if (!done && err) atomicCAS(err, 0, RSC_ERR_TIMEOUT);
+      s_ok[g] = done ? 1 : 0;
+    }
+    group_sync(g);
+    tc::fence_after_sync();
+    if (!s_ok[g]) {
+      alive = false;
+      break;
+    }
+    // ---- read back and write the half spectrum, 32 columns at a time
+    const float unscale = ldexpf(1.0f, -(sa + sb));
+    float *out = coef + (p < P_total ? p : 0) * nout;
+    for (int piece = 0; piece * 32 < NP; ++piece) {
+      uint32_t v[32];
+      tc::tmem_ld32(dcol + lane_base + piece * 32, v);
+      tc::tmem_wait_ld();
+      if (p < P_total) {
+#pragma unroll
+        for (int u = 0; u < 32; u += 4) {
+          const int o = piece * 32 + u;
+          if (o < nout)
+            *reinterpret_cast<float4 *>(out + o) =
+                make_float4(__uint_as_float(v[u]) * unscale, __uint_as_float(v[u + 1]) * unscale,
+                            __uint_as_float(v[u + 2]) * unscale,
+                            __uint_as_float(v[u + 3]) * unscale);
+        }
+      }
+    }
+    tc::fence_before_sync();
+  }
+  // a group whose wait gave up may still have MMAs in flight: wait (bounded)
+  // before the accumulator columns are released
+  if (!alive && row == 0) tc::mbar_wait_bounded(bar, (iter & 1), kPjWaitNs);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * kPjRows);
+}
+
+// Reads and clears the basis's device error word (after a synchronisation).
+int take_error(const rsc_basis *b) {
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, b->err, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v != 0) e = cudaMemset(b->err, 0, sizeof v);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  return v;
+}
+
 int launch_project(const rsc_basis *b, const ImageItem *items_dev, int n_items, int64_t P_total,
                    float *coef, cudaStream_t st) {
   if (P_total == 0) return RSC_OK;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+  if (b->Bt && (reinterpret_cast<uintptr_t>(coef) & 15) == 0) {
+    const int total = pj_layout(b->NP).total;
+    cudaError_t e = cudaFuncSetAttribute(project_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, total);
+    if (e != cudaSuccess) return rsc_cuda_fail(e);
+    const int64_t tile_pairs = ((P_total + kPjRows - 1) / kPjRows + 1) / 2;
+    const unsigned grid = (unsigned)std::min<int64_t>(tile_pairs, (int64_t)nsm);
+    project_tc_kernel<<<grid, kPjThreads, total, st>>>(items_dev, n_items, P_total, b->N,
+                                                        b->npix, b->offs, b->Bt, b->KP, b->NP,
+                                                        b->sb, b->nout, coef, b->err);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
+  }
   const int64_t blocks = (P_total + 127) / 128;
   const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)nsm * 16);
   project_kernel<<<grid, 128, 0, st>>>(items_dev, n_items, P_total, b->N, b->npix, b->offs, b->Po,
@@ -288,8 +506,42 @@ int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, doub
         Po[(size_t)p * nout_pad + o + 1] = (float)(Pr[(size_t)(row + 1) * npix + p] * M_SQRT1_2);
       }
   }
+  // tensor-core operator: [NP outputs][KP pixels], scaled by 2^sb (max entry
+  // below 2^14), split into fp16 hi and lo
+  const bool tc_ok = npix <= 128 && nout <= 128 && nout % 4 == 0;
+  const int KP = (npix + 15) / 16 * 16, NP = (nout + 15) / 16 * 16;
+  int sb = 0;
+  std::vector<uint16_t> Bt;
+  if (tc_ok) {
+    std::vector<double> Pd((size_t)NP * KP, 0.0);
+    double vmax = 0.0;
+    for (int p = 0; p < npix; ++p) {
+      for (int j = 0; j < J; ++j) Pd[(size_t)(2 * j) * KP + p] = Pr[(size_t)j * npix + p];
+      for (int k = 1; k <= kmax; ++k)
+        for (int j = 0; j < J; ++j) {
+          const int row = J + 2 * ((k - 1) * J + j), o = 2 * (k * J + j);
+          Pd[(size_t)o * KP + p] = Pr[(size_t)row * npix + p] * M_SQRT1_2;
+          Pd[(size_t)(o + 1) * KP + p] = Pr[(size_t)(row + 1) * npix + p] * M_SQRT1_2;
+        }
+    }
+    for (double v : Pd) vmax = std::max(vmax, fabs(v));
+    int ev = 0;
+    (void)frexp(vmax, &ev);
+    sb = 14 - ev;
+    Bt.assign((size_t)2 * NP * KP, 0);
+    for (size_t i = 0; i < Pd.size(); ++i) {
+      const double v = ldexp(Pd[i], sb);
+      const __half hi = __float2half_rn((float)v);
+      const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
+      Bt[i] = *reinterpret_cast<const uint16_t *>(&hi);
+      Bt[Pd.size() + i] = *reinterpret_cast<const uint16_t *>(&lo);
+    }
+  }
   rsc_basis *b = new rsc_basis();
   memset(b, 0, sizeof *b);
+  b->KP = KP;
+  b->NP = NP;
+  b->sb = sb;
   b->N = N;
   b->J = J;
   b->kmax = kmax;
@@ -305,9 +557,16 @@ int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, doub
     e = cudaMemcpy(b->offs, offs.data(), offs.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(b->Po, Po.data(), Po.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
+  if (e == cudaSuccess && tc_ok) e = cudaMalloc(&b->Bt, Bt.size() * sizeof(uint16_t));
+  if (e == cudaSuccess && tc_ok)
+    e = cudaMemcpy(b->Bt, Bt.data(), Bt.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(b->offs);
     cudaFree(b->Po);
+    cudaFree(b->err);
+    cudaFree(b->Bt);
     delete b;
     if (e == cudaErrorMemoryAllocation) {
       cudaGetLastError();
@@ -323,6 +582,8 @@ int rsc_basis_destroy(rsc_basis *b) {
   if (!b) return RSC_OK;
   cudaFree(b->offs);
   cudaFree(b->Po);
+  cudaFree(b->err);
+  cudaFree(b->Bt);
   delete b;
   return RSC_OK;
 }
@@ -355,6 +616,7 @@ int rsc_project(const rsc_basis *b, const float *image, int32_t h, int32_t w, fl
   // the host copy of `it` must outlive the async copy
   e = cudaStreamSynchronize(st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
+  if (rc == RSC_OK) rc = take_error(b);
   return rc;
 }
 
@@ -401,6 +663,7 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *b, const float *con
   // the host work list must outlive its async copy
   e = cudaStreamSynchronize(st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
+  if (rc == RSC_OK) rc = take_error(b);
   return rc;
 }
 
