@@ -346,8 +346,20 @@ def measure_rksvd(rsc, torch, dev, iters: int = 20) -> dict:
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
     mse = [h["mse"] for h in hist]
+    # one coding pass and one update with the learned dictionary, timed apart
+    import paper_1806_04374_gb300 as rsc_
+    dic = rsc_.Dictionary(d, R)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    codes = rsc_.encode(dic, xd, K, "f16")
+    ev[1].record()
+    rsc_.ksvd_update(dic, xd, codes)
+    ev[2].record()
+    torch.cuda.synchronize(dev)
+    dic.close()
     return {"patches": P, "atoms_learned": M, "atoms_planted": 64, "R": R, "K": K,
             "iterations": iters, "s_per_iteration": dt / (iters + 1),
+            "encode_ms": ev[0].elapsed_time(ev[1]), "ksvd_update_ms": ev[1].elapsed_time(ev[2]),
             "mse_first": mse[0], "mse_last": mse[-1],
             "recovery_0.99": recovery(d.cpu().numpy(), d_true, R),
             "timing": "host clock around the whole loop (encode + update + sync per iteration)"}

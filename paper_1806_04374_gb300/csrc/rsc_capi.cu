@@ -135,14 +135,27 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   if (n > kTcMaxN || rows * L * 2 > ((size_t)1 << 30) ||
       (size_t)M * M * H * 16 > ((size_t)1 << 28))
     return RSC_OK;
-  // packed steered rows: slot q of row (r, m) from rsc_slot_code
+  // packed steered rows: slot q of row (r, m) from rsc_slot_code; the angle
+  // k r 2 pi / R is taken mod 2 pi through the table of the R grid angles
+  std::vector<double> cgrid(R), sgrid(R);
+  for (int i = 0; i < R; ++i) {
+    const double th = 2.0 * M_PI * (double)i / (double)R;
+    cgrid[i] = cos(th);
+    sgrid[i] = sin(th);
+  }
+  std::vector<int> codes_plain(L), codes_paired(L);
+  for (int q = 0; q < L; ++q) {
+    codes_plain[q] = rsc_slot_code(q, J, d->kmax, false);
+    codes_paired[q] = rsc_slot_code(q, J, d->kmax, true);
+  }
   auto fill_row = [&](uint16_t *row, int m, int r, bool paired) {
+    const std::vector<int> &codes = paired ? codes_paired : codes_plain;
     for (int q = 0; q < L; ++q) {
-      const int code = rsc_slot_code(q, J, d->kmax, paired);
+      const int code = codes[q];
       if (code < 0) continue;
       const int e = code >> 8, k = (code >> 1) & 127, c = code & 1;
-      const double th = 2.0 * M_PI * (double)(((int64_t)k * r) % R) / (double)R;
-      const double co = cos(th), si = sin(th);
+      const int ia = (int)(((int64_t)k * r) % R);
+      const double co = cgrid[ia], si = sgrid[ia];
       const double dre = h[((size_t)m * HJ + e) * 2];
       const double dim = k ? h[((size_t)m * HJ + e) * 2 + 1] : 0.0;
       const double re = co * dre + si * dim, im = co * dim - si * dre;  // e^{-ik theta} d
