@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(256)
         float tv[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
         int ti[4] = {-1, -1, -1, -1};
         float disc = -INFINITY;
+        const float win2 = 2.0f * err_per_norm * rnorm;
         for (int mc = 0; mc < M; mc += kChunk) {
           const int mend = min(kChunk, M - mc);
           // (a) one lane per atom: G_k = sum_j conj(d[j,k]) r[j,k]
@@ -312,7 +313,10 @@ __global__ void __launch_bounds__(256)
                 sb = fmaf(gv[2 * k + 2], ts[i][k], sb);
               }
               const int r = lane + 32 * i;
-              if (r < R) top4_insert(tv, ti, disc, fabsf(sa + sb), (mc + ml) * R + r);
+              const float v = fabsf(sa + sb);
+              // a value more than 2E below this lane's running best is below
+              // the final window and need not be kept (the best only grows)
+              if (r < R && !(v < tv[0] - win2)) top4_insert(tv, ti, disc, v, (mc + ml) * R + r);
             }
           }
           __syncwarp();
