@@ -39,7 +39,8 @@ struct Layout {
   int dT_off;             // transposed atoms [2][HJ][M] or -1 (read from global)
   // per-warp
   int warp_off, warp_bytes;
-  int x_off, rhi_off, rlo_off, g_off, cand_off, L_off, z_off, a_off, adf_off, sel_off, gram_off;
+  int x_off, rhi_off, rlo_off, g_off, cand_off, L_off, inv_off, z_off, a_off, adf_off, sel_off,
+      gram_off;
   int acache_off;  // [K][HJ] float4: steered selected atoms (re hi, re lo, im hi, im lo)
   int total;
 };
@@ -65,6 +66,7 @@ __host__ __device__ inline Layout make_layout(int M, int J, int H, int R, int K,
   L.g_off = w;    w = align16(w + kChunk * GStride<KM>::v * 4);
   L.cand_off = w; w = align16(w + kCandCap * 4);
   L.L_off = w;    w = align16(w + K * (K + 1) / 2 * 8);
+  L.inv_off = w;  w = align16(w + K * 8);
   L.z_off = w;    w = align16(w + K * 8);
   L.a_off = w;    w = align16(w + K * 8);
   L.adf_off = w;  w = align16(w + 2 * K * 4);
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(256)
   float *s_g = reinterpret_cast<float *>(wbase + Lo.g_off);
   int *s_cand = reinterpret_cast<int *>(wbase + Lo.cand_off);
   double *s_L = reinterpret_cast<double *>(wbase + Lo.L_off);
+  double *s_inv = reinterpret_cast<double *>(wbase + Lo.inv_off);  // 1 / L_ii
   double *s_z = reinterpret_cast<double *>(wbase + Lo.z_off);
   double *s_a = reinterpret_cast<double *>(wbase + Lo.a_off);
   float *s_adf = reinterpret_cast<float *>(wbase + Lo.adf_off);
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(256)
           const double *Li = s_L + i * (i + 1) / 2;
           double v = s_gram[K + 1 + i];
           for (int j = 0; j < i; ++j) v -= Li[j] * Lt[j];
-          v /= Li[i];
+          v *= s_inv[i];
           Lt[i] = v;
           p2 -= v * v;
         }
@@ -415,14 +418,15 @@ __global__ void __launch_bounds__(256)
           ok = 1;
           const double ltt = sqrt(p2);
           Lt[t] = ltt;
+          s_inv[t] = 1.0 / ltt;
           double zt = rhs;
           for (int i = 0; i < t; ++i) zt -= Lt[i] * s_z[i];
-          s_z[t] = zt / ltt;
+          s_z[t] = zt * s_inv[t];
           // back substitution L^T a = z over the t+1 selected atoms
           for (int i = t; i >= 0; --i) {
             double v = s_z[i];
             for (int q = i + 1; q <= t; ++q) v -= s_L[q * (q + 1) / 2 + i] * s_a[q];
-            v /= s_L[i * (i + 1) / 2 + i];
+            v *= s_inv[i];
             s_a[i] = v;
             const float hi = __double2float_rn(v);
             s_adf[2 * i] = hi;
