@@ -176,8 +176,8 @@ def source_digest(names=SCORE_SOURCES) -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(P: int):
-    """DRAM bytes per launch of the scoring kernel at P patches, from the
+def recorded_traffic(P: float):
+    """DRAM bytes per launch of the scoring kernel for a launch over P patches, from the
     committed ncu summary (dram__bytes_read.sum + dram__bytes_write.sum of one
     capture, per patch, scaled to P: the kernel's traffic is linear in the
     patches it reads and writes), or None when the kernel's sources changed
@@ -677,7 +677,8 @@ def main():
                 "peak": peak,
                 "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": recorded_traffic(P) if args.precision == "f16" else None,
+                "traffic": (recorded_traffic(P * args.steps / n_launch)
+                            if args.precision == "f16" else None),
                 "flops_per_patch": fl["per_patch"],
                 "flops_convention": "(a) 2J(1+4kmax)M + (b) 2.5 R log2 R M per patch-step, x K",
                 "kernel_ms": launch_s * 1e3,
