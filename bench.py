@@ -339,6 +339,9 @@ def measure_rksvd(rsc, torch, dev, iters: int = 20) -> dict:
     d0[:, 0, :, 1] = 0.0
     d0 /= np.sqrt(synth.coef_norm2(d0))[:, None, None, None]
     xd = torch.from_numpy(x).to(dev)
+    # warm-up on a slice (loads the library's and torch's kernels once)
+    rksvd.learn(xd[:8192], torch.from_numpy(d0.astype(np.float32)).to(dev), R, K, iters=1,
+                precision="f16")
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     d, _, hist = rksvd.learn(xd, torch.from_numpy(d0.astype(np.float32)).to(dev), R, K,
