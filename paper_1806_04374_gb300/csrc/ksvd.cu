@@ -14,9 +14,10 @@
 // largest-magnitude packed entry is made positive.
 //
 // Kernels: per patch (count samples per atom, fill the per-atom sample lists,
-// packed FP32 residuals and coding errors); per atom one CTA accumulating C_m
-// (FP32 partial sums over 32 samples, folded into FP64) and one CTA running an
-// FP64 power iteration from the old atom; one CTA for the resets.  All
+// packed FP32 residuals and coding errors); per atom kCovSplit CTAs
+// accumulating C_m over slices of its samples (4 x 4 register tiles, FP32
+// partial sums over 32 samples folded into FP64, FP64 atomics) and one CTA
+// running an FP64 power iteration from the old atom; one CTA for the resets.  All
 // vectors are packed reals (k = 0 real parts, sqrt(2) Re/Im of k >= 1).
 #include <math.h>
 
@@ -127,43 +128,47 @@ __global__ void ksvd_fill_kernel(const KsvdArgs a) {
   }
 }
 
-// C_m = sum over the atom's samples of y y^T (upper triangle, then mirrored).
+// C_m = sum over the atom's samples of y y^T.  The samples of atom m are
+// split over kCovSplit CTAs; each thread owns 4 x 4 tiles of the upper
+// triangle (two float4 reads of a sample row feed 16 FMAs), sums 32 samples
+// in FP32, folds them into FP64, and adds its tiles to C with FP64 atomics
+// (C starts at zero).
+constexpr int kCovSplit = 8;
+
 __global__ void __launch_bounds__(kCovThreads) ksvd_cov_kernel(const KsvdArgs a) {
-  extern __shared__ float ysm[];  // kCovBatch rows of n + 1 floats
-  const int m = blockIdx.x;
+  extern __shared__ __align__(16) float ysm[];  // kCovBatch rows of ldy floats
+  const int m = blockIdx.x / kCovSplit, part = blockIdx.x - m * kCovSplit;
   const int n = a.n, J = a.J, H = a.H, HJ = H * J, R = a.R;
-  const int ldy = n + 1;
+  const int nb4 = (n + 3) / 4, ldy = 4 * nb4 + 4;  // +4: rows start in different banks
   auto ys = [&](int s, int q) -> float & { return ysm[s * ldy + q]; };
-  const int beg = a.offset[m], end = a.offset[m + 1];
-  const int ntri = n * (n + 1) / 2;
+  const int beg0 = a.offset[m], cnt = a.offset[m + 1] - beg0;
+  const int per = (cnt + kCovSplit - 1) / kCovSplit;
+  const int beg = beg0 + part * per, end = min(beg0 + cnt, beg + per);
+  if (beg >= end) return;
   double *Cm = a.C + (size_t)m * n * n;
-  // this thread's entries of the upper triangle: t = t0 + u * 256 + tid
-  for (int t0 = 0; t0 < ntri; t0 += kCovThreads * 24) {
-    // up to 24 entries per thread per pass (registers)
-    double acc[24];
-    int ii[24], jj[24];
-#pragma unroll
-    for (int u = 0; u < 24; ++u) {
-      acc[u] = 0.0;
-      const int t = t0 + u * kCovThreads + threadIdx.x;
-      int i = -1, j = -1;
-      if (t < ntri) {
-        // row i of the upper triangle starts at i*n - i(i-1)/2
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (mid * n - mid * (mid - 1) / 2 <= t) lo = mid; else hi = mid - 1;
-        }
-        i = lo;
-        j = i + (t - (i * n - i * (i - 1) / 2));
+  const int ntiles = nb4 * (nb4 + 1) / 2;
+  for (int t = threadIdx.x; t - threadIdx.x < ntiles; t += kCovThreads) {
+    // tile (bi, bj), bi <= bj, of the upper triangle (row bi starts at
+    // bi*nb4 - bi(bi-1)/2)
+    int bi = -1, bj = -1;
+    if (t < ntiles) {
+      int lo = 0, hi = nb4 - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mid * nb4 - mid * (mid - 1) / 2 <= t) lo = mid; else hi = mid - 1;
       }
-      ii[u] = i;
-      jj[u] = j;
+      bi = lo;
+      bj = bi + (t - (bi * nb4 - bi * (bi - 1) / 2));
     }
+    double acc[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u] = 0.0;
     for (int b0 = beg; b0 < end; b0 += kCovBatch) {
       const int nb = min(kCovBatch, end - b0);
       __syncthreads();
-      // build y for the batch: y = S_{-r0} e_p + a_{i0} d_m (packed)
+      // build y for the batch: y = S_{-r0} e_p + a_{i0} d_m (packed; zero pad)
+      for (int w = threadIdx.x; w < nb * ldy; w += blockDim.x) ysm[w] = 0.0f;
+      __syncthreads();
       for (int w = threadIdx.x; w < nb * HJ; w += blockDim.x) {
         const int s = w / HJ, e = w - s * HJ;
         const int2 smp = a.samples[b0 + s];
@@ -191,19 +196,34 @@ __global__ void __launch_bounds__(kCovThreads) ksvd_cov_kernel(const KsvdArgs a)
         }
       }
       __syncthreads();
+      if (bi >= 0) {
+        float part16[16];
 #pragma unroll
-      for (int u = 0; u < 24; ++u) {
-        if (ii[u] < 0) continue;
-        float part = 0.0f;
-        for (int s = 0; s < nb; ++s) part = fmaf(ys(s, ii[u]), ys(s, jj[u]), part);
-        acc[u] += (double)part;
+        for (int u = 0; u < 16; ++u) part16[u] = 0.0f;
+        for (int s = 0; s < nb; ++s) {
+          const float4 yi = *reinterpret_cast<const float4 *>(&ysm[s * ldy + 4 * bi]);
+          const float4 yj = *reinterpret_cast<const float4 *>(&ysm[s * ldy + 4 * bj]);
+          const float vi[4] = {yi.x, yi.y, yi.z, yi.w}, vj[4] = {yj.x, yj.y, yj.z, yj.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) part16[u * 4 + v] = fmaf(vi[u], vj[v], part16[u * 4 + v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] += (double)part16[u];
       }
     }
+    if (bi >= 0) {
 #pragma unroll
-    for (int u = 0; u < 24; ++u) {
-      if (ii[u] < 0) continue;
-      Cm[(size_t)ii[u] * n + jj[u]] = acc[u];
-      Cm[(size_t)jj[u] * n + ii[u]] = acc[u];
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int i = 4 * bi + u, j = 4 * bj + v;
+          if (i < n && j < n && i <= j) {
+            atomicAdd(Cm + (size_t)i * n + j, acc[u * 4 + v]);
+            if (i != j) atomicAdd(Cm + (size_t)j * n + i, acc[u * 4 + v]);
+          }
+        }
     }
   }
 }
@@ -425,10 +445,11 @@ extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, 
     ksvd_count_kernel<<<grid, 256, 0, st>>>(a);
     ksvd_scan_kernel<<<1, 32, 0, st>>>(a);
     ksvd_fill_kernel<<<grid, 256, 0, st>>>(a);
-    const size_t cov_smem = (size_t)kCovBatch * (n + 1) * 4;
+    const size_t cov_smem = (size_t)kCovBatch * (4 * ((n + 3) / 4) + 4) * 4;
     e = cudaFuncSetAttribute(ksvd_cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cov_smem);
-    if (e == cudaSuccess) ksvd_cov_kernel<<<M, kCovThreads, cov_smem, st>>>(a);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.C, 0, (size_t)M * n * n * 8, st);
+    if (e == cudaSuccess) ksvd_cov_kernel<<<M * kCovSplit, kCovThreads, cov_smem, st>>>(a);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(ksvd_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)eig_smem);
