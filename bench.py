@@ -680,7 +680,7 @@ def main():
                 "peak": peak,
                 "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": (recorded_traffic(P * args.steps / n_launch)
+                "traffic": (recorded_traffic(P * args.steps * wl.K / n_launch)
                             if args.precision == "f16" else None),
                 "flops_per_patch": fl["per_patch"],
                 "flops_convention": "(a) 2J(1+4kmax)M + (b) 2.5 R log2 R M per patch-step, x K",

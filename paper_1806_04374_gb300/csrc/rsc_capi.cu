@@ -80,11 +80,6 @@ void free_dict(rsc_dict *d) {
   delete d;
 }
 
-// fp16 bits of kDictScale * v (rounded once, from double)
-uint16_t f16_bits(double v) {
-  const __half b = __double2half(v * (double)kDictScale);
-  return *reinterpret_cast<const uint16_t *>(&b);
-}
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -120,12 +115,83 @@ int encode_rows_map(CUtensorMap *map, void *base, size_t rows, int box_rows, int
   return RSC_OK;
 }
 
+// Packed steered rows (rsc_slot_code layout): entry q of row r*M + m,
+// r < nR, is slot q of kDictScale S_r d_m in fp16, computed in FP64 from the
+// atoms; the angle k r 2 pi / R is reduced exactly (k r mod R).
+__global__ void steered_rows_kernel(const float *__restrict__ d, int M, int J, int kmax, int R,
+                                    int nR, int L, int paired, uint16_t *out) {
+  const int HJ = (kmax + 1) * J;
+  const int64_t total = (int64_t)nR * M * L;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % L);
+    const int64_t row = idx / L;
+    const int m = (int)(row % M), r = (int)(row / M);
+    const int code = rsc_slot_code(q, J, kmax, paired != 0);
+    uint16_t bits = 0;
+    if (code >= 0) {
+      const int e = code >> 8, k = (code >> 1) & 127, c = code & 1;
+      const double th = 2.0 * M_PI * (double)(int)(((int64_t)k * r) % R) / (double)R;
+      const double co = cos(th), si = sin(th);
+      const double dre = d[((size_t)m * HJ + e) * 2];
+      const double dim = k ? (double)d[((size_t)m * HJ + e) * 2 + 1] : 0.0;
+      const double re = co * dre + si * dim, im = co * dim - si * dre;  // e^{-ik theta} d
+      const double v = (k == 0 ? re : M_SQRT2 * (c ? im : re)) * (double)kDictScale;
+      const __half hv = __double2half(v);
+      bits = *reinterpret_cast<const uint16_t *>(&hv);
+    }
+    out[idx] = bits;
+  }
+}
+
+// Cross-Gram table H_k(a, b) = sum_j conj(d_a[j,k]) d_b[j,k] in FP64, stored
+// as double-float (re hi, re lo, im hi, im lo) at [(a M + b) H + k].
+__global__ void xgram_kernel(const float *__restrict__ d, int M, int J, int H,
+                             float4 *__restrict__ X) {
+  const int HJ = H * J;
+  const int64_t total = (int64_t)M * M * H;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % H);
+    const int64_t ab = idx / H;
+    const int mb = (int)(ab % M), ma = (int)(ab / M);
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < J; ++j) {
+      const double ar = d[((size_t)ma * HJ + k * J + j) * 2];
+      const double ai = k ? (double)d[((size_t)ma * HJ + k * J + j) * 2 + 1] : 0.0;
+      const double br = d[((size_t)mb * HJ + k * J + j) * 2];
+      const double bi = k ? (double)d[((size_t)mb * HJ + k * J + j) * 2 + 1] : 0.0;
+      re += ar * br + ai * bi;
+      im += ar * bi - ai * br;
+    }
+    const float rh = (float)re, ih = (float)im;
+    X[idx] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+  }
+}
+
+// ||d_m||^2 in FP64, stored as double-float.
+__global__ void anorm_kernel(const float *__restrict__ d, int M, int J, int H,
+                             float2 *__restrict__ NA) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int HJ = H * J;
+  double n2 = 0.0;
+  for (int k = 0; k < H; ++k)
+    for (int j = 0; j < J; ++j) {
+      const double re = d[((size_t)m * HJ + k * J + j) * 2];
+      const double im = k ? (double)d[((size_t)m * HJ + k * J + j) * 2 + 1] : 0.0;
+      n2 += (k ? 2.0 : 1.0) * (re * re + im * im);
+    }
+  const float hi = (float)n2;
+  NA[m] = make_float2(hi, (float)(n2 - (double)hi));
+}
+
 // Tables of the tensor-core path: the packed steered dictionary (fp16 of
 // kDictScale times the entries, row r*M + m = S_r d_m, angle-major so that 32 consecutive rows hold different
 // atoms; the packed layout described in rsc_internal.h), the
 // per-harmonic cross-Gram table H_k(a, b) in double-float and the TMA map.
 // Returns RSC_OK also when the sizes are outside the path (tables left null).
-int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
+int build_tc_tables(rsc_dict *d, cudaStream_t st) {
   const int M = d->M, J = d->J, H = d->H, R = d->R, HJ = H * J;
   const int n = J + 2 * d->kmax * J;
   d->n = n;
@@ -135,93 +201,34 @@ int build_tc_tables(rsc_dict *d, const std::vector<float> &h, cudaStream_t st) {
   if (n > kTcMaxN || rows * L * 2 > ((size_t)1 << 30) ||
       (size_t)M * M * H * 16 > ((size_t)1 << 28))
     return RSC_OK;
-  // packed steered rows: slot q of row (r, m) from rsc_slot_code; the angle
-  // k r 2 pi / R is taken mod 2 pi through the table of the R grid angles
-  std::vector<double> cgrid(R), sgrid(R);
-  for (int i = 0; i < R; ++i) {
-    const double th = 2.0 * M_PI * (double)i / (double)R;
-    cgrid[i] = cos(th);
-    sgrid[i] = sin(th);
-  }
-  std::vector<int> codes_plain(L), codes_paired(L);
-  for (int q = 0; q < L; ++q) {
-    codes_plain[q] = rsc_slot_code(q, J, d->kmax, false);
-    codes_paired[q] = rsc_slot_code(q, J, d->kmax, true);
-  }
-  auto fill_row = [&](uint16_t *row, int m, int r, bool paired) {
-    const std::vector<int> &codes = paired ? codes_paired : codes_plain;
-    for (int q = 0; q < L; ++q) {
-      const int code = codes[q];
-      if (code < 0) continue;
-      const int e = code >> 8, k = (code >> 1) & 127, c = code & 1;
-      const int ia = (int)(((int64_t)k * r) % R);
-      const double co = cgrid[ia], si = sgrid[ia];
-      const double dre = h[((size_t)m * HJ + e) * 2];
-      const double dim = k ? h[((size_t)m * HJ + e) * 2 + 1] : 0.0;
-      const double re = co * dre + si * dim, im = co * dim - si * dre;  // e^{-ik theta} d
-      row[q] = f16_bits(k == 0 ? re : M_SQRT2 * (c ? im : re));
-    }
-  };
-  std::vector<uint16_t> B(rows * L, 0);
-  for (int m = 0; m < M; ++m)
-    for (int r = 0; r < R; ++r) fill_row(&B[((size_t)r * M + m) * L], m, r, false);
   const bool paired = L == kTcKst && rsc_paired_ok(J, d->kmax, R);
-  std::vector<uint16_t> BP;
   if (paired) {
     int ne, no;
     rsc_paired_counts(J, d->kmax, &ne, &no);
     d->ke = (ne + 15) / 16;
     d->ko = (no + 15) / 16;
-    BP.assign(rows / 2 * kTcKst, 0);
-    for (int m = 0; m < M; ++m)
-      for (int r = 0; r < R / 2; ++r) fill_row(&BP[((size_t)r * M + m) * kTcKst], m, r, true);
   }
-  std::vector<float4> X((size_t)M * M * H);
-  for (int ma = 0; ma < M; ++ma)
-    for (int mb = 0; mb < M; ++mb)
-      for (int k = 0; k < H; ++k) {
-        double re = 0.0, im = 0.0;
-        for (int j = 0; j < J; ++j) {
-          const double ar = h[((size_t)ma * HJ + k * J + j) * 2];
-          const double ai = k ? h[((size_t)ma * HJ + k * J + j) * 2 + 1] : 0.0;
-          const double br = h[((size_t)mb * HJ + k * J + j) * 2];
-          const double bi = k ? h[((size_t)mb * HJ + k * J + j) * 2 + 1] : 0.0;
-          re += ar * br + ai * bi;  // conj(a) b
-          im += ar * bi - ai * br;
-        }
-        const float rh = (float)re, ih = (float)im;
-        X[((size_t)ma * M + mb) * H + k] =
-            make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
-      }
-  std::vector<float2> NA(M);
-  for (int m = 0; m < M; ++m) {
-    double n2 = 0.0;
-    for (int k = 0; k < H; ++k)
-      for (int j = 0; j < J; ++j) {
-        const double re = h[((size_t)m * HJ + k * J + j) * 2];
-        const double im = k ? h[((size_t)m * HJ + k * J + j) * 2 + 1] : 0.0;
-        n2 += (k ? 2.0 : 1.0) * (re * re + im * im);
-      }
-    const float hi = (float)n2;
-    NA[m] = make_float2(hi, (float)(n2 - (double)hi));
-  }
-  cudaError_t e = cudaMalloc(&d->steered_f16, B.size() * 2);
-  if (e == cudaSuccess && paired) e = cudaMalloc(&d->paired_f16, BP.size() * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&d->xgram, X.size() * sizeof(float4));
-  if (e == cudaSuccess) e = cudaMalloc(&d->anorm, NA.size() * sizeof(float2));
+  cudaError_t e = cudaMalloc(&d->steered_f16, rows * L * 2);
+  if (e == cudaSuccess && paired) e = cudaMalloc(&d->paired_f16, rows / 2 * kTcKst * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&d->xgram, (size_t)M * M * H * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc(&d->anorm, (size_t)M * sizeof(float2));
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d->steered_f16, B.data(), B.size() * 2, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && paired)
-    e = cudaMemcpyAsync(d->paired_f16, BP.data(), BP.size() * 2, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d->xgram, X.data(), X.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d->anorm, NA.data(), NA.size() * sizeof(float2), cudaMemcpyHostToDevice,
-                        st);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  // the tables are built on the device from the uploaded atoms (FP64 arithmetic)
+  const int T = 256;
+  const int64_t nb = (int64_t)rows * L, np = paired ? (int64_t)rows / 2 * kTcKst : 0;
+  steered_rows_kernel<<<(unsigned)((nb + T - 1) / T), T, 0, st>>>(
+      d->d, M, J, d->kmax, R, R, L, 0, static_cast<uint16_t *>(d->steered_f16));
+  if (paired)
+    steered_rows_kernel<<<(unsigned)((np + T - 1) / T), T, 0, st>>>(
+        d->d, M, J, d->kmax, R, R / 2, kTcKst, 1, static_cast<uint16_t *>(d->paired_f16));
+  const int64_t nx = (int64_t)M * M * H;
+  xgram_kernel<<<(unsigned)((nx + T - 1) / T), T, 0, st>>>(d->d, M, J, H, d->xgram);
+  anorm_kernel<<<(M + T - 1) / T, T, 0, st>>>(d->d, M, J, H, d->anorm);
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
 
@@ -463,7 +470,7 @@ int rsc_dict_create(const float *coef, rsc_dims dims, void *stream, rsc_dict **o
     free_dict(d);
     return rsc_cuda_fail(e);
   }
-  const int rc = build_tc_tables(d, h, st);
+  const int rc = build_tc_tables(d, st);
   if (rc != RSC_OK) {
     free_dict(d);
     return rc;
