@@ -47,6 +47,34 @@ def test_project_matches_oracle(rsc, shape):
     b.close()
 
 
+def test_project_unaligned_output_and_scales(rsc):
+    """The tensor-core projection writes 16-byte vectors; an output buffer that
+    is not 16-byte aligned takes the CUDA-core kernel instead, with the same
+    result.  Images far outside fp16's range (1e-20 and 1e20 times the test
+    image) are projected like the oracle does (per-window power-of-two
+    scaling)."""
+    import ctypes
+    import torch
+    N, J, kmax = 11, 6, 8
+    b = rsc.Basis(N, J, kmax)
+    img = image(N + 9, N + 14, 8)
+    ref = obasis.project(img, N, J, kmax)
+    P = ref.shape[0]
+    t = torch.from_numpy(img).cuda()
+    buf = torch.zeros(P * (kmax + 1) * J * 2 + 1, dtype=torch.float32, device="cuda")
+    st = rsc.load_library().rsc_project(ctypes.c_void_p(b.handle), ctypes.c_void_p(t.data_ptr()),
+                                        img.shape[0], img.shape[1],
+                                        ctypes.c_void_p(buf.data_ptr() + 4), ctypes.c_void_p(0))
+    assert st == 0
+    got = buf[1:].cpu().numpy().reshape(ref.shape)
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 2e-5
+    for scale in (1e-20, 1e20):
+        got = rsc.project(b, (t.double() * scale).float()).cpu().numpy().astype(np.float64)
+        refs = obasis.project((img.astype(np.float64) * scale).astype(np.float32), N, J, kmax)
+        assert np.abs(got - refs).max() / np.abs(refs).max() < 2e-5, scale
+    b.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "f16"])
 def test_encode_uneven_images(rsc, precision):
     """Images of different sizes (one smaller than a window) coded in one
