@@ -554,10 +554,12 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    def timed(precision: str, sample_clocks: bool):
+    def timed(precision: str, sample_clocks: bool, timing_mode: int = 1, steps: int = 0):
         """W warm-up steps, then K timed steps between barriers; returns the
         step times, the max-over-ranks total, clocks, hand-offs and the
-        per-kernel event times recorded by the library."""
+        per-kernel event times recorded by the library (timing_mode 2: the
+        FP16 path's two halves run one after the other)."""
+        steps = steps or args.steps
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
                 rsc.encode(dic, xd, K, precision, stream=stream, out=out)
@@ -565,23 +567,23 @@ def main():
             if rsc.rsc_dict_check(dic.handle, int(stream.cuda_stream)) != 0:
                 raise RuntimeError("device-side error during warm-up")
             rsc.rsc_dict_fallback_count(dic.handle)
-            rsc.rsc_dict_set_timing(dic.handle, True)
+            rsc.rsc_dict_set_timing(dic.handle, timing_mode)
             rsc.rsc_dict_timing(dic.handle)
             barrier()
             torch.cuda.synchronize(dev)
             clocks = ClockSampler(dev.index if dev.index is not None else 0) if sample_clocks else None
-            evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
             if clocks:
                 clocks.start()
             evs[0].record(stream)
-            for s in range(args.steps):
+            for s in range(steps):
                 rsc.encode(dic, xd, K, precision, stream=stream, out=out)
                 evs[s + 1].record(stream)
             stream.synchronize()
             torch.cuda.synchronize(dev)
             barrier()
             clk = clocks.stop() if clocks else None
-        step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
         total_ms = evs[0].elapsed_time(evs[-1])
         if rsc.rsc_dict_check(dic.handle, int(stream.cuda_stream)) != 0:
             raise RuntimeError("device-side error during the timed steps")
@@ -596,6 +598,8 @@ def main():
                 "kernel_ms": kms, "kernel_launches": kn}
 
     main_run = timed(args.precision, True)
+    # the same steps with the two halves serialised: each kernel timed alone
+    iso_run = timed(args.precision, False, timing_mode=2, steps=min(args.steps, 10))
     cmp_run = None
     if args.precision != "fp32" and not args.no_fp32_compare:
         cmp_run = timed("fp32", False)
@@ -700,6 +704,18 @@ def main():
                                    "refine": main_run["kernel_ms"][2] / args.steps},
             "clocks": clk,
         }
+        n_iso = max(iso_run["kernel_launches"][0], 1)
+        iso_steps = min(args.steps, 10)
+        iso_launch_s = iso_run["kernel_ms"][0] / n_iso / 1e3
+        iso_flops = fl["per_patch"] * P * iso_steps / n_iso
+        line["roofline_isolated"] = {
+            "kernel": kname, "bound": bound, "achieved": iso_flops / iso_launch_s / 1e12,
+            "peak": peak, "unit": "TFLOP/s",
+            "frac": iso_flops / iso_launch_s / 1e12 / peak,
+            "kernel_ms": iso_launch_s * 1e3, "flops_per_launch": iso_flops,
+            "ms_per_step": iso_run["total_ms"] / iso_steps,
+            "note": "same kernel, its launches timed with the two halves of the patches run one "
+                    "after the other on one stream (the headline run overlaps them)"}
         if args.precision == "f16":
             mf = mma_flops_per_patch(wl)
             mtf = mf * P * args.steps / n_launch / launch_s / 1e12

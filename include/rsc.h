@@ -240,14 +240,20 @@ int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t P, int32_t 
  */
 int rsc_dict_check(const rsc_dict *dict, void *stream);
 
-/* Count of patch-steps, since the last call, in which the scoring pass left
- * more candidates within its error bound than it keeps, so that the step was
- * decided by an exact re-scan of all M*R candidates (diagnostic; resets). */
+/* Diagnostic count since the last call (resets): on the FP32 path, the
+ * patch-steps in which a lane discarded a candidate inside the error bound,
+ * so that the step was decided by an exact re-scan of all M*R candidates; on
+ * the FP16 path, the patches whose certification window held more than the
+ * kept candidates and which were finished by the FP32 path. */
 int rsc_dict_fallback_count(const rsc_dict *dict, int64_t *count);
 
 /*
- * Per-phase timing (diagnostic).  While enabled, every rsc_encode on `dict`
- * records CUDA events on its stream around each kernel it launches.
+ * Per-phase timing (diagnostic).  While enabled (enable != 0), every
+ * rsc_encode on `dict` records CUDA events around each kernel it launches, on
+ * the stream that launches it.  The FP16 path normally codes two halves of the
+ * patches on two streams so that their kernels overlap; with enable = 2 the
+ * halves run one after the other on the call's stream, so that each launch's
+ * time is the kernel's alone (enable = 1 keeps the overlap).
  * rsc_dict_timing waits for those events, returns the summed milliseconds
  * and launch counts per phase since the last call, and clears them.
  * Phases: 0 = scoring kernel of the call's path (the FP32 kernel, or the

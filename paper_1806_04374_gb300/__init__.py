@@ -170,8 +170,10 @@ def rsc_dict_fallback_count(handle: int) -> int:
     return v.value
 
 
-def rsc_dict_set_timing(handle: int, enable: bool) -> int:
-    return load_library().rsc_dict_set_timing(ctypes.c_void_p(handle), int(bool(enable)))
+def rsc_dict_set_timing(handle: int, enable) -> int:
+    """enable: False/0 off, True/1 on, 2 on with the FP16 path's halves run
+    one after the other (each kernel timed alone)."""
+    return load_library().rsc_dict_set_timing(ctypes.c_void_p(handle), int(enable))
 
 
 def rsc_dict_timing(handle: int):

@@ -541,6 +541,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   // pass of another (latency-bound), so each hides part of the other.
   int G = (int)(P / kGroupMin);
   G = G < 1 ? 1 : (G > kMaxGroups ? kMaxGroups : G);
+  if (dict->timing == 2) G = 1;  // timing of each kernel alone
   int64_t Pg[kMaxGroups] = {};
   size_t bytes[kMaxGroups] = {}, total = 0;
   for (int g = 0, left = G; g < G; ++g, --left) {
@@ -697,7 +698,7 @@ int rsc_dict_check(const rsc_dict *dict, void *stream) {
 
 int rsc_dict_set_timing(rsc_dict *dict, int enable) {
   if (!dict) return RSC_ERR_INVALID;
-  dict->timing = enable ? 1 : 0;
+  dict->timing = enable == 2 ? 2 : (enable ? 1 : 0);
   return RSC_OK;
 }
 
