@@ -130,8 +130,9 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
  * codes.  Readings of the paper: a patch using m more than once contributes
  * its occurrence with the largest |weight| (ties: earliest); an atom used by
  * no patch is reset to the unit-normalised patch with the largest coding
- * error (several: successive patches in descending error, at most 64
- * distinct); the largest-magnitude packed entry of each new atom is positive.
+ * error (several: successive patches in descending error; at most 64
+ * resets, further unused atoms keep their old value); the largest-magnitude
+ * packed entry of each new atom is positive.
  *   dict      : the dictionary the codes refer to.
  *   x         : device, P x (kmax+1) x J x 2 floats (the coded patches).
  *   P, K      : patches (>= 1) and code length (1..16).
@@ -145,6 +146,45 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
 int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
                     const int32_t *atom, const int32_t *angle_idx, const double *coef,
                     float *new_coef, int32_t *n_used, void *stream);
+
+/*
+ * rsc_ksvd_accumulate / rsc_ksvd_finish -- rsc_ksvd_update in two halves, for
+ * patches spread over several GPUs (the one exchange step of the R-K-SVD
+ * iteration, Fig. "code": every atom's columns come from every patch).  Each
+ * rank accumulates over its own patches; the caller sums C and count over the
+ * ranks (an all-reduce), merges the ranks' top lists into one list in
+ * descending error (ties: smaller global patch index) and calls finish with
+ * the sums on every rank; with one rank this is exactly rsc_ksvd_update.
+ * rsc_ksvd_accumulate:
+ *   dict, x, P, K, atom, angle_idx, coef : as rsc_ksvd_update (this rank's
+ *               patches and codes).
+ *   C         : device double [M][n][n] output, n = J (2 kmax + 1): the sum
+ *               over this rank's columns of y y^T in the packed coordinates
+ *               (overwritten).
+ *   count     : device int32 [M] output: this rank's columns per atom.
+ *   top_err, top_idx, top_vec : device outputs, ntop entries: this rank's
+ *               patches of largest coding error ||x - D_aug b||^2 (float),
+ *               descending, ties: smaller index; their local indices (int64,
+ *               -1 past the end of a short list) and the patches
+ *               unit-normalised (float [ntop][kmax+1][J][2]).
+ *   ntop      : 0..64.
+ * rsc_ksvd_finish:
+ *   C, count  : device, the sums over the ranks.
+ *   top_idx, top_vec, ntop : device, the merged list (top_idx only tells
+ *               valid entries, >= 0, from missing ones); the i-th atom with
+ *               count 0 takes the i-th valid entry, later unused atoms keep
+ *               their old value.
+ *   new_coef, n_used : as rsc_ksvd_update (n_used = count).
+ * Both return after launch; rsc_ksvd_accumulate takes its per-patch scratch
+ * from the stream-ordered allocator, rsc_ksvd_finish allocates nothing.
+ */
+int rsc_ksvd_accumulate(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
+                        const int32_t *atom, const int32_t *angle_idx, const double *coef,
+                        double *C, int32_t *count, float *top_err, int64_t *top_idx,
+                        float *top_vec, int32_t ntop, void *stream);
+int rsc_ksvd_finish(const rsc_dict *dict, const double *C, const int32_t *count,
+                    const int64_t *top_idx, const float *top_vec, int32_t ntop, float *new_coef,
+                    int32_t *n_used, void *stream);
 
 /*
  * Steerable basis and projection (Sec. II-D; steps 1-2 of the proposed

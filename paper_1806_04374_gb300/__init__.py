@@ -32,7 +32,7 @@ EXPORTS = (
     "rsc_dict_check", "rsc_dict_fallback_count", "rsc_dict_set_timing", "rsc_dict_timing",
     "rsc_status_string", "rsc_last_cuda_error", "rsc_version", "rsc_encode_noalloc",
     "rsc_ksvd_update", "rsc_basis_create", "rsc_basis_destroy", "rsc_basis_info", "rsc_project",
-    "rsc_encode_images",
+    "rsc_encode_images", "rsc_ksvd_accumulate", "rsc_ksvd_finish",
 )
 
 
@@ -69,6 +69,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_encode_host.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.rsc_encode_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_ksvd_update.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp]
+    lib.rsc_ksvd_accumulate.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
+    lib.rsc_ksvd_finish.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp]
     lib.rsc_basis_create.argtypes = [i32, i32, i32, ctypes.c_double, ctypes.c_double,
                                      ctypes.POINTER(vp)]
     lib.rsc_basis_destroy.argtypes = [vp]
@@ -283,6 +285,51 @@ def ksvd_update(dic: Dictionary, x, codes: dict, stream=None):
                          used.data_ptr(), _stream_handle(stream))
     if st != RSC_OK:
         raise RscError(st, "rsc_ksvd_update")
+    return new, used
+
+
+KSVD_TOP = 64  # patches of largest coding error kept per rank for the atom resets
+
+
+def ksvd_accumulate(dic: Dictionary, x, codes: dict, ntop: int = KSVD_TOP, stream=None):
+    """rsc_ksvd_accumulate on CUDA tensors: this rank's share of an R-K-SVD
+    update.  Returns dict(C [M, n, n] float64, count [M] int32, top_err
+    [ntop] float32, top_idx [ntop] int64, top_vec [ntop, kmax+1, J, 2])."""
+    import torch
+    P, K = codes["atom"].shape
+    n = dic.J * (2 * dic.kmax + 1)
+    dev = x.device
+    out = {"C": torch.empty((dic.M, n, n), dtype=torch.float64, device=dev),
+           "count": torch.empty((dic.M,), dtype=torch.int32, device=dev),
+           "top_err": torch.empty((ntop,), dtype=torch.float32, device=dev),
+           "top_idx": torch.empty((ntop,), dtype=torch.int64, device=dev),
+           "top_vec": torch.empty((ntop, dic.H, dic.J, 2), dtype=torch.float32, device=dev)}
+    st = load_library().rsc_ksvd_accumulate(
+        ctypes.c_void_p(dic.handle), ctypes.c_void_p(x.data_ptr()), P, K,
+        ctypes.c_void_p(codes["atom"].data_ptr()), ctypes.c_void_p(codes["angle_idx"].data_ptr()),
+        ctypes.c_void_p(codes["coef"].data_ptr()), ctypes.c_void_p(out["C"].data_ptr()),
+        ctypes.c_void_p(out["count"].data_ptr()), ctypes.c_void_p(out["top_err"].data_ptr()),
+        ctypes.c_void_p(out["top_idx"].data_ptr()), ctypes.c_void_p(out["top_vec"].data_ptr()),
+        ntop, ctypes.c_void_p(_stream_handle(stream)))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_ksvd_accumulate")
+    return out
+
+
+def ksvd_finish(dic: Dictionary, C, count, top_idx, top_vec, stream=None):
+    """rsc_ksvd_finish on CUDA tensors (sums over the ranks and the merged
+    top list).  Returns (new atoms, n_used)."""
+    import torch
+    new = torch.empty((dic.M, dic.H, dic.J, 2), dtype=torch.float32, device=C.device)
+    used = torch.empty((dic.M,), dtype=torch.int32, device=C.device)
+    st = load_library().rsc_ksvd_finish(
+        ctypes.c_void_p(dic.handle), ctypes.c_void_p(C.data_ptr()),
+        ctypes.c_void_p(count.data_ptr()), ctypes.c_void_p(top_idx.data_ptr()),
+        ctypes.c_void_p(top_vec.data_ptr()), int(top_idx.shape[0]),
+        ctypes.c_void_p(new.data_ptr()), ctypes.c_void_p(used.data_ptr()),
+        ctypes.c_void_p(_stream_handle(stream)))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_ksvd_finish")
     return new, used
 
 

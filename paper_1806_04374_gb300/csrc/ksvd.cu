@@ -50,7 +50,15 @@ struct KsvdArgs {
   double *C;        // [M][n][n]
   float *new_coef;  // [M][H][J][2]
   int32_t *n_used;  // [M] or null
+  // the patches of largest coding error (descending, ties: smaller index),
+  // unit-normalised, for the reset of unused atoms
+  int ntop;         // entries of the list
+  float *top_err;   // [ntop]
+  int64_t *top_idx; // [ntop] patch index (-1: none)
+  float *top_vec;   // [ntop][H][J][2]
 };
+
+constexpr int kTopMax = 64;  // patches kept for the resets (unused atoms beyond: unchanged)
 
 // Occurrence i of patch p is the one that represents its atom (largest
 // |weight| among the occurrences of that atom, ties: earliest).
@@ -243,8 +251,12 @@ __device__ double block_sum(double v, double *red) {
 __global__ void __launch_bounds__(kEigThreads) ksvd_eig_kernel(const KsvdArgs a, int max_iter) {
   extern __shared__ __align__(16) double es[];
   const int m = blockIdx.x;
-  if (a.count[m] == 0) return;
   const int n = a.n, J = a.J, H = a.H, HJ = H * J;
+  if (a.count[m] == 0) {  // unused: the old atom, unless the reset replaces it
+    for (int i = threadIdx.x; i < 2 * HJ; i += blockDim.x)
+      a.new_coef[(size_t)m * HJ * 2 + i] = a.d[(size_t)m * HJ * 2 + i];
+    return;
+  }
   double *Cs = es;                 // n * n
   double *u = Cs + n * n;          // n
   double *v = u + n;               // n
@@ -311,21 +323,20 @@ __global__ void __launch_bounds__(kEigThreads) ksvd_eig_kernel(const KsvdArgs a,
   }
 }
 
-// Unused atoms: successive patches of largest coding error, unit-normalised.
-__global__ void ksvd_reset_kernel(const KsvdArgs a) {
+// The a.ntop patches of largest coding error, in descending error (ties:
+// smaller index), each unit-normalised (one CTA of 1024 threads).
+__global__ void ksvd_top_kernel(const KsvdArgs a) {
   __shared__ float bv[1024];
   __shared__ long long bi[1024];
-  __shared__ long long picked[64];
+  __shared__ long long picked[kTopMax];
   __shared__ double nrm;
   const int J = a.J, HJ = a.H * J;
-  int npicked = 0;
-  for (int m = 0; m < a.M; ++m) {
-    if (a.count[m] != 0) continue;
+  for (int t = 0; t < a.ntop; ++t) {
     float best = -1.0f;
     long long bp = -1;
     for (int64_t p = threadIdx.x; p < a.P; p += blockDim.x) {
       bool taken = false;
-      for (int q = 0; q < npicked && q < 64; ++q) taken |= (picked[q] == p);
+      for (int q = 0; q < t; ++q) taken |= (picked[q] == p);
       if (taken) continue;
       const float e = a.err[p];
       if (e > best) {
@@ -350,97 +361,107 @@ __global__ void ksvd_reset_kernel(const KsvdArgs a) {
     }
     const long long p = bi[0];
     __syncthreads();
-    if (p < 0) continue;
     if (threadIdx.x == 0) {
-      if (npicked < 64) picked[npicked] = p;
-      const float *xp = a.x + p * (int64_t)(2 * HJ);
-      double s = 0.0;
-      for (int e = 0; e < HJ; ++e) {
-        const double re = xp[2 * e], im = e < J ? 0.0 : xp[2 * e + 1];
-        s += (e < J ? 1.0 : 2.0) * (re * re + im * im);
+      picked[t] = p;
+      a.top_idx[t] = p;
+      a.top_err[t] = p >= 0 ? bv[0] : -1.0f;
+      double s2 = 0.0;
+      if (p >= 0) {
+        const float *xp = a.x + p * (int64_t)(2 * HJ);
+        for (int e = 0; e < HJ; ++e) {
+          const double re = xp[2 * e], im = e < J ? 0.0 : xp[2 * e + 1];
+          s2 += (e < J ? 1.0 : 2.0) * (re * re + im * im);
+        }
       }
-      nrm = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+      nrm = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
     }
-    ++npicked;
     __syncthreads();
-    const float *xp = a.x + p * (int64_t)(2 * HJ);
-    float *out = a.new_coef + (size_t)m * HJ * 2;
+    float *out = a.top_vec + (size_t)t * HJ * 2;
+    const float *xp = a.x + (p >= 0 ? p : 0) * (int64_t)(2 * HJ);
     for (int e = threadIdx.x; e < HJ; e += blockDim.x) {
-      out[2 * e] = (float)(xp[2 * e] * nrm);
-      out[2 * e + 1] = e < J ? 0.0f : (float)(xp[2 * e + 1] * nrm);
+      out[2 * e] = p >= 0 ? (float)(xp[2 * e] * nrm) : 0.0f;
+      out[2 * e + 1] = (p >= 0 && e >= J) ? (float)(xp[2 * e + 1] * nrm) : 0.0f;
     }
     __syncthreads();
   }
 }
 
+// Unused atoms (count 0), in atom order, take the successive entries of the
+// top list; atoms beyond the list (or beyond its valid entries) keep the
+// eigen-kernel's output, which is the old atom for an atom with no samples.
+__global__ void ksvd_reset_kernel(const KsvdArgs a) {
+  const int HJ = a.H * a.J;
+  int t = 0;
+  for (int m = 0; m < a.M; ++m) {
+    if (a.count[m] != 0) continue;
+    if (t >= a.ntop || a.top_idx[t] < 0) break;
+    const float *v = a.top_vec + (size_t)t * HJ * 2;
+    float *out = a.new_coef + (size_t)m * HJ * 2;
+    for (int i = threadIdx.x; i < 2 * HJ; i += blockDim.x) out[i] = v[i];
+    ++t;
+  }
+}
+
 }  // namespace
 
-extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
-                               const int32_t *atom, const int32_t *angle_idx, const double *coef,
-                               float *new_coef, int32_t *n_used, void *stream) {
-  if (!dict || P < 1 || K < 1 || K > kMaxK || !x || !atom || !angle_idx || !coef || !new_coef)
-    return RSC_ERR_INVALID;
+namespace {
+
+// Checks shared by the entry points; fills the sizes of `a`.
+int ksvd_setup(const rsc_dict *dict, int64_t P, int K, KsvdArgs &a) {
+  if (!dict || P < 1 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
   if (P >= ((int64_t)1 << 31)) return RSC_ERR_UNSUPPORTED;
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   if (dev != dict->device) return RSC_ERR_INVALID;
-  const int M = dict->M, J = dict->J, H = dict->H, R = dict->R;
-  const int n = J + 2 * dict->kmax * J;
-  if (n > kMaxPacked) return RSC_ERR_UNSUPPORTED;
-  // the unused-atom reset keeps at most 64 picks
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int ldE = (n + 3) & ~3;
+  a = KsvdArgs{};
+  a.P = P;
+  a.K = K;
+  a.M = dict->M;
+  a.J = dict->J;
+  a.H = dict->H;
+  a.R = dict->R;
+  a.n = dict->J + 2 * dict->kmax * dict->J;
+  if (a.n > kMaxPacked) return RSC_ERR_UNSUPPORTED;
+  a.ldE = (a.n + 3) & ~3;
+  a.d = dict->d;
+  a.tw = dict->tw;
+  return RSC_OK;
+}
+
+// Accumulation: sample lists, residuals, C (zeroed here) and counts, and the
+// top list of a.ntop patches; the per-patch scratch comes from one
+// stream-ordered allocation freed on `st`.
+int ksvd_accumulate(KsvdArgs &a, cudaStream_t st) {
+  const int64_t P = a.P;
+  const int M = a.M, n = a.n;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t bE = al((size_t)P * ldE * 4), bErr = al((size_t)P * 4), bCnt = al((size_t)M * 4),
-               bOff = al((size_t)(M + 1) * 4), bSmp = al((size_t)P * K * 8),
-               bC = al((size_t)M * n * n * 8);
+  const size_t bE = al((size_t)P * a.ldE * 4), bErr = al((size_t)P * 4), bCur = al((size_t)M * 4),
+               bOff = al((size_t)(M + 1) * 4), bSmp = al((size_t)P * a.K * 8);
   unsigned char *scratch = nullptr;
-  e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bE + bErr + 2 * bCnt + bOff + bSmp + bC,
-                      st);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bE + bErr + bCur + bOff + bSmp,
+                                  st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
   }
   if (e != cudaSuccess) return rsc_cuda_fail(e);
-  KsvdArgs a;
-  a.x = x;
-  a.P = P;
-  a.K = K;
-  a.M = M;
-  a.J = J;
-  a.H = H;
-  a.R = R;
-  a.n = n;
-  a.ldE = ldE;
-  a.d = dict->d;
-  a.tw = dict->tw;
-  a.atom = atom;
-  a.angle = angle_idx;
-  a.coef = coef;
   unsigned char *q = scratch;
   a.E = reinterpret_cast<float *>(q);
   q += bE;
   a.err = reinterpret_cast<float *>(q);
   q += bErr;
-  a.count = reinterpret_cast<int *>(q);
-  q += bCnt;
   a.cursor = reinterpret_cast<int *>(q);
-  q += bCnt;
+  q += bCur;
   a.offset = reinterpret_cast<int *>(q);
   q += bOff;
   a.samples = reinterpret_cast<int2 *>(q);
-  q += bSmp;
-  a.C = reinterpret_cast<double *>(q);
-  a.new_coef = new_coef;
-  a.n_used = n_used;
-
-  int rc = RSC_OK;
-  int nsm = 0;
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const unsigned grid = (unsigned)std::min<int64_t>((P + 255) / 256, (int64_t)nsm * 8);
-  const size_t eig_smem = ((size_t)n * n + 2 * n + 32) * 8;
   e = cudaMemsetAsync(a.count, 0, (size_t)M * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.C, 0, (size_t)M * n * n * 8, st);
   if (e == cudaSuccess) {
     ksvd_count_kernel<<<grid, 256, 0, st>>>(a);
     ksvd_scan_kernel<<<1, 32, 0, st>>>(a);
@@ -448,19 +469,125 @@ extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, 
     const size_t cov_smem = (size_t)kCovBatch * (4 * ((n + 3) / 4) + 4) * 4;
     e = cudaFuncSetAttribute(ksvd_cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cov_smem);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.C, 0, (size_t)M * n * n * 8, st);
     if (e == cudaSuccess) ksvd_cov_kernel<<<M * kCovSplit, kCovThreads, cov_smem, st>>>(a);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ksvd_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)eig_smem);
-    if (e == cudaSuccess) {
-      ksvd_eig_kernel<<<M, kEigThreads, eig_smem, st>>>(a, 5000);
-      ksvd_reset_kernel<<<1, 1024, 0, st>>>(a);
-      e = cudaGetLastError();
-    }
+    if (e == cudaSuccess && a.ntop > 0) ksvd_top_kernel<<<1, 1024, 0, st>>>(a);
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
-  if (e != cudaSuccess) rc = rsc_cuda_fail(e);
-  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  int rc = e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
+  const cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (rc == RSC_OK && e2 != cudaSuccess) rc = rsc_cuda_fail(e2);
   return rc;
+}
+
+// New atoms from C, the counts and the top list.
+int ksvd_finish(KsvdArgs &a, cudaStream_t st) {
+  const int n = a.n;
+  const size_t eig_smem = ((size_t)n * n + 2 * n + 32) * 8;
+  cudaError_t e = cudaFuncSetAttribute(ksvd_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)eig_smem);
+  if (e == cudaSuccess) {
+    ksvd_eig_kernel<<<a.M, kEigThreads, eig_smem, st>>>(a, 5000);
+    ksvd_reset_kernel<<<1, 256, 0, st>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && a.n_used)
+    e = cudaMemcpyAsync(a.n_used, a.count, (size_t)a.M * 4, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
+                               const int32_t *atom, const int32_t *angle_idx, const double *coef,
+                               float *new_coef, int32_t *n_used, void *stream) {
+  if (!x || !atom || !angle_idx || !coef || !new_coef) return RSC_ERR_INVALID;
+  KsvdArgs a;
+  int rc = ksvd_setup(dict, P, K, a);
+  if (rc != RSC_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int M = a.M, n = a.n, HJ = a.H * a.J;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t bC = al((size_t)M * n * n * 8), bCnt = al((size_t)M * 4),
+               bTe = al(kTopMax * 4), bTi = al(kTopMax * 8), bTv = al((size_t)kTopMax * HJ * 8);
+  unsigned char *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bC + bCnt + bTe + bTi + bTv,
+                                  st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return RSC_ERR_OOM;
+  }
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  unsigned char *q = scratch;
+  a.C = reinterpret_cast<double *>(q);
+  q += bC;
+  a.count = reinterpret_cast<int *>(q);
+  q += bCnt;
+  a.top_err = reinterpret_cast<float *>(q);
+  q += bTe;
+  a.top_idx = reinterpret_cast<int64_t *>(q);
+  q += bTi;
+  a.top_vec = reinterpret_cast<float *>(q);
+  a.ntop = kTopMax;
+  a.x = x;
+  a.atom = atom;
+  a.angle = angle_idx;
+  a.coef = coef;
+  a.new_coef = new_coef;
+  a.n_used = n_used;
+  rc = ksvd_accumulate(a, st);
+  if (rc == RSC_OK) rc = ksvd_finish(a, st);
+  e = cudaFreeAsync(scratch, st);
+  if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
+  return rc;
+}
+
+extern "C" int rsc_ksvd_accumulate(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
+                                   const int32_t *atom, const int32_t *angle_idx,
+                                   const double *coef, double *C, int32_t *count, float *top_err,
+                                   int64_t *top_idx, float *top_vec, int32_t ntop, void *stream) {
+  if (!x || !atom || !angle_idx || !coef || !C || !count) return RSC_ERR_INVALID;
+  if (ntop < 0 || ntop > kTopMax || (ntop > 0 && (!top_err || !top_idx || !top_vec)))
+    return RSC_ERR_INVALID;
+  KsvdArgs a;
+  int rc = ksvd_setup(dict, P, K, a);
+  if (rc != RSC_OK) return rc;
+  a.x = x;
+  a.atom = atom;
+  a.angle = angle_idx;
+  a.coef = coef;
+  a.C = C;
+  a.count = count;
+  a.ntop = ntop;
+  a.top_err = top_err;
+  a.top_idx = top_idx;
+  a.top_vec = top_vec;
+  return ksvd_accumulate(a, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int rsc_ksvd_finish(const rsc_dict *dict, const double *C, const int32_t *count,
+                               const int64_t *top_idx, const float *top_vec, int32_t ntop,
+                               float *new_coef, int32_t *n_used, void *stream) {
+  if (!dict || !C || !count || !new_coef) return RSC_ERR_INVALID;
+  if (ntop < 0 || ntop > kTopMax || (ntop > 0 && (!top_idx || !top_vec))) return RSC_ERR_INVALID;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  if (dev != dict->device) return RSC_ERR_INVALID;
+  KsvdArgs a{};
+  a.M = dict->M;
+  a.J = dict->J;
+  a.H = dict->H;
+  a.R = dict->R;
+  a.n = dict->J + 2 * dict->kmax * dict->J;
+  if (a.n > kMaxPacked) return RSC_ERR_UNSUPPORTED;
+  a.d = dict->d;
+  a.tw = dict->tw;
+  a.C = const_cast<double *>(C);
+  a.count = const_cast<int *>(count);
+  a.ntop = ntop;
+  a.top_idx = const_cast<int64_t *>(top_idx);
+  a.top_vec = const_cast<float *>(top_vec);
+  a.new_coef = new_coef;
+  a.n_used = n_used;
+  return ksvd_finish(a, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -55,3 +55,55 @@ def test_two_rank_shards_and_max_time():
     assert fps[0] != fps[1]                 # disjoint shards
     assert all(r[2] == 20.0 for r in res)   # max over ranks
     assert all(r[3] for r in res)           # shard = the generator's chunks for that rank
+
+
+def test_merge_top_order_ties_and_padding():
+    """The merged list of largest-error patches is what one rank holding all
+    patches would keep: descending error, ties to the smaller global index,
+    short lists padded with index -1."""
+    from paper_1806_04374_gb300.rksvd import merge_top
+    errs = [np.array([3.0, 1.0, 0.5, -1.0], np.float32), np.array([3.0, 2.0, -1.0, -1.0], np.float32)]
+    gidx = [np.array([5, 2, 7, -1]), np.array([10, 11, -1, -1])]
+    vecs = [np.arange(4, dtype=np.float32)[:, None] * np.ones((4, 3), np.float32),
+            10 + np.arange(4, dtype=np.float32)[:, None] * np.ones((4, 3), np.float32)]
+    idx, vec = merge_top(errs, gidx, vecs, ntop=6)
+    assert idx.tolist() == [5, 10, 11, 2, 7, -1]
+    assert vec[:, 0].tolist() == [0.0, 10.0, 11.0, 1.0, 2.0, 0.0]
+
+
+def _ksvd_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1806_04374_gb300.rksvd import _all_reduce_sum, gather_top
+    # this rank's partial covariance and its list (host tensors)
+    C = torch.full((2, 3, 3), float(rank + 1), dtype=torch.float64)
+    _all_reduce_sum(C, None)
+    err = torch.tensor([5.0 - rank, 1.0, -1.0], dtype=torch.float32)
+    idx = torch.tensor([0, 1, -1], dtype=torch.int64)
+    vec = torch.full((3, 2), float(rank), dtype=torch.float32)
+    top_idx, top_vec = gather_top(err, idx, vec, offset=100 * rank, group=None)
+    q.put((rank, float(C[1, 2, 0]), top_idx.tolist(), top_vec[:, 0].tolist()))
+    dist.destroy_process_group()
+
+
+def test_two_rank_ksvd_exchange():
+    """The R-K-SVD exchange on two gloo ranks: covariances summed, the ranks'
+    largest-error lists gathered with global indices and merged identically
+    on every rank."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_ksvd_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in res:
+        assert r[1] == 3.0                           # 1 + 2
+        assert r[2] == [0, 100, 1]                   # 5.0 (rank 0), 4.0 (rank 1), then 1.0 tie -> 1
+        assert r[3] == [0.0, 1.0, 0.0]

@@ -101,3 +101,43 @@ def test_unused_atoms_reset_and_repeated_atoms(rsc):
     assert np.array_equal(used, used_ref) and used[3] == 0 and used[4] == 0
     ratios = {m: eig_ratio(x, d, R, atom, angle, coef, m) for m in range(3)}
     assert_atoms_close(new, ref, ratios)
+
+
+def test_split_update_over_two_shards_equals_single_update(rsc):
+    """rsc_ksvd_accumulate on two shards of the patches (as two ranks would),
+    the covariances and counts summed, the largest-error lists merged, then
+    rsc_ksvd_finish: the same atoms and counts as rsc_ksvd_update on all the
+    patches, including the resets of unused atoms (M exceeds the atoms the
+    planted data use, so some atoms go unused)."""
+    import torch
+    from paper_1806_04374_gb300.rksvd import merge_top
+    M, J, kmax, R, K, P = 24, 6, 8, 16, 2, 3001
+    d_true = synth.make_dictionary(4, J, kmax, 31)
+    x, _ = synth.make_patches(d_true, P, 2, 0.05, 32)
+    d0 = synth.make_dictionary(M, J, kmax, 33)
+    dic = rsc.Dictionary(torch.from_numpy(d0).cuda(), R)
+    xd = torch.from_numpy(x).cuda()
+    codes = rsc.encode(dic, xd, K, "fp32")
+    ref_new, ref_used = rsc.ksvd_update(dic, xd, codes)
+    split = 1700
+    parts = []
+    for lo, hi in ((0, split), (split, P)):
+        sub = {k: v[lo:hi].contiguous() for k, v in codes.items()}
+        parts.append((lo, rsc.ksvd_accumulate(dic, xd[lo:hi].contiguous(), sub)))
+    C = parts[0][1]["C"] + parts[1][1]["C"]
+    count = (parts[0][1]["count"] + parts[1][1]["count"]).to(torch.int32)
+    errs, gidx, vecs = [], [], []
+    for lo, acc in parts:
+        idx = acc["top_idx"].cpu().numpy()
+        errs.append(acc["top_err"].cpu().numpy())
+        gidx.append(np.where(idx >= 0, idx + lo, -1))
+        vecs.append(acc["top_vec"].cpu().numpy())
+    top_idx, top_vec = merge_top(errs, gidx, vecs)
+    new, used = rsc.ksvd_finish(dic, C, count, torch.from_numpy(top_idx).cuda(),
+                                torch.from_numpy(top_vec).cuda())
+    torch.cuda.synchronize()
+    ref_used = ref_used.cpu().numpy()
+    assert np.array_equal(used.cpu().numpy(), ref_used)
+    assert (ref_used == 0).sum() >= 2          # resets exercised
+    assert np.abs(new.cpu().numpy() - ref_new.cpu().numpy()).max() < 1e-5
+    dic.close()
