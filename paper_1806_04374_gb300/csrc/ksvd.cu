@@ -53,6 +53,7 @@ struct KsvdArgs {
   // the patches of largest coding error (descending, ties: smaller index),
   // unit-normalised, for the reset of unused atoms
   int ntop;         // entries of the list
+  int top_needed;   // 1: list only as long as the atoms with count 0 need (one rank)
   float *top_err;   // [ntop]
   int64_t *top_idx; // [ntop] patch index (-1: none)
   float *top_vec;   // [ntop][H][J][2]
@@ -328,17 +329,34 @@ __global__ void __launch_bounds__(kEigThreads) ksvd_eig_kernel(const KsvdArgs a,
 __global__ void ksvd_top_kernel(const KsvdArgs a) {
   __shared__ float bv[1024];
   __shared__ long long bi[1024];
-  __shared__ long long picked[kTopMax];
+  __shared__ float prev_e;
+  __shared__ long long prev_i;
   __shared__ double nrm;
   const int J = a.J, HJ = a.H * J;
-  for (int t = 0; t < a.ntop; ++t) {
+  __shared__ int ntop;
+  if (threadIdx.x == 0) {
+    prev_e = INFINITY;
+    prev_i = -1;
+    int n = a.ntop;
+    if (a.top_needed) {  // the counts are final: as many entries as unused atoms
+      int unused = 0;
+      for (int m = 0; m < a.M; ++m) unused += a.count[m] == 0;
+      n = min(n, unused);
+      for (int t = n; t < a.ntop; ++t) a.top_idx[t] = -1;
+    }
+    ntop = n;
+  }
+  __syncthreads();
+  for (int t = 0; t < ntop; ++t) {
+    // the t-th entry is the largest (error, then smaller index) below the
+    // previous one in that order
+    const float pe = prev_e;
+    const long long pi = prev_i;
     float best = -1.0f;
     long long bp = -1;
     for (int64_t p = threadIdx.x; p < a.P; p += blockDim.x) {
-      bool taken = false;
-      for (int q = 0; q < t; ++q) taken |= (picked[q] == p);
-      if (taken) continue;
       const float e = a.err[p];
+      if (!(e < pe || (e == pe && p > pi))) continue;
       if (e > best) {
         best = e;
         bp = p;
@@ -362,7 +380,10 @@ __global__ void ksvd_top_kernel(const KsvdArgs a) {
     const long long p = bi[0];
     __syncthreads();
     if (threadIdx.x == 0) {
-      picked[t] = p;
+      if (p >= 0) {
+        prev_e = bv[0];
+        prev_i = p;
+      }
       a.top_idx[t] = p;
       a.top_err[t] = p >= 0 ? bv[0] : -1.0f;
       double s2 = 0.0;
@@ -528,6 +549,7 @@ extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, 
   q += bTi;
   a.top_vec = reinterpret_cast<float *>(q);
   a.ntop = kTopMax;
+  a.top_needed = 1;
   a.x = x;
   a.atom = atom;
   a.angle = angle_idx;
