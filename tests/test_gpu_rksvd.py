@@ -48,3 +48,53 @@ def test_trajectory_matches_oracle_loop(cuda_ok):
     got = [h["mse"] for h in hist[:iters]]
     print("gpu", got, "oracle", ref)
     assert np.allclose(got, ref, rtol=1e-3)
+
+
+def _learn_rank(rank, world, port, q):
+    import os
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    from paper_1806_04374_gb300 import rksvd
+    R, K, M, P = 16, 2, 10, 4000
+    d_true = synth.make_dictionary(6, 6, 8, 921)
+    x, _ = synth.make_patches(d_true, P, 2, 0.05, 922)
+    d0 = synth.make_dictionary(M, 6, 8, 923)
+    lo, hi = rank * P // world, (rank + 1) * P // world
+    d, _, hist = rksvd.learn(torch.from_numpy(x[lo:hi]).cuda(), torch.from_numpy(d0).cuda(), R, K,
+                             iters=3, precision="f16", group=dist.group.WORLD, offset=lo)
+    q.put((rank, d.cpu().numpy()))
+    dist.destroy_process_group()
+
+
+def test_two_rank_learning_matches_one_gpu(cuda_ok):
+    """R-K-SVD with the patches split over two ranks (two processes on this
+    GPU, gloo for the exchange; their kernels never wait on one another)
+    learns the same dictionary as one process holding all the patches."""
+    import socket
+    import torch
+    import torch.multiprocessing as mp
+    from paper_1806_04374_gb300 import rksvd
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_learn_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    R, K, M, P = 16, 2, 10, 4000
+    d_true = synth.make_dictionary(6, 6, 8, 921)
+    x, _ = synth.make_patches(d_true, P, 2, 0.05, 922)
+    d0 = synth.make_dictionary(M, 6, 8, 923)
+    d, _, _ = rksvd.learn(torch.from_numpy(x).cuda(), torch.from_numpy(d0).cuda(), R, K, iters=3,
+                          precision="f16")
+    d = d.cpu().numpy()
+    assert np.abs(res[0][1] - res[1][1]).max() == 0.0   # every rank holds the same atoms
+    assert np.abs(res[0][1] - d).max() < 1e-4, np.abs(res[0][1] - d).max()
