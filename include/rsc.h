@@ -193,8 +193,9 @@ int rsc_ksvd_finish(const rsc_dict *dict, const double *C, const int32_t *count,
  * centre): J Gaussian radial rings (centres j * ring_spacing, j = 1..J,
  * width ring_width; <= 0 selects the defaults (N-1)/(2J) and 1 pixel) times
  * the harmonics e^{i k phi}, |k| <= kmax, orthonormalised within each k, and
- * its analysis operator (pseudo-inverse of the synthesis matrix, cutoff
- * 1e-10 relative), then uploads it to the current device.  Pixel (row, col)
+ * its analysis operator (pseudo-inverse of the synthesis matrix; singular
+ * values up to 1e-3 of the largest are treated as zero, which bounds the
+ * operator's norm by 1e3 / sigma_max), then uploads it to the current device.  Pixel (row, col)
  * of a window lies at x = col - (N-1)/2, y = (N-1)/2 - row.
  *   Limits: N <= 64, kmax <= 16, (kmax+1)*J <= 512 (RSC_ERR_UNSUPPORTED);
  *   rings that are linearly dependent on the grid give RSC_ERR_INVALID.

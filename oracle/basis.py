@@ -17,7 +17,12 @@ indicators (Eq. (basis-cont)):
 Readings: pixel (row, col) sits at x = col - c, y = c - row (c = (N-1)/2),
 phi = atan2(y, x); e^{i k phi} is taken as 0 at the centre pixel for k != 0;
 ring centres r_j = j * (N - 1) / (2 J), width 1 pixel; pseudo-inverse cutoff
-1e-10 relative to the largest singular value.
+1e-3 relative to the largest singular value (the paper's operator presumes
+Phi^* Phi invertible; at 21 x 21 with J = 10, kmax = 12 the synthesis matrix
+has singular values down to 4e-8 of the largest, and inverting those would
+put pixel noise, amplified up to 2.5e7 times, into coefficient directions
+that synthesise almost nothing; 1e-3 leaves the 11 x 11, J = 6, kmax = 8
+operator unchanged).
 Coefficients are returned as half spectra [k = 0..kmax][j][re, im].
 """
 from __future__ import annotations
@@ -71,10 +76,14 @@ def real_synthesis(Phi, kmax: int, J: int):
     return np.stack(cols, 1)
 
 
+RCOND = 1e-3
+
+
 def analysis(N: int, J: int, kmax: int, **kw):
-    """Packed pseudo-inverse [n, npix] and the mask."""
+    """Packed pseudo-inverse [n, npix] (singular values at most RCOND times
+    the largest treated as zero) and the mask."""
     Phi, mask = synthesis(N, J, kmax, **kw)
-    Pr = np.linalg.pinv(real_synthesis(Phi, kmax, J), rcond=1e-10)
+    Pr = np.linalg.pinv(real_synthesis(Phi, kmax, J), rcond=RCOND)
     return Pr, mask
 
 

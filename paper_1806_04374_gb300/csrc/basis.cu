@@ -9,8 +9,13 @@
 // orthonormal within each harmonic (Loewdin, G^{-1/2} from a Jacobi
 // eigendecomposition of the real ring Gram matrix), and the analysis
 // operator: the pseudo-inverse of the real synthesis matrix (one-sided
-// Jacobi SVD, cutoff 1e-10 of the largest singular value), which is the
-// paper's (Phi^* Phi)^{-1} Phi^* whenever Phi^* Phi is invertible.
+// Jacobi SVD, singular values up to 1e-3 of the largest treated as zero),
+// which is the paper's (Phi^* Phi)^{-1} Phi^* whenever Phi^* Phi is
+// invertible and its condition number is below 10^3.  The cutoff keeps the
+// operator from amplifying pixel noise by more than 10^3 / sigma_max: at
+// 21 x 21 pixels with J = 10, kmax = 12 the synthesis matrix has singular
+// values down to 4e-8 of the largest, whose directions synthesise almost
+// nothing and would otherwise dominate the coefficients.
 // Readings: pixel (row, col) at x = col - c, y = c - row, phi = atan2(y, x);
 // e^{i k phi} = 0 at the centre pixel for k != 0; ring centres
 // r_j = j * spacing (default (N-1)/(2J)), ring width sigma (default 1 px).
@@ -491,7 +496,7 @@ int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, doub
         X[(size_t)(col + 1) * npix + p] = -M_SQRT2 * qq * sin(k * phi[p]);
       }
     }
-  const std::vector<double> Pr = pinv(X, npix, n, 1e-10);  // n x npix
+  const std::vector<double> Pr = pinv(X, npix, n, 1e-3);  // n x npix
   // outputs: half spectrum [k][j][re, im]; packed k >= 1 slots carry sqrt(2)
   const int nout = 2 * H * J;
   const int nout_pad = (nout + 31) / 32 * 32;

@@ -14,8 +14,9 @@
 //     f32 out) for both tiles into one of two TMEM accumulator buffers per
 //     tile, and tcgen05.commit's the stage, the buffer and the A tiles back;
 //   * warps 0-7 (one thread per patch, TMEM lane = patch) read each buffer
-//     back with tcgen05.ld and keep the kTcTop (4) largest block maxima of |score|
-//     (block = 32 rows = 32 atoms at one angle) with their rows, plus the
+//     back with tcgen05.ld and keep the rsc_ntop(L) (4; 8 for long rows)
+//     largest block maxima of |score| (block = 32 rows = 32 atoms at one
+//     angle) with their rows, plus the
 //     largest value left out (disc), then hand the buffer back.  A block whose
 //     maximum is more than the patch's window (>= 2 E, from the refine pass)
 //     below the running best can neither win nor fall inside the final
@@ -50,6 +51,7 @@ struct SShape {
   static constexpr int a_off = 0, b_off = kSTiles * kATile;
   static constexpr int bar_off = b_off + kSStages * kBStage;
   static constexpr int total = bar_off + 256 + 1024;  // barriers + alignment slack
+  static constexpr int NT = NB > 2 ? kTcTopLong : kTcTop;  // candidates per patch
 };
 
 // barrier slots (8 bytes each)
@@ -216,10 +218,10 @@ __global__ void __launch_bounds__(kSThreads, 1)
       const int64_t p = (pair * kSTiles + tile) * kSTile + row;
       const bool act = p < a.P && a.status[p] > 0;
       const float win = act ? a.win[p] : 0.0f;
-      float tv[kTop];
-      int ti[kTop];
+      float tv[Sh::NT];
+      int ti[Sh::NT];
 #pragma unroll
-      for (int q = 0; q < kTop; ++q) {
+      for (int q = 0; q < Sh::NT; ++q) {
         tv[q] = -INFINITY;
         ti[q] = -1;
       }
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
             for (int u = 0; u < 32; u += 2) m1 = fmax3(m1, key[u], key[u + 1]);
             // kept: the block maximum beats the last kept one and is not below
             // the window under the running best (NaN-safe form)
-            if (m1 >= 0.0f && m1 > tv[kTop - 1] && !(m1 < tv[0] - win)) {
+            if (m1 >= 0.0f && m1 > tv[Sh::NT - 1] && !(m1 < tv[0] - win)) {
               const int us = __float_as_int(m1) & 31;
               float m2 = -1.0f;
 #pragma unroll
@@ -301,10 +303,10 @@ __global__ void __launch_bounds__(kSThreads, 1)
       }
       if (!ok) break;
       if (act) {
-        int *ci = a.cand_idx + p * kTop;
-        float *cv = a.cand_val + p * kTop;
+        int *ci = a.cand_idx + p * Sh::NT;
+        float *cv = a.cand_val + p * Sh::NT;
 #pragma unroll
-        for (int q = 0; q < kTop; q += 4) {
+        for (int q = 0; q < Sh::NT; q += 4) {
           *reinterpret_cast<int4 *>(ci + q) = make_int4(ti[q], ti[q + 1], ti[q + 2], ti[q + 3]);
           *reinterpret_cast<float4 *>(cv + q) = make_float4(tv[q], tv[q + 1], tv[q + 2], tv[q + 3]);
         }

@@ -255,7 +255,7 @@ size_t f16_scratch_bytes(int64_t P, int K, int L) {
   int nD = 0, nF = 0, nI = 0;
   rsc_state_layout(K, &nD, &nF, &nI);
   auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  return al256((size_t)P * L * 2) + 2 * al256((size_t)P * kTcTop * 4) +
+  return al256((size_t)P * L * 2) + 2 * al256((size_t)P * rsc_ntop(L) * 4) +
          3 * al256((size_t)P * 4) + al256((size_t)nD * P * 8) + al256((size_t)nF * P * 4) +
          al256((size_t)nI * P * 4) + al256((size_t)(P + 4) * 4);
 }
@@ -293,8 +293,8 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   ra.anorm = dict->anorm;
   ra.L = dict->row_len;
   ra.A = take((size_t)P * ra.L * 2);
-  ra.cand_idx = reinterpret_cast<int *>(take((size_t)P * kTcTop * 4));
-  ra.cand_val = reinterpret_cast<float *>(take((size_t)P * kTcTop * 4));
+  ra.cand_idx = reinterpret_cast<int *>(take((size_t)P * rsc_ntop(ra.L) * 4));
+  ra.cand_val = reinterpret_cast<float *>(take((size_t)P * rsc_ntop(ra.L) * 4));
   ra.cand_disc = reinterpret_cast<float *>(take((size_t)P * 4));
   ra.status = reinterpret_cast<int *>(take((size_t)P * 4));
   ra.win = reinterpret_cast<float *>(take((size_t)P * 4));

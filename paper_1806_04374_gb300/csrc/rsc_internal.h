@@ -139,13 +139,19 @@ struct TcArgs {
 // candidates overflow are appended to redo_list for the FP32 path.
 int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream);
 
-// Block maxima kept per patch and greedy step by the tensor-core scoring.
+// Candidates (block maxima and in-window second values) kept per patch and
+// greedy step by the tensor-core scoring: 4 for rows of kTcKst slots, 8 for
+// rows of kTcKstLong slots (the larger atom x angle grids those shapes come
+// with, e.g. M = 256, R = 128, put more units within the certification
+// window; with 4 a patch would be handed to the FP32 path at ~0.6% of steps).
 constexpr int kTcTop = 4;
+constexpr int kTcTopLong = 8;
+constexpr int rsc_ntop(int L) { return L == kTcKstLong ? kTcTopLong : kTcTop; }
 
 // One scoring pass of the split FP16 path (romp_score.cu): packed fp16
 // residual rows (TMA map tmA: [P][kTcKst]) times the steered dictionary
-// (tmB) -> per patch the kTcTop largest block maxima of |score| with their
-// rows (r*M + m) and the largest value left out.
+// (tmB) -> per patch the rsc_ntop(L) largest candidates of |score| with
+// their rows (r*M + m) and the largest value left out.
 struct ScoreArgs {
   int64_t P;
   int ksteps, MR, nchunks;
@@ -154,8 +160,8 @@ struct ScoreArgs {
   int paired, ke, ko;
   int L;  // packed row length (kTcKst or kTcKstLong; the latter plain only)
   const int *status;  // > 0: patch still being coded
-  int *cand_idx;      // [P][kTcTop]
-  float *cand_val;    // [P][kTcTop]
+  int *cand_idx;      // [P][rsc_ntop(L)]
+  float *cand_val;    // [P][rsc_ntop(L)]
   float *cand_disc;   // [P]
   // [P] per-patch certification window in accumulator units (written by the
   // refine pass with the row): a block maximum more than `win` below the

@@ -49,19 +49,20 @@ __device__ __forceinline__ bool df_abs_eq(df a, df b) {
   return a.hi == b.hi && a.lo == b.lo;
 }
 
-constexpr int kTop = kTcTop;  // block maxima kept per patch and step
+constexpr int kTop = kTcTop;  // candidates kept per patch and step (rows of kTcKst)
 
-// Inserts (x, idx) into the descending list (v, i) of kTop entries; disc
+// Inserts (x, idx) into the descending list (v, i) of NT entries; disc
 // keeps the largest value that did not stay in the list.  Strict comparisons
 // keep the earlier entry first among equal values.
-__device__ __forceinline__ void topn_insert(float (&v)[kTop], int (&i)[kTop], float &disc,
-                                            float x, int idx) {
-  if (x > v[kTop - 1]) {
-    disc = fmaxf(disc, v[kTop - 1]);
-    v[kTop - 1] = x;
-    i[kTop - 1] = idx;
+template <int NT>
+__device__ __forceinline__ void topn_insert(float (&v)[NT], int (&i)[NT], float &disc, float x,
+                                            int idx) {
+  if (x > v[NT - 1]) {
+    disc = fmaxf(disc, v[NT - 1]);
+    v[NT - 1] = x;
+    i[NT - 1] = idx;
 #pragma unroll
-    for (int q = kTop - 1; q > 0; --q) {
+    for (int q = NT - 1; q > 0; --q) {
       if (v[q] > v[q - 1]) {
         const float tf = v[q - 1];
         v[q - 1] = v[q];

@@ -52,17 +52,28 @@ def test_quarter_turn_of_the_patch_is_steering_by_half_pi():
 
 
 def test_pseudo_inverse_properties():
-    # 21 x 21: 349 pixels >= 250 coefficients, a synthesised patch projects back exactly
-    N, J, kmax = 21, 10, 12
-    Phi, _ = basis.synthesis(N, J, kmax)
-    Xr = basis.real_synthesis(Phi, kmax, J)
-    Pr, _ = basis.analysis(N, J, kmax)
-    assert np.allclose(Pr @ Xr, np.eye(Xr.shape[1]), atol=1e-8)
-    # 11 x 11: 97 pixels < 102 coefficients, Moore-Penrose X X+ X = X
-    Phi, _ = basis.synthesis(11, 6, 8)
-    Xr = basis.real_synthesis(Phi, 8, 6)
-    Pr, _ = basis.analysis(11, 6, 8)
-    assert np.allclose(Xr @ Pr @ Xr, Xr, atol=1e-9)
+    """Truncated pseudo-inverse: singular values <= 1e-3 sigma_max are
+    dropped.  Pr Xr is then the orthogonal projector onto the kept right
+    singular vectors (symmetric, idempotent, exact on its range), the
+    operator norm is at most 1e3 / sigma_max (a cutoff of 1e-10 gives
+    2.5e7 / sigma_max at 21 x 21), and Xr Pr Xr differs from Xr by at most
+    the largest dropped singular value."""
+    rng = np.random.default_rng(3)
+    for N, J, kmax, dropped in ((21, 10, 12, 12), (11, 6, 8, 8)):
+        Phi, _ = basis.synthesis(N, J, kmax)
+        Xr = basis.real_synthesis(Phi, kmax, J)
+        Pr, _ = basis.analysis(N, J, kmax)
+        s = np.linalg.svd(Xr, compute_uv=False)
+        n = Xr.shape[1]
+        assert (s <= basis.RCOND * s[0]).sum() + (n - s.size) == dropped
+        P = Pr @ Xr
+        assert np.allclose(P, P.T, atol=1e-9)
+        assert np.allclose(P @ P, P, atol=1e-9)
+        assert abs(np.trace(P) - (n - dropped)) < 1e-8
+        c = P @ rng.standard_normal(n)
+        assert np.allclose(Pr @ (Xr @ c), c, atol=1e-9)
+        assert np.linalg.norm(Pr, 2) <= 1.0 / (basis.RCOND * s[0]) * (1 + 1e-9)
+        assert np.linalg.norm(Xr - Xr @ Pr @ Xr, 2) <= basis.RCOND * s[0]
 
 
 def test_project_windows_order():
