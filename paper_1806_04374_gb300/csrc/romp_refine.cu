@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
 // K = 5; for K = 8 the state (Cholesky row, weights, Gram entries of up to 8
 // atoms) spills 1.8 KB a thread at that budget, and 3 blocks (<= 168
 // registers) measured 8% faster on the 21 x 21-patch image workload.
-template <int KK, bool PAIRED, int NT>
+template <int KK, bool PAIRED>
 __global__ void __launch_bounds__(128, KK > 5 ? 3 : 5) romp_refine_kernel(const RefineArgs a) {
   const int H = a.H, J = a.J, R = a.R, M = a.M, HJ = H * J;
   const int *qtab;
@@ -271,19 +271,15 @@ __global__ void __launch_bounds__(128, KK > 5 ? 3 : 5) romp_refine_kernel(const 
     load_state<KK>(a, p, S, t, e, xnorm, rnorm, dr);
     // accumulator scores are 2^(16 - e) times the true scores
     const float unscale = ldexpf(1.0f, e - 16);
-    float tv[NT];
-    int ti[NT];
-#pragma unroll
-    for (int q = 0; q < NT; q += 4) {
-      const int4 iv = *reinterpret_cast<const int4 *>(a.cand_idx + p * NT + q);
-      const float4 fv = *reinterpret_cast<const float4 *>(a.cand_val + p * NT + q);
-      ti[q] = iv.x; ti[q + 1] = iv.y; ti[q + 2] = iv.z; ti[q + 3] = iv.w;
-      tv[q] = fv.x * unscale; tv[q + 1] = fv.y * unscale;
-      tv[q + 2] = fv.z * unscale; tv[q + 3] = fv.w * unscale;
-    }
-    const float disc = a.cand_disc[p] * unscale;
+    // the scoring pass's two candidate lists (one per column half of each
+    // chunk, each sorted in descending order): their heads give the best
+    // value; the entries are read again by the re-scoring loop below
+    const float *cvp = a.cand_val + p * kTcCand;
+    const int *cip = a.cand_idx + p * kTcCand;
+    const float2 dv = *reinterpret_cast<const float2 *>(a.cand_disc + 2 * p);
+    const float disc = fmaxf(dv.x, dv.y) * unscale;
     const float stop_level = 1e-10f * xnorm;
-    const float s1 = tv[0];
+    const float s1 = fmaxf(cvp[0], cvp[kTcTop]) * unscale;
     // fp16 error of a score (score_err_base) plus 2^-16 s1 for the low
     // mantissa bits the scoring kernel replaces by a column index
     const float E = score_err_base(rnorm, dr, e, a.L) + 1.52587890625e-5f * fabsf(s1);
@@ -308,11 +304,16 @@ __global__ void __launch_bounds__(128, KK > 5 ? 3 : 5) romp_refine_kernel(const 
 #pragma unroll
         for (int i = 0; i < KK; ++i) bg[i] = df_make(0.0f);
         int bm = -1, br = 0, bflat = 0;
-#pragma unroll
-        for (int q = 0; q < NT; ++q) {
-          const bool any = ti[q] >= 0 && tv[q] >= thr;
+#pragma unroll 1
+        for (int q = 0; q < kTcCand; ++q) {
+          const float val = cvp[q] * unscale;
+          const int id = cip[q];
+          const bool any = id >= 0 && val >= thr;
+          // each list is sorted: past its first entry outside the window the
+          // rest of that list is outside too
+          if (!any) q |= kTcTop - 1;
           if (any) {
-            const int m = ti[q] % M, r = ti[q] / M;
+            const int m = id % M, r = id / M;
             df ax[NP], sc[NP], gq[NP][KK];
             if (PAIRED) {
               const DF2 x2 = score_x_pair(a.d + (size_t)m * HJ * 2, xp, J, H, r, tw);
@@ -430,11 +431,9 @@ int launch_refine_t(const RefineArgs &a, bool init, cudaStream_t stream) {
   if (init)
     romp_init_kernel<KK><<<grid, 128, shm, stream>>>(a);
   else if (a.paired)
-    romp_refine_kernel<KK, true, kTcTop><<<grid, 128, shm, stream>>>(a);
-  else if (rsc_ntop(a.L) == kTcTopLong)
-    romp_refine_kernel<KK, false, kTcTopLong><<<grid, 128, shm, stream>>>(a);
+    romp_refine_kernel<KK, true><<<grid, 128, shm, stream>>>(a);
   else
-    romp_refine_kernel<KK, false, kTcTop><<<grid, 128, shm, stream>>>(a);
+    romp_refine_kernel<KK, false><<<grid, 128, shm, stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return RSC_OK;

@@ -2,25 +2,32 @@
 // warp-specialised, for the FP16 path of rsc_encode.
 //
 // score(p, m, r) = <S_r d_m, r_p> for every patch p and every steered atom
-// (m, r) is the dense contraction of the packed residuals (fp16, scaled, 112 columns,
-// in HBM) with the steered dictionary [S_0 D ... S_{R-1} D] (fp16, scaled, M*R rows,
-// angle-major), i.e. steps (a) and (b) of OMP (Sec. II-C) over the augmented
-// dictionary of Fig. "code", the two linear maps folded into one.  Per CTA
-// (persistent, one per SM) and pair of 128-patch tiles:
-//   * warp 8 (one lane) loads the two residual tiles and streams the steered
-//     dictionary in 128-row chunks through a 3-stage shared-memory ring with
-//     TMA (128-byte swizzle);
-//   * warp 9 (one lane) issues tcgen05.mma (M = 128, N = 128, K = 16, fp16 in,
-//     f32 out) for both tiles into one of two TMEM accumulator buffers per
-//     tile, and tcgen05.commit's the stage, the buffer and the A tiles back;
-//   * warps 0-7 (one thread per patch, TMEM lane = patch) read each buffer
-//     back with tcgen05.ld and keep the rsc_ntop(L) (4; 8 for long rows)
-//     largest block maxima of |score| (block = 32 rows = 32 atoms at one
-//     angle) with their rows, plus the
-//     largest value left out (disc), then hand the buffer back.  A block whose
-//     maximum is more than the patch's window (>= 2 E, from the refine pass)
-//     below the running best can neither win nor fall inside the final
-//     window, so it is neither kept nor needs its second maximum.
+// (m, r) is the dense contraction of the packed residuals (fp16, scaled, L
+// columns, in HBM) with the steered dictionary [S_0 D ... S_{R-1} D] (fp16,
+// scaled, M*R rows, angle-major), i.e. steps (a) and (b) of OMP (Sec. II-C)
+// over the augmented dictionary of Fig. "code", the two linear maps folded
+// into one.  Per CTA (persistent, one per SM) and 128-patch tile:
+//   * warp 8 (one lane) loads the tile's residual rows (A, double-buffered
+//     across tiles when they are short) and streams the steered dictionary
+//     in chunks of N rows (256 atoms at one angle block, or 128 atom pairs),
+//     one 64-column K-block per stage of a shared-memory ring, with TMA
+//     (128-byte swizzle);
+//   * warp 9 (one lane) issues tcgen05.mma (M = 128, N = 256 or 128, K = 16,
+//     fp16 in, f32 out) into one of two TMEM accumulator buffers of 256
+//     columns, and tcgen05.commit's each stage, each buffer and the A tile
+//     back to their producers.  The time of one MMA hardly depends on N up
+//     to 64 on this part (measured: the same launch time at N = 16, 32, 64),
+//     so the widest N that two accumulator buffers allow is used;
+//   * warps 0-7 read each buffer back with tcgen05.ld: warp w reads TMEM
+//     lanes 32 (w mod 4) .. + 31 (one thread per patch) and one column half
+//     (w / 4, swapped on odd chunks).  Each warp keeps its own kTcTop largest block maxima of |score|
+//     (block = 32 columns: 32 atoms at one angle, or 32 atom pairs) with
+//     their rows, plus the largest value it left out (disc); the refine pass
+//     takes the union of the two lists, so the halves never synchronise.  A
+//     block whose maximum is more than the patch's window (>= 2 E, from the
+//     refine pass) below the half's running best can neither win nor fall
+//     inside the final window, so it is neither kept nor needs its second
+//     maximum.
 // All hand-offs are mbarriers; every wait is bounded (2 s of globaltimer) and
 // a failed wait records RSC_ERR_TIMEOUT, stops the CTA's loops, drains the
 // copies and MMAs it issued, and frees its TMEM.
@@ -30,48 +37,51 @@
 
 namespace {
 
-constexpr int kSTile = 128;
-constexpr int kSTiles = 2;
-constexpr int kSStages = 3;
-constexpr int kSBlk = 128 * 128;       // one 64-column block of 128 rows (bytes)
-constexpr int kSThreads = 320;         // 8 epilogue warps + TMA warp + MMA warp
+constexpr int kSTile = 128;             // patches per tile (MMA M, TMEM lanes)
+constexpr int kSStagesMax = 6;          // barrier slots reserved for the B ring
+constexpr int kABlk = kSTile * 128;     // one 64-column block of an A tile (bytes)
+constexpr int kSBufC = 256;             // accumulator columns per TMEM buffer
+constexpr uint32_t kSCols = 2 * kSBufC; // two buffers: all 512 TMEM columns
+constexpr int kSThreads = 320;          // 8 epilogue warps + TMA warp + MMA warp
 constexpr uint64_t kSWaitNs = 2000000000ull;
 
 // Shape of one instantiation: NB 64-column blocks per packed row (2 for rows
-// of kTcKst, 4 for kTcKstLong), BR dictionary rows (atoms or atom pairs) per
-// chunk, BUFC accumulator columns per TMEM buffer.
+// of kTcKst, 4 for kTcKstLong).
 template <bool PAIRED, int NB>
 struct SShape {
-  static constexpr int BR = (PAIRED || NB > 2) ? kTcBP : kTcBN;
-  static constexpr int BUFC = PAIRED ? 2 * kTcBP : BR;
-  static constexpr uint32_t kCols = kSTiles * 2 * BUFC;  // 512 or 256
-  static constexpr int kATile = NB * kSBlk;               // one A tile (bytes)
-  static constexpr int kBBlk = BR * 128;                  // one 64-column block of a B stage
-  static constexpr int kBStage = NB * kBBlk;
-  static constexpr int a_off = 0, b_off = kSTiles * kATile;
-  static constexpr int bar_off = b_off + kSStages * kBStage;
+  static constexpr int N = PAIRED ? kTcSNP : kTcSN;   // B rows per chunk = MMA N
+  static constexpr int NKB = NB;                      // K-blocks (ring stages) per chunk
+  static constexpr int kATile = NB * kABlk;           // one A tile (bytes)
+  static constexpr int kABufs = NB > 2 ? 1 : 2;       // A tiles in flight
+  static constexpr int kBStage = N * 128;             // one K-block of a chunk (bytes)
+  static constexpr int kStages = NB > 2 ? 5 : (PAIRED ? 6 : 4);
+  static constexpr int HALF = N / 2;                  // B rows per epilogue column half
+  static constexpr int PIECES = HALF / 32;            // 32-column pieces per half
+  static constexpr int a_off = 0, b_off = kABufs * kATile;
+  static constexpr int bar_off = b_off + kStages * kBStage;
   static constexpr int total = bar_off + 256 + 1024;  // barriers + alignment slack
-  static constexpr int NT = NB > 2 ? kTcTopLong : kTcTop;  // candidates per patch
+  static_assert(kStages <= kSStagesMax, "barrier slots");
+  static_assert(PAIRED ? 2 * N == kSBufC : N == kSBufC, "accumulator buffer width");
 };
 
 // barrier slots (8 bytes each)
 enum : int {
-  kBarAFull = 0,
-  kBarAEmpty = 1,
-  kBarBFull = 2,                 // + stage
-  kBarBEmpty = 2 + kSStages,     // + stage
-  kBarAccFull = 2 + 2 * kSStages,      // + buffer
-  kBarAccEmpty = 4 + 2 * kSStages,     // + buffer
-  kBarCount = 6 + 2 * kSStages,
+  kBarAFull = 0,                          // + A buffer
+  kBarAEmpty = 2,                         // + A buffer
+  kBarBFull = 4,                          // + stage
+  kBarBEmpty = 4 + kSStagesMax,           // + stage
+  kBarAccFull = 4 + 2 * kSStagesMax,      // + buffer
+  kBarAccEmpty = 6 + 2 * kSStagesMax,     // + buffer
+  kBarCount = 8 + 2 * kSStagesMax,
 };
+static_assert(kBarCount * 8 + 8 <= 256, "barrier area");
 
 template <bool PAIRED, int NB>
 __global__ void __launch_bounds__(kSThreads, 1)
     romp_score_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const ScoreArgs a) {
   using Sh = SShape<PAIRED, NB>;
-  constexpr int BR = Sh::BR;
-  constexpr uint32_t kBBlk = (uint32_t)Sh::kBBlk;
+  constexpr int N = Sh::N, NKB = Sh::NKB, kStages = Sh::kStages, kABufs = Sh::kABufs;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -85,30 +95,29 @@ __global__ void __launch_bounds__(kSThreads, 1)
   auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr uint32_t kCols = Sh::kCols;
-  constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, PAIRED ? kTcBP : BR);
+  constexpr uint32_t kIdesc = tc::idesc_f16_f32(128, N);
 
   if (tid == 0) {
-    tc::mbar_init(bar(kBarAFull), 1);
-    tc::mbar_init(bar(kBarAEmpty), 1);
-    for (int s = 0; s < kSStages; ++s) {
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(bar(kBarAFull + i), 1);
+      tc::mbar_init(bar(kBarAEmpty + i), 1);
+      tc::mbar_init(bar(kBarAccFull + i), 1);
+      tc::mbar_init(bar(kBarAccEmpty + i), 8);  // one arrival per epilogue warp
+    }
+    for (int s = 0; s < kSStagesMax; ++s) {
       tc::mbar_init(bar(kBarBFull + s), 1);
       tc::mbar_init(bar(kBarBEmpty + s), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(bar(kBarAccFull + b), 1);
-      tc::mbar_init(bar(kBarAccEmpty + b), 8);  // one arrival per epilogue warp
     }
     *s_abort = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kCols);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kSCols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *s_tmem;
 
-  const int64_t npairs = (a.P + kSTiles * kSTile - 1) / (kSTiles * kSTile);
+  const int64_t ntiles = (a.P + kSTile - 1) / kSTile;
   const int nch = a.nchunks;
   auto fail = [&]() {
     *s_abort = 1;
@@ -118,115 +127,122 @@ __global__ void __launch_bounds__(kSThreads, 1)
   if (warp == 8) {
     // ---------------------------------------------------------------- TMA
     if (lane == 0) {
-      uint32_t gB = 0, issuedB = 0, iter = 0, issuedA = 0;
-      for (int64_t pair = blockIdx.x; pair < npairs && !*s_abort; pair += gridDim.x, ++iter) {
-        if (iter > 0 && !tc::mbar_wait_bounded(bar(kBarAEmpty), (iter - 1) & 1, kSWaitNs)) {
+      uint32_t gs = 0, it = 0;
+      uint32_t issuedA[2] = {0u, 0u};
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles && !*s_abort; tile += gridDim.x, ++it) {
+        const int ab = (int)(it % kABufs);
+        const uint32_t ua = it / kABufs;
+        if (ua > 0 && !tc::mbar_wait_bounded(bar(kBarAEmpty + ab), (ua - 1) & 1, kSWaitNs)) {
           fail();
           break;
         }
-        tc::mbar_arrive_expect_tx(bar(kBarAFull), kSTiles * Sh::kATile);
-        for (int t = 0; t < kSTiles; ++t) {
-          const int y = (int)((pair * kSTiles + t) * kSTile);
-          const uint32_t dst = tc::smem_u32(sA + t * Sh::kATile);
+        tc::mbar_arrive_expect_tx(bar(kBarAFull + ab), Sh::kATile);
+        const uint32_t dstA = tc::smem_u32(sA + ab * Sh::kATile);
 #pragma unroll
-          for (int j = 0; j < NB; ++j) tc::tma_load_2d(dst + j * kSBlk, &tmA, bar(kBarAFull), 64 * j, y);
-        }
-        ++issuedA;
-        for (int c = 0; c < nch; ++c, ++gB) {
-          const int s = gB % kSStages;
-          if (gB >= (uint32_t)kSStages &&
-              !tc::mbar_wait_bounded(bar(kBarBEmpty + s), ((gB / kSStages) - 1) & 1, kSWaitNs)) {
-            fail();
-            break;
+        for (int j = 0; j < NB; ++j)
+          tc::tma_load_2d(dstA + j * kABlk, &tmA, bar(kBarAFull + ab), 64 * j, (int)(tile * kSTile));
+        ++issuedA[ab];
+        for (int c = 0; ok && c < nch; ++c) {
+          for (int j = 0; j < NKB; ++j, ++gs) {
+            const int s = (int)(gs % kStages);
+            if (gs >= (uint32_t)kStages &&
+                !tc::mbar_wait_bounded(bar(kBarBEmpty + s), ((gs / kStages) - 1) & 1, kSWaitNs)) {
+              fail();
+              ok = false;
+              break;
+            }
+            tc::mbar_arrive_expect_tx(bar(kBarBFull + s), Sh::kBStage);
+            tc::tma_load_2d(tc::smem_u32(sB + s * Sh::kBStage), &tmB, bar(kBarBFull + s), 64 * j, c * N);
           }
-          const uint32_t dst = tc::smem_u32(sB + s * Sh::kBStage);
-          tc::mbar_arrive_expect_tx(bar(kBarBFull + s), Sh::kBStage);
-#pragma unroll
-          for (int j = 0; j < NB; ++j)
-            tc::tma_load_2d(dst + j * kBBlk, &tmB, bar(kBarBFull + s), 64 * j, c * BR);
-          ++issuedB;
         }
       }
       // drain: every issued load lands before the CTA exits
-      for (uint32_t i = (issuedB > (uint32_t)kSStages ? issuedB - kSStages : 0); i < issuedB; ++i)
-        tc::mbar_wait_bounded(bar(kBarBFull + i % kSStages), (i / kSStages) & 1, kSWaitNs);
-      if (issuedA) tc::mbar_wait_bounded(bar(kBarAFull), (issuedA - 1) & 1, kSWaitNs);
+      for (uint32_t i = (gs > (uint32_t)kStages ? gs - kStages : 0); i < gs; ++i)
+        tc::mbar_wait_bounded(bar(kBarBFull + i % kStages), (i / kStages) & 1, kSWaitNs);
+      for (int ab = 0; ab < kABufs; ++ab)
+        if (issuedA[ab]) tc::mbar_wait_bounded(bar(kBarAFull + ab), (issuedA[ab] - 1) & 1, kSWaitNs);
     }
   } else if (warp == 9) {
     // ---------------------------------------------------------------- MMA
     if (lane == 0) {
-      uint32_t g = 0, iter = 0;
-      bool any = false;
-      for (int64_t pair = blockIdx.x; pair < npairs && !*s_abort; pair += gridDim.x, ++iter) {
-        if (!tc::mbar_wait_bounded(bar(kBarAFull), iter & 1, kSWaitNs)) {
+      uint32_t g = 0, gs = 0, it = 0, last = 0;
+      bool any = false, ok = true;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles && !*s_abort; tile += gridDim.x, ++it) {
+        const int ab = (int)(it % kABufs);
+        const uint32_t ua = it / kABufs;
+        if (!tc::mbar_wait_bounded(bar(kBarAFull + ab), ua & 1, kSWaitNs)) {
           fail();
           break;
         }
         tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_u32(sA);
-        bool ok = true;
+        const uint32_t a0 = tc::smem_u32(sA + ab * Sh::kATile);
         for (int c = 0; c < nch; ++c, ++g) {
-          const int s = g % kSStages;
           const uint32_t b = g & 1, ub = g >> 1;
-          if (!tc::mbar_wait_bounded(bar(kBarBFull + s), (g / kSStages) & 1, kSWaitNs) ||
-              (ub > 0 && !tc::mbar_wait_bounded(bar(kBarAccEmpty + b), (ub - 1) & 1, kSWaitNs))) {
+          if (ub > 0 && !tc::mbar_wait_bounded(bar(kBarAccEmpty + b), (ub - 1) & 1, kSWaitNs)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          const uint32_t b0 = tc::smem_u32(sB + s * Sh::kBStage);
-#pragma unroll
-          for (int t = 0; t < kSTiles; ++t) {
-            const uint32_t d = tmem + (uint32_t)(t * 2 + b) * Sh::BUFC;
-            const uint32_t at = a0 + t * Sh::kATile;
-            if (PAIRED) {
-              // even half (A and B block 0) -> columns 0..63, odd half
-              // (block 1) -> columns 64..127 of the buffer
-              for (int ks = 0; ks < a.ke; ++ks)
-                tc::mma_f16(d, tc::smem_desc_sw128(at + ks * 32), tc::smem_desc_sw128(b0 + ks * 32),
-                            kIdesc, ks > 0 ? 1u : 0u);
-              for (int ks = 0; ks < a.ko; ++ks)
-                tc::mma_f16(d + kTcBP, tc::smem_desc_sw128(at + kSBlk + ks * 32),
-                            tc::smem_desc_sw128(b0 + kBBlk + ks * 32), kIdesc, ks > 0 ? 1u : 0u);
-            } else {
-              for (int ks = 0; ks < a.ksteps; ++ks)
-                tc::mma_f16(d, tc::smem_desc_sw128(at + (ks >> 2) * kSBlk + (ks & 3) * 32),
-                            tc::smem_desc_sw128(b0 + (ks >> 2) * kBBlk + (ks & 3) * 32), kIdesc,
-                            ks > 0 ? 1u : 0u);
+          const uint32_t d = tmem + b * kSBufC;
+          for (int j = 0; j < NKB; ++j, ++gs) {
+            const int s = (int)(gs % kStages);
+            if (!tc::mbar_wait_bounded(bar(kBarBFull + s), (gs / kStages) & 1, kSWaitNs)) {
+              ok = false;
+              break;
             }
+            tc::fence_after_sync();
+            const uint32_t b0 = tc::smem_u32(sB + s * Sh::kBStage);
+            const uint32_t aj = a0 + j * kABlk;
+            if (PAIRED) {
+              // block 0: even harmonics -> columns 0..N-1 of the buffer;
+              // block 1: odd harmonics -> columns N..2N-1
+              const int nk = j == 0 ? a.ke : a.ko;
+              for (int ks = 0; ks < nk; ++ks)
+                tc::mma_f16(d + (uint32_t)(j * N), tc::smem_desc_sw128(aj + ks * 32),
+                            tc::smem_desc_sw128(b0 + ks * 32), kIdesc, ks > 0 ? 1u : 0u);
+            } else {
+              const int nk = min(4, a.ksteps - 4 * j);
+              for (int ks = 0; ks < nk; ++ks)
+                tc::mma_f16(d, tc::smem_desc_sw128(aj + ks * 32), tc::smem_desc_sw128(b0 + ks * 32),
+                            kIdesc, (j > 0 || ks > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(bar(kBarBEmpty + s));
+            last = gs;
+            any = true;
           }
-          tc::mma_commit(bar(kBarBEmpty + s));
+          if (!ok) break;
           tc::mma_commit(bar(kBarAccFull + b));
-          if (c == nch - 1) tc::mma_commit(bar(kBarAEmpty));
-          any = true;
         }
         if (!ok) {
           fail();
           break;
         }
+        tc::mma_commit(bar(kBarAEmpty + ab));
       }
-      // drain: the last commit covers every MMA this thread issued
-      if (any) tc::mbar_wait_bounded(bar(kBarAccFull + ((g - 1) & 1)), ((g - 1) >> 1) & 1, kSWaitNs);
+      // drain: every MMA is followed by its stage's commit before this
+      // thread waits on anything else, so the last stage commit covers them all
+      if (any) tc::mbar_wait_bounded(bar(kBarBEmpty + last % kStages), (last / kStages) & 1, kSWaitNs);
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int tile = warp >> 2, quarter = warp & 3;
+    const int quarter = warp & 3, half = warp >> 2;
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     uint32_t g = 0;
-    for (int64_t pair = blockIdx.x; pair < npairs; pair += gridDim.x) {
-      const int64_t p = (pair * kSTiles + tile) * kSTile + row;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const int64_t p = tile * kSTile + row;
       const bool act = p < a.P && a.status[p] > 0;
       const float win = act ? a.win[p] : 0.0f;
-      float tv[Sh::NT];
-      int ti[Sh::NT];
+      float tv[kTcTop];
+      int ti[kTcTop];
 #pragma unroll
-      for (int q = 0; q < Sh::NT; ++q) {
+      for (int q = 0; q < kTcTop; ++q) {
         tv[q] = -INFINITY;
         ti[q] = -1;
       }
       float disc = -INFINITY;
-      bool ok = true;
       for (int c = 0; c < nch; ++c, ++g) {
         const uint32_t b = g & 1, ub = g >> 1;
         const bool done = !*s_abort && tc::mbar_wait_bounded(bar(kBarAccFull + b), ub & 1, kSWaitNs);
@@ -236,16 +252,22 @@ __global__ void __launch_bounds__(kSThreads, 1)
           break;
         }
         tc::fence_after_sync();
-        const uint32_t taddr = tmem + lane_base + (uint32_t)(tile * 2 + b) * Sh::BUFC;
-        const int nvalid = min(BR, a.MR - c * BR);
+        // this warp's column half of the buffer, hc = half xor (chunk parity),
+        // so the same atom at consecutive angles (consecutive chunks when a
+        // chunk is one angle) alternates between the two lists: plain rows
+        // hc*N/2 .. + N/2 - 1 of the chunk; paired: pairs hc*N/2 .. + N/2 - 1,
+        // their even parts in columns 0..N-1 and odd parts in N..2N-1
+        const int hc = half ^ (c & 1);
+        const uint32_t taddr = tmem + lane_base + b * kSBufC + (uint32_t)(hc * Sh::HALF);
+        const int nvalid = min(N, a.MR - c * N) - hc * Sh::HALF;
 #pragma unroll 1
-        for (int piece = 0; piece < BR / 32; ++piece) {
+        for (int piece = 0; piece < Sh::PIECES; ++piece) {
           uint32_t v[32];
           tc::tmem_ld32(taddr + piece * 32, v);
           if (PAIRED) {
             // pair value |E| + |O| = max(|score(r)|, |score(r + R/2)|)
             uint32_t o[32];
-            tc::tmem_ld32(taddr + kTcBP + piece * 32, o);
+            tc::tmem_ld32(taddr + N + piece * 32, o);
             tc::tmem_wait_ld();
 #pragma unroll
             for (int u = 0; u < 32; ++u)
@@ -259,7 +281,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
             // bits, so one max gives the block maximum and its column (the
             // truncation is < 2^-18 relative and covered by the refine's
             // error bound)
-            const int base = c * BR + piece * 32;
+            const int base = c * N + hc * Sh::HALF + piece * 32;
             const int nv = nvalid - piece * 32;
             float key[32];
 #pragma unroll
@@ -275,7 +297,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
             for (int u = 0; u < 32; u += 2) m1 = fmax3(m1, key[u], key[u + 1]);
             // kept: the block maximum beats the last kept one and is not below
             // the window under the running best (NaN-safe form)
-            if (m1 >= 0.0f && m1 > tv[Sh::NT - 1] && !(m1 < tv[0] - win)) {
+            if (m1 >= 0.0f && m1 > tv[kTcTop - 1] && !(m1 < tv[0] - win)) {
               const int us = __float_as_int(m1) & 31;
               float m2 = -1.0f;
 #pragma unroll
@@ -303,14 +325,13 @@ __global__ void __launch_bounds__(kSThreads, 1)
       }
       if (!ok) break;
       if (act) {
-        int *ci = a.cand_idx + p * Sh::NT;
-        float *cv = a.cand_val + p * Sh::NT;
-#pragma unroll
-        for (int q = 0; q < Sh::NT; q += 4) {
-          *reinterpret_cast<int4 *>(ci + q) = make_int4(ti[q], ti[q + 1], ti[q + 2], ti[q + 3]);
-          *reinterpret_cast<float4 *>(cv + q) = make_float4(tv[q], tv[q + 1], tv[q + 2], tv[q + 3]);
-        }
-        a.cand_disc[p] = disc;
+        // this half's list: entries [half * kTcTop, half * kTcTop + kTcTop)
+        // of the patch's kTcCand candidates; the refine takes the union
+        int *ci = a.cand_idx + p * kTcCand + half * kTcTop;
+        float *cv = a.cand_val + p * kTcCand + half * kTcTop;
+        *reinterpret_cast<int4 *>(ci) = make_int4(ti[0], ti[1], ti[2], ti[3]);
+        *reinterpret_cast<float4 *>(cv) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+        a.cand_disc[p * 2 + half] = disc;
       }
     }
   }
@@ -318,7 +339,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+  if (warp == 0) tc::tmem_dealloc(tmem, kSCols);
 }
 
 }  // namespace
@@ -338,8 +359,8 @@ int launch_score_t(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap
   auto kern = romp_score_kernel<PAIRED, NB>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, total);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
-  const int64_t pairs = (a.P + kSTiles * kSTile - 1) / (kSTiles * kSTile);
-  const int64_t grid = pairs < nsm ? pairs : nsm;
+  const int64_t tiles = (a.P + kSTile - 1) / kSTile;
+  const int64_t grid = tiles < nsm ? tiles : nsm;
   kern<<<(unsigned)grid, kSThreads, total, stream>>>(tmA, tmB, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);

@@ -232,9 +232,10 @@ int build_tc_tables(rsc_dict *d, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
 
-  int rc = encode_rows_map(&d->tmap_b, d->steered_f16, rows, L == kTcKst ? kTcBN : kTcBP, L);
+  int rc = encode_rows_map(&d->tmap_b, d->steered_f16, rows, kTcBN, L);
+  if (rc == RSC_OK) rc = encode_rows_map(&d->tmap_bs, d->steered_f16, rows, kTcSN, L);
   if (rc == RSC_OK && paired)
-    rc = encode_rows_map(&d->tmap_bp, d->paired_f16, rows / 2, kTcBP, kTcKst);
+    rc = encode_rows_map(&d->tmap_bp, d->paired_f16, rows / 2, kTcSNP, kTcKst);
   return rc;
 }
 
@@ -255,8 +256,8 @@ size_t f16_scratch_bytes(int64_t P, int K, int L) {
   int nD = 0, nF = 0, nI = 0;
   rsc_state_layout(K, &nD, &nF, &nI);
   auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  return al256((size_t)P * L * 2) + 2 * al256((size_t)P * rsc_ntop(L) * 4) +
-         3 * al256((size_t)P * 4) + al256((size_t)nD * P * 8) + al256((size_t)nF * P * 4) +
+  return al256((size_t)P * L * 2) + 2 * al256((size_t)P * kTcCand * 4) + al256((size_t)P * 8) +
+         2 * al256((size_t)P * 4) + al256((size_t)nD * P * 8) + al256((size_t)nF * P * 4) +
          al256((size_t)nI * P * 4) + al256((size_t)(P + 4) * 4);
 }
 
@@ -293,9 +294,9 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   ra.anorm = dict->anorm;
   ra.L = dict->row_len;
   ra.A = take((size_t)P * ra.L * 2);
-  ra.cand_idx = reinterpret_cast<int *>(take((size_t)P * rsc_ntop(ra.L) * 4));
-  ra.cand_val = reinterpret_cast<float *>(take((size_t)P * rsc_ntop(ra.L) * 4));
-  ra.cand_disc = reinterpret_cast<float *>(take((size_t)P * 4));
+  ra.cand_idx = reinterpret_cast<int *>(take((size_t)P * kTcCand * 4));
+  ra.cand_val = reinterpret_cast<float *>(take((size_t)P * kTcCand * 4));
+  ra.cand_disc = reinterpret_cast<float *>(take((size_t)P * 8));
   ra.status = reinterpret_cast<int *>(take((size_t)P * 4));
   ra.win = reinterpret_cast<float *>(take((size_t)P * 4));
   ra.sD = reinterpret_cast<double *>(take((size_t)nD * P * 8));
@@ -319,8 +320,8 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   sa.ke = dict->ke;
   sa.ko = dict->ko;
   sa.MR = sa.paired ? dict->M * (dict->R / 2) : dict->M * dict->R;
-  // B rows per chunk: 128 (short plain rows) or 64 (paired, long rows)
-  const int br = (sa.paired || sa.L != kTcKst) ? kTcBP : kTcBN;
+  // B rows per chunk: kTcSN atoms (plain) or kTcSNP atom pairs (paired)
+  const int br = sa.paired ? kTcSNP : kTcSN;
   sa.nchunks = (sa.MR + br - 1) / br;
   sa.status = ra.status;
   sa.cand_idx = const_cast<int *>(ra.cand_idx);
@@ -341,7 +342,7 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   }
   for (int step = 0; step < K && rc == RSC_OK; ++step) {
     int slot = timing_begin(dict, 0, st);
-    rc = rsc_launch_score(sa, tmA, sa.paired ? dict->tmap_bp : dict->tmap_b, st);
+    rc = rsc_launch_score(sa, tmA, sa.paired ? dict->tmap_bp : dict->tmap_bs, st);
     timing_end(dict, slot, st);
     if (rc != RSC_OK) break;
     slot = timing_begin(dict, 2, st);

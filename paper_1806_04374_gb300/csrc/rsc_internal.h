@@ -40,8 +40,9 @@ struct rsc_dict {
   // per-phase timing (diagnostic): event pairs recorded around launches
   int timing;
   void *timing_state;    // owned std::vector of recorded pairs, see rsc_capi.cu
-  CUtensorMap tmap_b;    // TMA map of steered_f16, box 64 x kTcBN, 128B swizzle
-  CUtensorMap tmap_bp;   // TMA map of paired_f16, box 64 x kTcBP, 128B swizzle
+  CUtensorMap tmap_b;    // TMA map of steered_f16, box 64 x kTcBN (fused kernel)
+  CUtensorMap tmap_bs;   // TMA map of steered_f16, box 64 x kTcSN (scoring pass)
+  CUtensorMap tmap_bp;   // TMA map of paired_f16, box 64 x kTcSNP (scoring pass)
 };
 
 // Packed real coordinates of a half spectrum, shared by the tensor-core
@@ -55,7 +56,8 @@ constexpr int kTcMaxN = 256; // packed lengths the tensor-core path handles
 constexpr int kTcBN = 128;   // steered atoms per MMA (N) and per TMA box
 constexpr int kTcMaxK = 8;   // greedy steps the tensor-core path handles
 
-constexpr int kTcBP = 64;   // steered-atom pairs per MMA chunk, paired layout
+constexpr int kTcSN = 256;   // steered atoms per chunk (MMA N) of the scoring pass
+constexpr int kTcSNP = 128;  // steered-atom pairs per chunk (MMA N), paired layout
 
 // Slot layouts of a packed row (kTcKst fp16 slots) of the tensor-core path;
 // returns (e << 8) | (k << 1) | c for slot q holding Re (c = 0) or Im (c = 1)
@@ -140,18 +142,16 @@ struct TcArgs {
 int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream);
 
 // Candidates (block maxima and in-window second values) kept per patch and
-// greedy step by the tensor-core scoring: 4 for rows of kTcKst slots, 8 for
-// rows of kTcKstLong slots (the larger atom x angle grids those shapes come
-// with, e.g. M = 256, R = 128, put more units within the certification
-// window; with 4 a patch would be handed to the FP32 path at ~0.6% of steps).
+// greedy step by the tensor-core scoring: kTcTop per list; the split scoring
+// pass keeps one list per half of the accumulator columns, kTcCand in all.
 constexpr int kTcTop = 4;
-constexpr int kTcTopLong = 8;
-constexpr int rsc_ntop(int L) { return L == kTcKstLong ? kTcTopLong : kTcTop; }
+constexpr int kTcCand = 2 * kTcTop;
 
 // One scoring pass of the split FP16 path (romp_score.cu): packed fp16
 // residual rows (TMA map tmA: [P][kTcKst]) times the steered dictionary
-// (tmB) -> per patch the rsc_ntop(L) largest candidates of |score| with
-// their rows (r*M + m) and the largest value left out.
+// (tmB) -> per patch two lists (one per half of each chunk's rows) of the
+// kTcTop largest candidates of |score| with their rows (r*M + m), and the
+// largest value each list left out.
 struct ScoreArgs {
   int64_t P;
   int ksteps, MR, nchunks;
@@ -160,9 +160,9 @@ struct ScoreArgs {
   int paired, ke, ko;
   int L;  // packed row length (kTcKst or kTcKstLong; the latter plain only)
   const int *status;  // > 0: patch still being coded
-  int *cand_idx;      // [P][rsc_ntop(L)]
-  float *cand_val;    // [P][rsc_ntop(L)]
-  float *cand_disc;   // [P]
+  int *cand_idx;      // [P][kTcCand]
+  float *cand_val;    // [P][kTcCand]
+  float *cand_disc;   // [P][2]
   // [P] per-patch certification window in accumulator units (written by the
   // refine pass with the row): a block maximum more than `win` below the
   // running best can neither win nor reach the window, so it is not kept

@@ -49,7 +49,7 @@ __device__ __forceinline__ bool df_abs_eq(df a, df b) {
   return a.hi == b.hi && a.lo == b.lo;
 }
 
-constexpr int kTop = kTcTop;  // candidates kept per patch and step (rows of kTcKst)
+constexpr int kTop = kTcTop;  // candidates kept per list, patch and step
 
 // Inserts (x, idx) into the descending list (v, i) of NT entries; disc
 // keeps the largest value that did not stay in the list.  Strict comparisons
