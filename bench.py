@@ -383,7 +383,7 @@ def run_c2(args) -> None:
     rsc.load_library()
     N, J, kmax, M, R, K = 21, 10, 12, 256, 128, 8
     rng = np.random.default_rng(20180621)
-    sides = rng.integers(64, 513, size=512)
+    sides = rng.integers(64, 513, size=512)[:args.c2_images]
     imgs = [torch.from_numpy(synth.make_line_image(int(s_), int(s_), 0.01, 20180621 + i)).to(dev)
             for i, s_ in enumerate(sides)]
     basis = rsc.Basis(N, J, kmax)
@@ -403,8 +403,8 @@ def run_c2(args) -> None:
         "unit": "patches/s", "n_gpus": 1, "dtype": "f16" if args.precision == "f16" else "f32",
         "data": "synthetic", "s": dt, "patches": P, "mean_steps_taken": steps,
         "handoffs": rsc.rsc_dict_fallback_count(dic.handle),
-        "config": {"workload": "512 images, side U{64..512}, N=21 (349 px), J=10, kmax=12 "
-                               "(n=250), M=256, R=128, K=8"}}))
+        "config": {"workload": f"{len(sides)} images, side U{{64..512}}, N=21 (349 px), J=10, "
+                               "kmax=12 (n=250), M=256, R=128, K=8"}}))
     dic.close()
     basis.close()
 
@@ -508,6 +508,8 @@ def main():
     ap.add_argument("--serve-batch", type=int, default=4_000_000)
     ap.add_argument("--c2", action="store_true",
                     help="code the full 21x21-patch image workload once instead")
+    ap.add_argument("--c2-images", type=int, default=512,
+                    help="with --c2: code only the first N of its 512 images (profiling)")
     args = ap.parse_args()
     if args.c2:
         run_c2(args)
