@@ -157,43 +157,106 @@ struct ImageItem {
   int64_t first;  // index of the image's first patch
 };
 
-__global__ void project_kernel(const ImageItem *items, int n_items, int64_t P_total, int N,
-                               int npix, const int2 *offs, const float *Po, int nout,
-                               int nout_pad, float *coef) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P_total;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = n_items - 1;  // last item with first <= g
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (items[mid].first <= g) lo = mid; else hi = mid - 1;
+// One pass of project_kernel: outputs oc .. oc + W - 1 of every window of the
+// block's tile, the operator's W columns staged in shared memory (npix x W
+// floats) and read by all threads as broadcasts; each thread accumulates its
+// window's W outputs over the pixels in order (FP32 FMA).
+template <int W>
+__device__ __forceinline__ void project_pass(float *sP, const float *Po, int npix, int nout_pad,
+                                             int oc, const float *base, int w, const int2 *offs,
+                                             float *out, int nout, bool vec) {
+  __syncthreads();  // the previous pass is done with sP
+  for (int i = threadIdx.x; i < npix * (W / 4); i += blockDim.x) {
+    const int p = i / (W / 4), c = i - p * (W / 4);
+    reinterpret_cast<float4 *>(sP)[i] =
+        __ldg(reinterpret_cast<const float4 *>(Po + (size_t)p * nout_pad + oc) + c);
+  }
+  __syncthreads();
+  if (!base) return;
+  float acc[W];
+#pragma unroll
+  for (int u = 0; u < W; ++u) acc[u] = 0.0f;
+  // pixels are loaded four at a time ahead of their FMAs (two warps per
+  // scheduler do not hide a load's latency otherwise); the sums keep the
+  // pixel order
+  constexpr int kAhead = 4;
+  int p = 0;
+  for (; p + kAhead <= npix; p += kAhead) {
+    float v[kAhead];
+#pragma unroll
+    for (int k = 0; k < kAhead; ++k) {
+      const int2 o = __ldg(offs + p + k);
+      v[k] = __ldg(base + (int64_t)o.x * w + o.y);
     }
-    const ImageItem it = items[lo];
-    const int64_t local = g - it.first;
-    const int nw = it.w - N + 1;
-    const int r0 = (int)(local / nw), c0 = (int)(local - (int64_t)r0 * nw);
-    const float *base = it.img + (int64_t)r0 * it.w + c0;
-    float *out = coef + g * nout;
-    for (int oc = 0; oc < nout; oc += 32) {
-      float acc[32];
 #pragma unroll
-      for (int u = 0; u < 32; ++u) acc[u] = 0.0f;
-      for (int p = 0; p < npix; ++p) {
-        const int2 o = __ldg(offs + p);
-        const float v = __ldg(base + (int64_t)o.x * it.w + o.y);
-        const float4 *row = reinterpret_cast<const float4 *>(Po + (size_t)p * nout_pad + oc);
+    for (int k = 0; k < kAhead; ++k) {
+      const float4 *row = reinterpret_cast<const float4 *>(sP + (p + k) * W);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float4 q = __ldg(row + u);
-          acc[4 * u] = fmaf(q.x, v, acc[4 * u]);
-          acc[4 * u + 1] = fmaf(q.y, v, acc[4 * u + 1]);
-          acc[4 * u + 2] = fmaf(q.z, v, acc[4 * u + 2]);
-          acc[4 * u + 3] = fmaf(q.w, v, acc[4 * u + 3]);
-        }
+      for (int u = 0; u < W / 4; ++u) {
+        const float4 q = row[u];
+        acc[4 * u] = fmaf(q.x, v[k], acc[4 * u]);
+        acc[4 * u + 1] = fmaf(q.y, v[k], acc[4 * u + 1]);
+        acc[4 * u + 2] = fmaf(q.z, v[k], acc[4 * u + 2]);
+        acc[4 * u + 3] = fmaf(q.w, v[k], acc[4 * u + 3]);
       }
-#pragma unroll
-      for (int u = 0; u < 32; ++u)
-        if (oc + u < nout) out[oc + u] = acc[u];
     }
+  }
+  for (; p < npix; ++p) {
+    const int2 o = __ldg(offs + p);
+    const float v = __ldg(base + (int64_t)o.x * w + o.y);
+    const float4 *row = reinterpret_cast<const float4 *>(sP + p * W);
+#pragma unroll
+    for (int u = 0; u < W / 4; ++u) {
+      const float4 q = row[u];
+      acc[4 * u] = fmaf(q.x, v, acc[4 * u]);
+      acc[4 * u + 1] = fmaf(q.y, v, acc[4 * u + 1]);
+      acc[4 * u + 2] = fmaf(q.z, v, acc[4 * u + 2]);
+      acc[4 * u + 3] = fmaf(q.w, v, acc[4 * u + 3]);
+    }
+  }
+  if (vec && oc + W <= nout) {
+#pragma unroll
+    for (int u = 0; u < W; u += 4)
+      *reinterpret_cast<float4 *>(out + oc + u) = make_float4(acc[u], acc[u + 1], acc[u + 2], acc[u + 3]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < W; ++u)
+      if (oc + u < nout) out[oc + u] = acc[u];
+  }
+}
+
+// Projection on the CUDA cores (windows of any size): one thread per window,
+// 64 outputs per pass (a last pass of 32 when the padded output count asks
+// for it), the operator slab in shared memory.
+__global__ void __launch_bounds__(128) project_kernel(const ImageItem *items, int n_items,
+                                                       int64_t P_total, int N, int npix,
+                                                       const int2 *offs, const float *Po, int nout,
+                                                       int nout_pad, float *coef) {
+  extern __shared__ float sP[];
+  const bool vec = (reinterpret_cast<uintptr_t>(coef) & 15) == 0 && (nout & 3) == 0;
+  const int64_t ntiles = (P_total + blockDim.x - 1) / blockDim.x;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t g = t * blockDim.x + threadIdx.x;
+    const float *base = nullptr;
+    int w = 0;
+    if (g < P_total) {
+      int lo = 0, hi = n_items - 1;  // last item with first <= g
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].first <= g) lo = mid; else hi = mid - 1;
+      }
+      const ImageItem it = items[lo];
+      const int64_t local = g - it.first;
+      const int nw = it.w - N + 1;
+      const int r0 = (int)(local / nw), c0 = (int)(local - (int64_t)r0 * nw);
+      base = it.img + (int64_t)r0 * it.w + c0;
+      w = it.w;
+    }
+    float *out = coef + (g < P_total ? g : 0) * nout;
+    int oc = 0;
+    for (; oc + 64 <= nout_pad && oc < nout; oc += 64)
+      project_pass<64>(sP, Po, npix, nout_pad, oc, base, w, offs, out, nout, vec);
+    if (oc < nout) project_pass<32>(sP, Po, npix, nout_pad, oc, base, w, offs, out, nout, vec);
   }
 }
 
@@ -412,10 +475,15 @@ int launch_project(const rsc_basis *b, const ImageItem *items_dev, int n_items, 
     return e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
   }
   const int64_t blocks = (P_total + 127) / 128;
-  const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)nsm * 16);
-  project_kernel<<<grid, 128, 0, st>>>(items_dev, n_items, P_total, b->N, b->npix, b->offs, b->Po,
-                                       b->nout, b->nout_pad, coef);
-  cudaError_t e = cudaGetLastError();
+  const int shm = b->npix * 64 * (int)sizeof(float);
+  cudaError_t e =
+      cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  const int per_sm = std::max(1, std::min(4, (220 * 1024) / shm));  // by shared memory, registers
+  const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)nsm * per_sm);
+  project_kernel<<<grid, 128, shm, st>>>(items_dev, n_items, P_total, b->N, b->npix, b->offs,
+                                         b->Po, b->nout, b->nout_pad, coef);
+  e = cudaGetLastError();
   return e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
 }
 
