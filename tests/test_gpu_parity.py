@@ -67,6 +67,32 @@ def test_1m_workload_sampled(rsc, precision):
     assert np.isfinite(g["coef"]).all()
 
 
+@pytest.mark.parametrize("shape", [
+    # (name, M, J, kmax, R, K, P): plain rows of 112 slots (odd R), one
+    # 256-row chunk per tile; rows of 256 slots, 8 chunks per tile, two
+    # stream groups (P >= 2 x 65,536)
+    ("plain112_R33", 7, 6, 8, 33, 3, 60000),
+    ("long_rows_n250", 32, 10, 12, 64, 4, 140000),
+], ids=lambda c: c[0])
+def test_many_tiles_per_cta_sampled(rsc, shape):
+    """Enough patches that every scoring CTA codes several 128-patch tiles
+    in one launch, so its residual-row buffers are reused (the paired layout
+    is covered by test_1m_workload_sampled): 400 sampled patches, including
+    tile edges and both ends, checked against the oracle."""
+    name, M, J, kmax, R, K, P = shape
+    d = synth.make_dictionary(M, J, kmax, 3000 + M)
+    x, _ = synth.make_patches(d, P, 3, 0.05, 4000 + R)
+    g = run_gpu(rsc, x, d, R, K, "f16")
+    rng = np.random.default_rng(11)
+    edges = [0, 127, 128, 255, 256, P // 2 - 1, P // 2, P - 129, P - 128, P - 1]
+    idx = np.unique(np.concatenate([edges, rng.choice(P, 390, replace=False)]))
+    sub = {k: (v[idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+    s = check(x[idx], d, R, K, sub, COEF_TOL["f16"])
+    print(name, s, "fallbacks", g["fallbacks"])
+    assert g["atom"].min() >= -1 and g["atom"].max() < M
+    assert np.isfinite(g["coef"]).all()
+
+
 CASES = [
     # (name, M, J, kmax, R, K, P, n_terms, sigma)
     ("R1_textbook_omp", 12, 6, 8, 1, 4, 97, 3, 0.05),
