@@ -45,6 +45,12 @@ struct rsc_basis {
   // part and the lo part of what hi leaves
   uint16_t *Bt;  // device [2][NP][KP]
   int KP, NP, sb;
+  // tensor-core projection of larger windows (128 < npix <= 512, n <= 256;
+  // null otherwise): [2][256 packed outputs][KPw pixels] fp16, hi then lo,
+  // times 2^sbw, streamed by TMA (map tmW: box 64 pixels x 256 outputs)
+  uint16_t *Bw;
+  int KPw, sbw;
+  CUtensorMap tmW;
   int *err;      // device error word of the projection kernels (bounded waits)
 };
 
@@ -447,6 +453,236 @@ __global__ void __launch_bounds__(kPjThreads, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kPjRows);
 }
 
+// Projection of larger windows (kTcKst < npix <= 512 pixels, n <= 256
+// packed outputs, e.g. 21 x 21: 349 px -> 250) on the tensor cores.  The
+// split operator (hi and lo fp16, [2][256 outputs][KPw pixels], packed output
+// order, times 2^sbw) is too large for shared memory, so it streams from L2
+// one 64-pixel K-block at a time.  Per CTA and tile of 128 windows:
+//   * warps 0-3 (one thread per window) gather each K-block's 64 pixels,
+//     scaled by 2^sa and split into hi and lo, into 128-byte-swizzled K-major
+//     rows of a 2-stage A ring, then read the accumulator back and write the
+//     half spectrum;
+//   * warp 4 (one lane) loads the operator's K-block (hi and lo, 64 KB) into
+//     a 2-stage B ring with TMA;
+//   * warp 5 (one lane) issues hi*hi + hi*lo + lo*hi (3 x 4 MMAs, M = 128,
+//     N = 256) per K-block into one 256-column TMEM accumulator.
+// The gather warps' TMEM reads of tile t finish before they hand over the
+// first A block of tile t + 1 (tcgen05 fences around that mbarrier), so the
+// accumulator needs no second handshake.  Every wait is bounded.
+constexpr int kPwThreads = 192;
+constexpr int kPwBlkA = 128 * 128;     // one part (hi or lo) of an A K-block (bytes)
+constexpr int kPwStageA = 2 * kPwBlkA;
+constexpr int kPwBlkB = 256 * 128;     // one part of a B K-block: 256 outputs x 64 px
+constexpr int kPwStageB = 2 * kPwBlkB;
+constexpr int kPwStages = 2;
+constexpr int kPwNP = 256;             // MMA N: packed outputs, padded
+constexpr int kPwBarOff = kPwStages * (kPwStageA + kPwStageB);
+constexpr int kPwSmem = kPwBarOff + 128 + 1024;
+enum : int { kPwAFull = 0, kPwAEmpty = 2, kPwBFull = 4, kPwBEmpty = 6, kPwAcc = 8, kPwBars = 9 };
+
+__global__ void __launch_bounds__(kPwThreads, 1)
+    project_tcw_kernel(const __grid_constant__ CUtensorMap tmW, const ImageItem *items,
+                       int n_items, int64_t P_total, int N, int npix, int nkb, const int2 *offs,
+                       int J, int n, int sb, int nout, float *coef, int *err) {
+  extern __shared__ unsigned char pw_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(pw_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char *sA = smem;
+  unsigned char *sB = smem + kPwStages * kPwStageA;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kPwBarOff);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + kPwBars);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(bars + kPwBars) + 1;
+  const uint32_t bar0 = tc::smem_u32(bars);
+  auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < kPwStages; ++i) {
+      tc::mbar_init(bar(kPwAFull + i), 4);  // one arrival per gather warp
+      tc::mbar_init(bar(kPwAEmpty + i), 1);
+      tc::mbar_init(bar(kPwBFull + i), 1);
+      tc::mbar_init(bar(kPwBEmpty + i), 1);
+    }
+    tc::mbar_init(bar(kPwAcc), 1);
+    *s_abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(s_tmem), kPwNP);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *s_tmem;
+  const int64_t ntiles = (P_total + 127) / 128;
+  auto fail = [&]() {
+    *s_abort = 1;
+    if (err) atomicCAS(err, 0, RSC_ERR_TIMEOUT);
+  };
+
+  if (warp == 4) {
+    // ------------------------------------------------------------ TMA (B)
+    if (lane == 0) {
+      uint32_t gj = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; ok && t < ntiles && !*s_abort; t += gridDim.x) {
+        for (int j = 0; j < nkb; ++j, ++gj) {
+          const int s = (int)(gj % kPwStages);
+          if (gj >= (uint32_t)kPwStages &&
+              !tc::mbar_wait_bounded(bar(kPwBEmpty + s), ((gj / kPwStages) - 1) & 1, kPjWaitNs)) {
+            fail();
+            ok = false;
+            break;
+          }
+          const uint32_t dst = tc::smem_u32(sB + s * kPwStageB);
+          tc::mbar_arrive_expect_tx(bar(kPwBFull + s), kPwStageB);
+          tc::tma_load_2d(dst, &tmW, bar(kPwBFull + s), 64 * j, 0);
+          tc::tma_load_2d(dst + kPwBlkB, &tmW, bar(kPwBFull + s), 64 * j, kPwNP);
+        }
+      }
+      for (uint32_t i = (gj > (uint32_t)kPwStages ? gj - kPwStages : 0); i < gj; ++i)
+        tc::mbar_wait_bounded(bar(kPwBFull + i % kPwStages), (i / kPwStages) & 1, kPjWaitNs);
+    }
+  } else if (warp == 5) {
+    // ------------------------------------------------------------ MMA
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_f16_f32(128, kPwNP);
+      uint32_t gj = 0, last = 0;
+      bool any = false, ok = true;
+      for (int64_t t = blockIdx.x; ok && t < ntiles && !*s_abort; t += gridDim.x) {
+        for (int j = 0; j < nkb; ++j, ++gj) {
+          const int s = (int)(gj % kPwStages);
+          const uint32_t par = (gj / kPwStages) & 1;
+          if (!tc::mbar_wait_bounded(bar(kPwAFull + s), par, kPjWaitNs) ||
+              !tc::mbar_wait_bounded(bar(kPwBFull + s), par, kPjWaitNs)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t a_hi = tc::smem_u32(sA + s * kPwStageA), a_lo = a_hi + kPwBlkA;
+          const uint32_t b_hi = tc::smem_u32(sB + s * kPwStageB), b_lo = b_hi + kPwBlkB;
+          for (int prod = 0; prod < 3; ++prod) {
+            const uint32_t aa = prod == 2 ? a_lo : a_hi, bb = prod == 1 ? b_lo : b_hi;
+            for (int ks = 0; ks < 4; ++ks)
+              tc::mma_f16(tmem, tc::smem_desc_sw128(aa + ks * 32), tc::smem_desc_sw128(bb + ks * 32),
+                          idesc, (j | prod | ks) ? 1u : 0u);
+          }
+          tc::mma_commit(bar(kPwAEmpty + s));
+          tc::mma_commit(bar(kPwBEmpty + s));
+          last = gj;
+          any = true;
+          if (j == nkb - 1) tc::mma_commit(bar(kPwAcc));
+        }
+      }
+      // every MMA is followed by its stage's commit: the last one covers all
+      if (any)
+        tc::mbar_wait_bounded(bar(kPwAEmpty + last % kPwStages), (last / kPwStages) & 1, kPjWaitNs);
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------ gather and epilogue
+    const int row = tid;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint32_t gj = 0, it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
+      const int64_t p = t * 128 + row;
+      const float *base = nullptr;
+      int w = 0;
+      float amax = 0.0f;
+      if (p < P_total) {
+        int lo = 0, hi = n_items - 1;  // last item with first <= p
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (items[mid].first <= p) lo = mid; else hi = mid - 1;
+        }
+        const ImageItem itm = items[lo];
+        const int64_t local = p - itm.first;
+        const int nw = itm.w - N + 1;
+        const int r0 = (int)(local / nw), c0 = (int)(local - (int64_t)r0 * nw);
+        base = itm.img + (int64_t)r0 * itm.w + c0;
+        w = itm.w;
+        for (int q = 0; q < npix; ++q) {
+          const int2 o = __ldg(offs + q);
+          amax = fmaxf(amax, fabsf(__ldg(base + (int64_t)o.x * w + o.y)));
+        }
+      }
+      int ea = 0;
+      (void)frexpf(amax, &ea);
+      const int sa = 14 - (ea < -100 ? -100 : (ea > 127 ? 127 : ea));  // max |x| 2^sa < 2^14
+      const float scale = ldexpf(1.0f, sa);
+      for (int j = 0; j < nkb; ++j, ++gj) {
+        const int s = (int)(gj % kPwStages);
+        const bool done = !*s_abort && (gj < (uint32_t)kPwStages ||
+                                        tc::mbar_wait_bounded(bar(kPwAEmpty + s),
+                                                              ((gj / kPwStages) - 1) & 1, kPjWaitNs));
+        if (!__all_sync(0xffffffffu, done)) {
+          if (lane == 0) fail();
+          ok = false;
+          break;
+        }
+        unsigned char *dst = sA + s * kPwStageA;
+        for (int c = 0; c < 8; ++c) {
+          uint32_t hv[4], lv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float x2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int q = j * 64 + c * 8 + 2 * u + h;
+              float x = 0.0f;
+              if (base && q < npix) {
+                const int2 o = __ldg(offs + q);
+                x = __ldg(base + (int64_t)o.x * w + o.y) * scale;
+              }
+              x2[h] = x;
+            }
+            const __half2 hh = __floats2half2_rn(x2[0], x2[1]);
+            const float2 hf = __half22float2(hh);
+            const __half2 ll = __floats2half2_rn(x2[0] - hf.x, x2[1] - hf.y);
+            hv[u] = *reinterpret_cast<const uint32_t *>(&hh);
+            lv[u] = *reinterpret_cast<const uint32_t *>(&ll);
+          }
+          const int off = row * 128 + ((c ^ (row & 7)) << 4);
+          *reinterpret_cast<uint4 *>(dst + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<uint4 *>(dst + kPwBlkA + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(kPwAFull + s)) : "memory");
+      }
+      if (!ok) break;
+      // ---- read the accumulator back: packed output q -> half spectrum
+      // index 2q (q < J: Re of k = 0, whose Im is 0) or J + q
+      const bool done = !*s_abort && tc::mbar_wait_bounded(bar(kPwAcc), it & 1, kPjWaitNs);
+      if (!__all_sync(0xffffffffu, done)) {
+        if (lane == 0) fail();
+        break;
+      }
+      tc::fence_after_sync();
+      const float unscale = ldexpf(1.0f, -(sa + sb));
+      float *out = coef + (p < P_total ? p : 0) * nout;
+      for (int piece = 0; piece * 32 < n; ++piece) {
+        uint32_t v[32];
+        tc::tmem_ld32(tmem + lane_base + piece * 32, v);
+        tc::tmem_wait_ld();
+        if (p < P_total) {
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            const int q = piece * 32 + u;
+            if (q < n) out[q < J ? 2 * q : J + q] = __uint_as_float(v[u]) * unscale;
+          }
+        }
+      }
+      if (p < P_total)
+        for (int jj = 0; jj < J; ++jj) out[2 * jj + 1] = 0.0f;
+      tc::fence_before_sync();
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, kPwNP);
+}
+
 // Reads and clears the basis's device error word (after a synchronisation).
 int take_error(const rsc_basis *b) {
   int v = 0;
@@ -471,6 +707,18 @@ int launch_project(const rsc_basis *b, const ImageItem *items_dev, int n_items, 
     project_tc_kernel<<<grid, kPjThreads, total, st>>>(items_dev, n_items, P_total, b->N,
                                                         b->npix, b->offs, b->Bt, b->KP, b->NP,
                                                         b->sb, b->nout, coef, b->err);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
+  }
+  if (b->Bw) {
+    cudaError_t e = cudaFuncSetAttribute(project_tcw_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPwSmem);
+    if (e != cudaSuccess) return rsc_cuda_fail(e);
+    const int64_t tiles = (P_total + 127) / 128;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)nsm);
+    project_tcw_kernel<<<grid, kPwThreads, kPwSmem, st>>>(
+        b->tmW, items_dev, n_items, P_total, b->N, b->npix, b->KPw / 64, b->offs, b->J, b->n,
+        b->sbw, b->nout, coef, b->err);
     e = cudaGetLastError();
     return e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
   }
@@ -610,8 +858,34 @@ int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, doub
       Bt[Pd.size() + i] = *reinterpret_cast<const uint16_t *>(&lo);
     }
   }
+  // wide operator (packed output order; k >= 1 rows carry 1/sqrt2 like Po)
+  const bool tcw_ok = !tc_ok && npix > 128 && npix <= 512 && n <= kPwNP;
+  const int KPw = (npix + 63) / 64 * 64;
+  int sbw = 0;
+  std::vector<uint16_t> Bw;
+  if (tcw_ok) {
+    std::vector<double> Pd((size_t)kPwNP * KPw, 0.0);
+    double vmax = 0.0;
+    for (int q = 0; q < n; ++q)
+      for (int p = 0; p < npix; ++p)
+        Pd[(size_t)q * KPw + p] = Pr[(size_t)q * npix + p] * (q < J ? 1.0 : M_SQRT1_2);
+    for (double v : Pd) vmax = std::max(vmax, fabs(v));
+    int ev = 0;
+    (void)frexp(vmax, &ev);
+    sbw = 14 - ev;
+    Bw.assign((size_t)2 * kPwNP * KPw, 0);
+    for (size_t i = 0; i < Pd.size(); ++i) {
+      const double v = ldexp(Pd[i], sbw);
+      const __half hi = __float2half_rn((float)v);
+      const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
+      Bw[i] = *reinterpret_cast<const uint16_t *>(&hi);
+      Bw[Pd.size() + i] = *reinterpret_cast<const uint16_t *>(&lo);
+    }
+  }
   rsc_basis *b = new rsc_basis();
   memset(b, 0, sizeof *b);
+  b->KPw = KPw;
+  b->sbw = sbw;
   b->KP = KP;
   b->NP = NP;
   b->sb = sb;
@@ -635,12 +909,19 @@ int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, doub
   if (e == cudaSuccess && tc_ok) e = cudaMalloc(&b->Bt, Bt.size() * sizeof(uint16_t));
   if (e == cudaSuccess && tc_ok)
     e = cudaMemcpy(b->Bt, Bt.data(), Bt.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
+  if (e == cudaSuccess && tcw_ok) e = cudaMalloc(&b->Bw, Bw.size() * sizeof(uint16_t));
+  if (e == cudaSuccess && tcw_ok)
+    e = cudaMemcpy(b->Bw, Bw.data(), Bw.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  int rc = RSC_OK;
+  if (e == cudaSuccess && tcw_ok) rc = rsc_encode_rows_map(&b->tmW, b->Bw, 2 * kPwNP, kPwNP, KPw);
+  if (e != cudaSuccess || rc != RSC_OK) {
     cudaFree(b->offs);
     cudaFree(b->Po);
     cudaFree(b->err);
     cudaFree(b->Bt);
+    cudaFree(b->Bw);
     delete b;
+    if (rc != RSC_OK) return rc;
     if (e == cudaErrorMemoryAllocation) {
       cudaGetLastError();
       return RSC_ERR_OOM;
@@ -657,6 +938,7 @@ int rsc_basis_destroy(rsc_basis *b) {
   cudaFree(b->Po);
   cudaFree(b->err);
   cudaFree(b->Bt);
+  cudaFree(b->Bw);
   delete b;
   return RSC_OK;
 }

@@ -366,6 +366,10 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
 
 }  // namespace
 
+int rsc_encode_rows_map(CUtensorMap *map, void *base, size_t rows, int box_rows, int row_len) {
+  return encode_rows_map(map, base, rows, box_rows, row_len);
+}
+
 int rsc_cuda_fail(cudaError_t e) {
   snprintf(g_cuda_msg, sizeof g_cuda_msg, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   return RSC_ERR_CUDA;

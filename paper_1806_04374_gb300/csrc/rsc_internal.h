@@ -141,6 +141,11 @@ struct TcArgs {
 // candidates overflow are appended to redo_list for the FP32 path.
 int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream);
 
+// TMA map of a row-major fp16 matrix [rows][row_len] (row_len * 2 bytes a
+// multiple of 16): box 64 columns x box_rows rows, 128-byte swizzle, zero fill
+// outside the matrix.
+int rsc_encode_rows_map(CUtensorMap *map, void *base, size_t rows, int box_rows, int row_len);
+
 // Candidates (block maxima and in-window second values) kept per patch and
 // greedy step by the tensor-core scoring: kTcTop per list; the split scoring
 // pass keeps one list per half of the accumulator columns, kTcCand in all.

@@ -47,15 +47,17 @@ def test_project_matches_oracle(rsc, shape):
     b.close()
 
 
-def test_project_unaligned_output_and_scales(rsc):
-    """The tensor-core projection writes 16-byte vectors; an output buffer that
-    is not 16-byte aligned takes the CUDA-core kernel instead, with the same
-    result.  Images far outside fp16's range (1e-20 and 1e20 times the test
-    image) are projected like the oracle does (per-window power-of-two
-    scaling)."""
+@pytest.mark.parametrize("shape", [(11, 6, 8), (21, 10, 12)])
+def test_project_unaligned_output_and_scales(rsc, shape):
+    """11 x 11: the tensor-core projection writes 16-byte vectors, so an
+    output buffer that is not 16-byte aligned takes the CUDA-core kernel
+    instead, with the same result.  21 x 21: the streamed tensor-core kernel
+    writes single floats at any alignment.  Images far outside fp16's range
+    (1e-20 and 1e20 times the test image) are projected like the oracle does
+    (per-window power-of-two scaling)."""
     import ctypes
     import torch
-    N, J, kmax = 11, 6, 8
+    N, J, kmax = shape
     b = rsc.Basis(N, J, kmax)
     img = image(N + 9, N + 14, 8)
     ref = obasis.project(img, N, J, kmax)
@@ -94,6 +96,30 @@ def test_encode_uneven_images(rsc, precision):
     g = {k: v.cpu().numpy() for k, v in out.items()}
     x = np.concatenate([obasis.project(im, N, J, kmax) for im in imgs if min(im.shape) >= N])
     assert g["atom"].shape[0] == x.shape[0] == 13 * 21 + 1 + 0 + 20 * 8
+    s = check(x.astype(np.float32), d, R, K, g, coef_tol=1e-4, margin=1e-4)
+    print(precision, s)
+    dic.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
+def test_encode_images_21x21(rsc, precision):
+    """21 x 21 windows (349 px, n = 250: the streamed tensor-core projection
+    and rows of 256 slots) of uneven images, one smaller than a window, coded
+    in one call and compared with the oracle run on the oracle's own
+    projection (selections pinned at a 1e-4 margin, weights to 1e-4)."""
+    import torch
+    N, J, kmax, M, R, K = 21, 10, 12, 12, 16, 3
+    shapes = [(29, 35), (21, 21), (15, 40), (40, 24)]
+    imgs = [image(h, w, 40 + i) for i, (h, w) in enumerate(shapes)]
+    d = synth.make_dictionary(M, J, kmax, 78)
+    b = rsc.Basis(N, J, kmax)
+    dic = rsc.Dictionary(torch.from_numpy(d).cuda(), R)
+    out = rsc.encode_images(dic, b, [torch.from_numpy(im).cuda() for im in imgs], K, precision)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    x = np.concatenate([obasis.project(im, N, J, kmax) for im in imgs if min(im.shape) >= N])
+    assert g["atom"].shape[0] == x.shape[0] == 9 * 15 + 1 + 0 + 20 * 4
     s = check(x.astype(np.float32), d, R, K, g, coef_tol=1e-4, margin=1e-4)
     print(precision, s)
     dic.close()
