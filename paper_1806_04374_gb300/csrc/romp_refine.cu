@@ -304,15 +304,28 @@ __global__ void __launch_bounds__(128, KK > 5 ? 3 : 5) romp_refine_kernel(const 
 #pragma unroll
         for (int i = 0; i < KK; ++i) bg[i] = df_make(0.0f);
         int bm = -1, br = 0, bflat = 0;
+        // the slots inside the window as a bit mask, so that the warp runs the
+        // re-scoring body max(units per lane) times, not once per slot
+        // position at which some lane has a unit
+        unsigned mask = 0;
+        {
+          const int4 i0 = *reinterpret_cast<const int4 *>(cip);
+          const int4 i1 = *reinterpret_cast<const int4 *>(cip + 4);
+          const float4 v0 = *reinterpret_cast<const float4 *>(cvp);
+          const float4 v1 = *reinterpret_cast<const float4 *>(cvp + 4);
+          const int iv[kTcCand] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+          const float vv[kTcCand] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+          for (int q = 0; q < kTcCand; ++q)
+            if (iv[q] >= 0 && vv[q] * unscale >= thr) mask |= 1u << q;
+        }
+        static_assert(kTcCand == 8, "candidate slots are read as two int4 / float4");
 #pragma unroll 1
-        for (int q = 0; q < kTcCand; ++q) {
-          const float val = cvp[q] * unscale;
+        while (mask) {
+          const int q = __ffs(mask) - 1;
+          mask &= mask - 1;
           const int id = cip[q];
-          const bool any = id >= 0 && val >= thr;
-          // each list is sorted: past its first entry outside the window the
-          // rest of that list is outside too
-          if (!any) q |= kTcTop - 1;
-          if (any) {
+          {
             const int m = id % M, r = id / M;
             df ax[NP], sc[NP], gq[NP][KK];
             if (PAIRED) {
