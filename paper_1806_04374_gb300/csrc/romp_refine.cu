@@ -254,10 +254,11 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
 
 // Register budget: 5 blocks of 128 threads per SM (<= 102 registers) up to
 // K = 5; for K = 8 the state (Cholesky row, weights, Gram entries of up to 8
-// atoms) spills 1.8 KB a thread at that budget, and 3 blocks (<= 168
-// registers) measured 8% faster on the 21 x 21-patch image workload.
+// atoms) spills 1.8 KB a thread at that budget.  Measured on the 21 x 21-patch
+// image workload: 4 blocks (<= 128 registers, 0.8 KB of spills) 1.9% faster
+// than 3 (<= 168) and 4% faster than 2 (no spills).
 template <int KK, bool PAIRED>
-__global__ void __launch_bounds__(128, KK > 5 ? 3 : 5) romp_refine_kernel(const RefineArgs a) {
+__global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const RefineArgs a) {
   const int H = a.H, J = a.J, R = a.R, M = a.M, HJ = H * J;
   const int *qtab;
   const TwS tw = load_tw(a, qtab);
