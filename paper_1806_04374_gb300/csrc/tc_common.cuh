@@ -180,6 +180,52 @@ struct DF2 {
   df a, b;
 };
 
+// score32 for (m, r) and (m, r + R/2): the even-k and odd-k parts E and O
+// of the FP32 estimate give s(r) = E + O and s(r + R/2) = E - O.
+template <int KK>
+__device__ float2 score32_pair(const float *__restrict__ dm, const float *__restrict__ xp,
+                               const float4 *__restrict__ xg, int M, int J, int H, int R, int m,
+                               int r, int t, const Ls<KK> &S, const TwS &tw) {
+  float ev = 0.0f, od = 0.0f;
+  for (int k = 0; k < H; ++k) {
+    float qr = 0.f, qi = 0.f;
+    const float2 *d2 = reinterpret_cast<const float2 *>(dm) + k * J;
+    const float2 *x2 = reinterpret_cast<const float2 *>(xp) + k * J;
+    for (int j = 0; j < J; ++j) {
+      const float2 dv = __ldg(d2 + j), xv = __ldg(x2 + j);
+      const float dim = k ? dv.y : 0.0f, xim = k ? xv.y : 0.0f;
+      qr = fmaf(dv.x, xv.x, fmaf(dim, xim, qr));
+      qi = fmaf(dv.x, xim, fmaf(-dim, xv.x, qi));
+    }
+    const float term = fmaf(tw.cos32(k, r), qr, -tw.sin32(k, r) * qi);
+    if (k & 1)
+      od = fmaf(2.0f, term, od);
+    else
+      ev = fmaf(k ? 2.0f : 1.0f, term, ev);
+  }
+  float sa = ev + od, sb = ev - od;
+#pragma unroll
+  for (int i = 0; i < KK; ++i) {
+    if (i < t) {
+      int dr = r - S.r[i];
+      if (dr < 0) dr += R;
+      const float4 *h = xg + ((size_t)m * M + S.m[i]) * H;
+      float ge = 0.0f, go = 0.0f;
+      for (int k = 0; k < H; ++k) {
+        const float4 v = __ldg(h + k);
+        const float term = fmaf(tw.cos32(k, dr), v.x, -tw.sin32(k, dr) * v.z);
+        if (k & 1)
+          go = fmaf(2.0f, term, go);
+        else
+          ge = fmaf(k ? 2.0f : 1.0f, term, ge);
+      }
+      sa = fmaf(-S.ahi[i], ge + go, sa);
+      sb = fmaf(-S.ahi[i], ge - go, sb);
+    }
+  }
+  return make_float2(sa, sb);
+}
+
 // score_x for (m, r) and (m, r + R/2), double-float.
 __device__ DF2 score_x_pair(const float *__restrict__ dm, const float *__restrict__ xp, int J,
                             int H, int r, const TwS &tw) {
