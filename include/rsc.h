@@ -240,7 +240,11 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *basis, const float 
  * Copies the patches to the device in chunks, codes them and copies the
  * results back, overlapping the copies of one chunk with the coding of the
  * next on two internal streams.  Blocks until every output is written.
- * Device memory for the chunks is allocated and freed inside the call.
+ * Device memory for two chunks (up to 2^18 patches each) and the two streams
+ * are made on the first call and kept with the dictionary, grown when a call
+ * needs more, and released by rsc_dict_destroy: later calls allocate and
+ * free nothing.  Calls on one dictionary from several host threads run one
+ * at a time.
  */
 int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
                     int32_t *atom, int32_t *angle_idx, float *angle, double *coef,

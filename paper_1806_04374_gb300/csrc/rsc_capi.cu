@@ -64,8 +64,70 @@ void timing_end(const rsc_dict *d, int slot, cudaStream_t st) {
   cudaEventRecord((*log)[slot].b, st);
 }
 
+// Device buffers of rsc_encode_host: two chunks (double-buffered on two
+// streams), grown when a call needs more, kept with the dictionary so that
+// calls allocate and free nothing (cudaFree would also synchronise the device).
+struct HostStage {
+  std::mutex mu;  // one rsc_encode_host at a time per dictionary
+  int64_t chunk = 0;
+  int K = 0, vec = 0;
+  cudaStream_t s[2] = {nullptr, nullptr};
+  struct Buf {
+    float *x = nullptr;
+    int32_t *atom = nullptr, *ang = nullptr;
+    float *angf = nullptr, *rn2 = nullptr;
+    double *coef = nullptr;
+  } b[2];
+  void release() {
+    for (int i = 0; i < 2; ++i) {
+      if (s[i]) cudaStreamSynchronize(s[i]);
+      cudaFree(b[i].x);
+      cudaFree(b[i].atom);
+      cudaFree(b[i].ang);
+      cudaFree(b[i].angf);
+      cudaFree(b[i].coef);
+      cudaFree(b[i].rn2);
+      b[i] = Buf{};
+    }
+    chunk = 0;
+    K = 0;
+  }
+  ~HostStage() {
+    release();
+    for (int i = 0; i < 2; ++i)
+      if (s[i]) cudaStreamDestroy(s[i]);
+  }
+  // Buffers for chunks of `n` patches of K steps and `v` floats each.
+  cudaError_t reserve(int64_t n, int k, int v) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+      if (!s[i]) e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
+    if (e != cudaSuccess || (n <= chunk && k <= K && v == vec)) return e;
+    release();
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      Buf &B = b[i];
+      e = cudaMalloc(&B.x, (size_t)n * v * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc(&B.atom, (size_t)n * k * sizeof(int32_t));
+      if (e == cudaSuccess) e = cudaMalloc(&B.ang, (size_t)n * k * sizeof(int32_t));
+      if (e == cudaSuccess) e = cudaMalloc(&B.angf, (size_t)n * k * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc(&B.coef, (size_t)n * k * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&B.rn2, (size_t)n * sizeof(float));
+    }
+    if (e != cudaSuccess) {
+      release();
+      return e;
+    }
+    chunk = n;
+    K = k;
+    vec = v;
+    return cudaSuccess;
+  }
+};
+std::mutex g_stage_mu;  // creation of a dictionary's HostStage
+
 void free_dict(rsc_dict *d) {
   if (!d) return;
+  delete static_cast<HostStage *>(d->host_stage);
   clear_timing(d);
   delete static_cast<TimingLog *>(d->timing_state);
   cudaFree(d->d);
@@ -623,34 +685,24 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
   if (rc != RSC_OK) return rc;
   const int64_t vec = (int64_t)dict->H * dict->J * 2;
   const int64_t chunk = P < (1 << 18) ? P : (1 << 18);
-  struct Buf {
-    float *x = nullptr;
-    int32_t *atom = nullptr, *ang = nullptr;
-    float *angf = nullptr, *rn2 = nullptr;
-    double *coef = nullptr;
-  } b[2];
-  cudaStream_t s[2] = {nullptr, nullptr};
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-    e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&b[i].x, chunk * vec * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&b[i].atom, chunk * K * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&b[i].ang, chunk * K * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&b[i].angf, chunk * K * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&b[i].coef, chunk * K * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b[i].rn2, chunk * sizeof(float));
+  HostStage *hs = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_stage_mu);
+    if (!dict->host_stage) dict->host_stage = new HostStage();
+    hs = static_cast<HostStage *>(dict->host_stage);
   }
-  rc = RSC_OK;
+  std::lock_guard<std::mutex> lock(hs->mu);
+  cudaError_t e = hs->reserve(chunk, K, (int)vec);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
-    rc = RSC_ERR_OOM;
-  } else if (e != cudaSuccess) {
-    rc = rsc_cuda_fail(e);
+    return RSC_ERR_OOM;
   }
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  rc = RSC_OK;
   for (int64_t lo = 0, ci = 0; rc == RSC_OK && lo < P; lo += chunk, ++ci) {
     const int64_t n = (P - lo) < chunk ? (P - lo) : chunk;
-    Buf &B = b[ci & 1];
-    cudaStream_t st = s[ci & 1];
+    HostStage::Buf &B = hs->b[ci & 1];
+    cudaStream_t st = hs->s[ci & 1];
     e = cudaMemcpyAsync(B.x, x + lo * vec, n * vec * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
       rc = rsc_cuda_fail(e);
@@ -674,17 +726,8 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
     if (e != cudaSuccess) rc = rsc_cuda_fail(e);
   }
   for (int i = 0; i < 2; ++i) {
-    if (s[i]) {
-      cudaError_t se = cudaStreamSynchronize(s[i]);
-      if (se != cudaSuccess && rc == RSC_OK) rc = rsc_cuda_fail(se);
-      cudaStreamDestroy(s[i]);
-    }
-    cudaFree(b[i].x);
-    cudaFree(b[i].atom);
-    cudaFree(b[i].ang);
-    cudaFree(b[i].angf);
-    cudaFree(b[i].coef);
-    cudaFree(b[i].rn2);
+    const cudaError_t se = cudaStreamSynchronize(hs->s[i]);
+    if (se != cudaSuccess && rc == RSC_OK) rc = rsc_cuda_fail(se);
   }
   return rc;
 }

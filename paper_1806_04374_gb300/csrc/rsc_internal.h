@@ -43,6 +43,9 @@ struct rsc_dict {
   CUtensorMap tmap_b;    // TMA map of steered_f16, box 64 x kTcBN (fused kernel)
   CUtensorMap tmap_bs;   // TMA map of steered_f16, box 64 x kTcSN (scoring pass)
   CUtensorMap tmap_bp;   // TMA map of paired_f16, box 64 x kTcSNP (scoring pass)
+  // device buffers and streams of rsc_encode_host (rsc_capi.cu), made on its
+  // first call and kept until rsc_dict_destroy
+  mutable void *host_stage;
 };
 
 // Packed real coordinates of a half spectrum, shared by the tensor-core
