@@ -292,16 +292,28 @@ __global__ void __launch_bounds__(kSThreads, 1)
               for (int u = 0; u < 32; ++u)
                 if (u >= nv) key[u] = -1.0f;
             }
-            float m1 = -1.0f;
+            // the block maximum as the larger of the two 16-column halves'
+            // maxima (two independent three-input max chains)
+            float h0 = -1.0f, h1 = -1.0f;
 #pragma unroll
-            for (int u = 0; u < 32; u += 2) m1 = fmax3(m1, key[u], key[u + 1]);
+            for (int u = 0; u < 16; u += 2) {
+              h0 = fmax3(h0, key[u], key[u + 1]);
+              h1 = fmax3(h1, key[16 + u], key[17 + u]);
+            }
+            const float m1 = fmaxf(h0, h1);
             // kept: the block maximum beats the last kept one and is not below
             // the window under the running best (NaN-safe form)
             if (m1 >= 0.0f && m1 > tv[kTcTop - 1] && !(m1 < tv[0] - win)) {
               const int us = __float_as_int(m1) & 31;
-              float m2 = -1.0f;
+              // second value: the other half's maximum or the second largest
+              // key of the winning half (keys are distinct)
+              const bool w1 = us >= 16;
+              float m2 = w1 ? h0 : h1;
 #pragma unroll
-              for (int u = 0; u < 32; ++u) m2 = fmaxf(m2, key[u] < m1 ? key[u] : -1.0f);
+              for (int u = 0; u < 16; ++u) {
+                const float kv = w1 ? key[16 + u] : key[u];
+                m2 = fmaxf(m2, kv < m1 ? kv : -1.0f);
+              }
               topn_insert(tv, ti, disc, m1, base + us);
               if (m2 >= 0.0f && !(m2 < tv[0] - win)) {
                 // the block's second value may lie in the window too: keep it
