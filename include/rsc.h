@@ -235,6 +235,39 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *basis, const float 
                       double *coef, float *resid_norm2, void *stream);
 
 /*
+ * rsc_reconstruct -- the coded patches back in steerable coordinates:
+ * x_hat_p = sum_i a_i S_{r_i} d_{m_i} (Sec. II-C's sparse code with the
+ * steering of Eq. (Sr)), accumulated in FP64.
+ *   atom, angle_idx, coef : device, P x K, as rsc_encode writes them (steps
+ *            with atom = -1 are skipped); int32 / int32 / double.
+ *   out    : device, P x (kmax+1) x J x 2 floats (half spectra; the Im of
+ *            k = 0 is written as 0), 8-byte aligned, caller-owned.
+ *   Enqueued on `stream`; returns after launch.  RSC_ERR_INVALID for bad
+ *   sizes, null or misaligned pointers, or another device than the
+ *   dictionary's.  For a patch x, |x - x_hat|^2 is the resid_norm2 that
+ *   rsc_encode reports (up to rounding).
+ */
+int rsc_reconstruct(const rsc_dict *dict, int64_t P, int32_t K, const int32_t *atom,
+                    const int32_t *angle_idx, const double *coef, float *out, void *stream);
+
+/*
+ * rsc_synthesize -- steerable coordinates back to pixels: pixels = Phi x_hat
+ * over the basis's circular patch (step 4 of the proposed algorithm,
+ * Sec. II-E: D = Phi D_hat returns a learned dictionary to the patch domain;
+ * applied to rsc_reconstruct's output it gives the reconstructed patches).
+ *   coef   : device, P x (kmax+1) x J x 2 floats (half spectra, the layout
+ *            rsc_project writes).
+ *   pixels : device, P x npix floats (rsc_basis_info's npix, the pixels with
+ *            distance <= N/2 from the centre in row-major order), caller-owned.
+ *   FP32 accumulation over the n packed coordinates.  Enqueued on `stream`;
+ *   returns after launch.  rsc_project after rsc_synthesize gives back the
+ *   coordinates' part in the span the projection keeps (the singular
+ *   directions above its cutoff).
+ */
+int rsc_synthesize(const rsc_basis *basis, const float *coef, int64_t P, float *pixels,
+                   void *stream);
+
+/*
  * rsc_encode_host -- rsc_encode on HOST buffers (same shapes and meaning as
  * above, all pointers host memory; pinned memory gives the fastest copies).
  * Copies the patches to the device in chunks, codes them and copies the

@@ -13,7 +13,9 @@ indicators (Eq. (basis-cont)):
      (the paper's (Phi^* Phi)^{-1} Phi^* of step 2 of the proposed
      algorithm, generalised because Phi^* Phi is singular when there are
      more basis vectors than pixels);
-  4. x_hat = Phi^+ x for every stride-1 window of an image.
+  4. x_hat = Phi^+ x for every stride-1 window of an image; the way back,
+     pixels = Phi x_hat, is synthesize (the proposed algorithm's step 4,
+     D = Phi D_hat).
 Readings: pixel (row, col) sits at x = col - c, y = c - row (c = (N-1)/2),
 phi = atan2(y, x); e^{i k phi} is taken as 0 at the centre pixel for k != 0;
 ring centres r_j = j * (N - 1) / (2 J), width 1 pixel; pseudo-inverse cutoff
@@ -94,6 +96,17 @@ def unpack_half(v, J: int, kmax: int):
     rest = v[..., J:].reshape(v.shape[:-1] + (kmax, J, 2)) / np.sqrt(2.0)
     out[..., 1:, :, :] = rest
     return out
+
+
+def synthesize(c, N: int, J: int, kmax: int, **kw):
+    """Pixels Phi x_hat of half spectra c [P, kmax+1, J, 2] over the circular
+    patch (step 4 of the proposed algorithm, Sec. II-E: D = Phi D_hat):
+    [P, npix], pixels in the row-major order of grid()."""
+    Phi, _ = synthesis(N, J, kmax, **kw)
+    X = real_synthesis(Phi, kmax, J)
+    c = np.asarray(c, np.float64)
+    v = np.concatenate([c[:, 0, :, 0], np.sqrt(2.0) * c[:, 1:].reshape(c.shape[0], -1)], 1)
+    return v @ X.T
 
 
 def project(image, N: int, J: int, kmax: int, **kw):

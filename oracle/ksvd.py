@@ -58,6 +58,21 @@ def steer(c, theta):
     return out
 
 
+def reconstruct(d, R, atom, angle, coef):
+    """The coded patches in steerable coordinates, sum_i a_i S_{theta_i} d_{m_i}
+    (Sec. II-C's sparse code, steering of Eq. (Sr), theta = 2 pi r / R); steps
+    with atom -1 contribute nothing.  Returns half spectra [P, H, J, 2]."""
+    d = np.asarray(d, np.float64)
+    atom, angle, coef = np.asarray(atom), np.asarray(angle), np.asarray(coef, np.float64)
+    P, K = atom.shape
+    out = np.zeros((P,) + d.shape[1:])
+    for p in range(P):
+        for i in range(K):
+            if atom[p, i] >= 0:
+                out[p] += coef[p, i] * steer(d[atom[p, i]], 2 * np.pi * angle[p, i] / R)
+    return out
+
+
 def augmented(d, R):
     """Packed columns S_{2 pi r / R} d_m, column index m*R + r."""
     M = d.shape[0]

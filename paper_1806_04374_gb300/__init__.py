@@ -32,7 +32,8 @@ EXPORTS = (
     "rsc_dict_check", "rsc_dict_fallback_count", "rsc_dict_set_timing", "rsc_dict_timing",
     "rsc_status_string", "rsc_last_cuda_error", "rsc_version", "rsc_encode_noalloc",
     "rsc_ksvd_update", "rsc_basis_create", "rsc_basis_destroy", "rsc_basis_info", "rsc_project",
-    "rsc_encode_images", "rsc_ksvd_accumulate", "rsc_ksvd_finish",
+    "rsc_encode_images", "rsc_ksvd_accumulate", "rsc_ksvd_finish", "rsc_reconstruct",
+    "rsc_synthesize",
 )
 
 
@@ -76,6 +77,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_basis_destroy.argtypes = [vp]
     lib.rsc_basis_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.rsc_project.argtypes = [vp, vp, i32, i32, vp, vp]
+    lib.rsc_reconstruct.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
+    lib.rsc_synthesize.argtypes = [vp, vp, i64, vp, vp]
     lib.rsc_encode_images.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(i32),
                                       ctypes.POINTER(i32), i32, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_dict_check.argtypes = [vp, vp]
@@ -374,6 +377,43 @@ def project(basis: Basis, image, stream=None):
                                     ctypes.c_void_p(_stream_handle(stream)))
     if st != RSC_OK:
         raise RscError(st, "rsc_project")
+    return out
+
+
+def reconstruct(dic: Dictionary, codes: dict, stream=None):
+    """rsc_reconstruct: sum_i a_i S_{r_i} d_{m_i} of each patch's code (CUDA
+    tensors atom, angle_idx [P, K] int32, coef [P, K] float64) -> half
+    spectra [P, kmax+1, J, 2] float32."""
+    import torch
+    atom = codes["atom"].contiguous()
+    ang = codes["angle_idx"].contiguous()
+    coef = codes["coef"].contiguous()
+    P, K = atom.shape
+    out = torch.empty((P, dic.kmax + 1, dic.J, 2), dtype=torch.float32, device=atom.device)
+    st = load_library().rsc_reconstruct(ctypes.c_void_p(dic.handle), P, K,
+                                        ctypes.c_void_p(atom.data_ptr()),
+                                        ctypes.c_void_p(ang.data_ptr()),
+                                        ctypes.c_void_p(coef.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(_stream_handle(stream)))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_reconstruct")
+    return out
+
+
+def synthesize(basis: Basis, coef, stream=None):
+    """rsc_synthesize: pixels Phi x_hat of the circular patch for CUDA half
+    spectra [P, kmax+1, J, 2] float32 -> [P, npix] float32 (the masked
+    pixels in row-major order)."""
+    import torch
+    coef = coef.contiguous()
+    P = coef.shape[0]
+    out = torch.empty((P, basis.npix), dtype=torch.float32, device=coef.device)
+    st = load_library().rsc_synthesize(ctypes.c_void_p(basis.handle), ctypes.c_void_p(coef.data_ptr()),
+                                       P, ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(_stream_handle(stream)))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_synthesize")
     return out
 
 

@@ -52,6 +52,7 @@ struct rsc_basis {
   int KPw, sbw;
   CUtensorMap tmW;
   int *err;      // device error word of the projection kernels (bounded waits)
+  float *Xs;     // device [n][npix]: real synthesis matrix (packed columns), FP32
 };
 
 namespace {
@@ -909,6 +910,10 @@ int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, doub
   if (e == cudaSuccess && tc_ok) e = cudaMalloc(&b->Bt, Bt.size() * sizeof(uint16_t));
   if (e == cudaSuccess && tc_ok)
     e = cudaMemcpy(b->Bt, Bt.data(), Bt.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  std::vector<float> Xf(X.begin(), X.end());  // [n][npix] (column-major X)
+  if (e == cudaSuccess) e = cudaMalloc(&b->Xs, Xf.size() * sizeof(float));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->Xs, Xf.data(), Xf.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && tcw_ok) e = cudaMalloc(&b->Bw, Bw.size() * sizeof(uint16_t));
   if (e == cudaSuccess && tcw_ok)
     e = cudaMemcpy(b->Bw, Bw.data(), Bw.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
@@ -920,6 +925,7 @@ int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, doub
     cudaFree(b->err);
     cudaFree(b->Bt);
     cudaFree(b->Bw);
+    cudaFree(b->Xs);
     delete b;
     if (rc != RSC_OK) return rc;
     if (e == cudaErrorMemoryAllocation) {
@@ -939,6 +945,7 @@ int rsc_basis_destroy(rsc_basis *b) {
   cudaFree(b->err);
   cudaFree(b->Bt);
   cudaFree(b->Bw);
+  cudaFree(b->Xs);
   delete b;
   return RSC_OK;
 }
@@ -1023,3 +1030,9 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *b, const float *con
 }
 
 }  // extern "C"
+
+int rsc_basis_internals(const rsc_basis *b, rsc_basis_view *v) {
+  if (!b || !v) return RSC_ERR_INVALID;
+  *v = rsc_basis_view{b->device, b->npix, b->n, b->J, b->nout, b->Xs};
+  return RSC_OK;
+}

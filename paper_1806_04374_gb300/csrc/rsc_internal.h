@@ -149,6 +149,13 @@ int rsc_launch_tc(const TcArgs &a, const CUtensorMap &tmap, cudaStream_t stream)
 // outside the matrix.
 int rsc_encode_rows_map(CUtensorMap *map, void *base, size_t rows, int box_rows, int row_len);
 
+// What other translation units need of a basis handle (basis.cu owns it).
+struct rsc_basis_view {
+  int device, npix, n, J, nout;
+  const float *X;  // device [n][npix]: real synthesis matrix, packed column order
+};
+int rsc_basis_internals(const rsc_basis *basis, rsc_basis_view *view);
+
 // Candidates (block maxima and in-window second values) kept per patch and
 // greedy step by the tensor-core scoring: kTcTop per list; the split scoring
 // pass keeps one list per half of the accumulator columns, kTcCand in all.
