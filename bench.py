@@ -295,6 +295,63 @@ def measure_projection(rsc, torch, dev, stream, reps: int = 5) -> dict:
             "config": "one 2048x2048 image, N=11 (97 px), J=6, kmax=8, stride 1"}
 
 
+def measure_roundtrip(rsc, torch, dev, stream, dic, codes, reps: int = 5) -> dict:
+    """The way back on the benchmark's own codes (10^6 patches, M = 64,
+    R = 64, K = 5): rsc_reconstruct (sum_i a_i S_i d_i, FP64 accumulation)
+    and rsc_synthesize (Phi x_hat on the 11 x 11 basis, 97 pixels), patches/s
+    of each from CUDA events on the launching stream."""
+    N, J, kmax = 11, 6, 8
+    basis = rsc.Basis(N, J, kmax)
+    P = int(codes["atom"].shape[0])
+    with torch.cuda.stream(stream):
+        rec = rsc.reconstruct(dic, codes, stream=stream)
+        pix = rsc.synthesize(basis, rec, stream=stream)
+        del pix
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            rec = rsc.reconstruct(dic, codes, stream=stream)
+        ev[1].record(stream)
+        for _ in range(reps):
+            pix = rsc.synthesize(basis, rec, stream=stream)
+            del pix
+        ev[2].record(stream)
+        stream.synchronize()
+    ms_rec = ev[0].elapsed_time(ev[1]) / reps
+    ms_syn = ev[1].elapsed_time(ev[2]) / reps
+    basis.close()
+    return {"patches": P, "reconstruct_ms": ms_rec, "reconstruct_patches_per_s": P / (ms_rec / 1e3),
+            "synthesize_ms": ms_syn, "synthesize_patches_per_s": P / (ms_syn / 1e3),
+            "config": "omp_1m codes (M=64, R=64, K=5); synthesis on the 11x11 basis (97 px, n=102)"}
+
+
+def measure_classify(rsc, torch, dev) -> dict:
+    """rsc_classify_images, the coding stage of the paper's texture
+    classifier: 8 line-texture images of 256 x 256 (484 k windows of 11 x 11)
+    coded with each of C = 4 dictionaries (M = 64, R = 64, K = 5, FP16 path),
+    labelled by least coding error and counted per image.  Host clock around
+    the blocking call after a warm-up call."""
+    N, J, kmax, M, R, K, C = 11, 6, 8, 64, 64, 5, 4
+    imgs = [torch.from_numpy(synth.make_line_image(256, 256, 0.01, 20180630 + i)).to(dev)
+            for i in range(8)]
+    basis = rsc.Basis(N, J, kmax)
+    dics = [rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180640 + c)).to(dev), R)
+            for c in range(C)]
+    labels, hist = rsc.classify_images(dics, basis, imgs[:1], K, "f16")
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    labels, hist = rsc.classify_images(dics, basis, imgs, K, "f16")
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    P = int(labels.shape[0])
+    for dd in dics:
+        dd.close()
+    basis.close()
+    return {"windows": P, "dictionaries": C, "s": dt, "windows_per_s": P / dt,
+            "patch_codings_per_s": P * C / dt,
+            "config": "8 images 256x256, N=11, J=6, kmax=8; C=4 dictionaries M=64, R=64, K=5; f16"}
+
+
 def measure_images_c2(rsc, torch, dev) -> dict:
     """rsc_encode_images at the image workload's coder sizes: 21 x 21 patches
     (349 px), J = 10, kmax = 12 (n = 250: tensor-core rows of 256 slots),
@@ -732,6 +789,8 @@ def main():
             line["projection"] = measure_projection(rsc, torch, dev, stream)
             line["rksvd"] = measure_rksvd(rsc, torch, dev)
             line["images_c2_sizes"] = measure_images_c2(rsc, torch, dev)
+            line["roundtrip"] = measure_roundtrip(rsc, torch, dev, stream, dic, out)
+            line["classify"] = measure_classify(rsc, torch, dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(d, x, wl)
         print(json.dumps(line))

@@ -235,6 +235,27 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *basis, const float 
                       double *coef, float *resid_norm2, void *stream);
 
 /*
+ * rsc_classify_images -- the coding stage of the paper's texture classifier
+ * (Sec. III-B): every stride-1 window of each image is projected once and
+ * coded with each of C dictionaries (one learned per class); its label is
+ * the dictionary that codes it with the least squared error (ties: the
+ * smaller index), and the labels are counted per image.
+ *   dicts  : C handles whose J and kmax equal the basis's (M and R may
+ *            differ); 1 <= C <= 4096.
+ *   images, h, w, n_images, K, prec : as rsc_encode_images.
+ *   labels : device, P int32 (P = the windows of all images, image-major,
+ *            row-major per image), or NULL when only the counts are wanted.
+ *   hist   : device, n_images x C int32: row i counts the labels of image
+ *            i's windows (zero for images smaller than a window).
+ *   Device scratch: about P x ((kmax+1) J 8 + K 16 + 12) bytes from the
+ *   stream-ordered allocator.  Synchronises `stream` before returning.
+ */
+int rsc_classify_images(const rsc_dict *const *dicts, int32_t C, const rsc_basis *basis,
+                        const float *const *images, const int32_t *h, const int32_t *w,
+                        int32_t n_images, int32_t K, int32_t prec, int32_t *labels,
+                        int32_t *hist, void *stream);
+
+/*
  * rsc_reconstruct -- the coded patches back in steerable coordinates:
  * x_hat_p = sum_i a_i S_{r_i} d_{m_i} (Sec. II-C's sparse code with the
  * steering of Eq. (Sr)), accumulated in FP64.

@@ -124,6 +124,25 @@ def romp(x, d, R: int, K: int, nthreads: int = 0, forced_atom=None, forced_angle
             "pick_score": pick, "best_score": best}
 
 
+def classify(xs, ds, Rs, K: int, nthreads: int = 0):
+    """The coding stage of the paper's texture classifier (Sec. III-B): every
+    patch coded with each dictionary (``romp``), labelled with the index of
+    the dictionary of least squared coding error (ties: the smaller index).
+    ``xs`` is a list of per-image patch arrays [P_i, kmax+1, J, 2]; returns
+    (labels per image, rn2 [C, P_total], histogram [n_images, C])."""
+    x = np.concatenate(xs) if xs else np.zeros((0,))
+    C = len(ds)
+    rn2 = np.stack([romp(x, ds[c], Rs[c], K, nthreads)["rn2"] for c in range(C)])
+    label = np.argmin(rn2, 0)  # first minimum: the smaller index on ties
+    hist, labels, lo = np.zeros((len(xs), C), np.int64), [], 0
+    for i, xi in enumerate(xs):
+        li = label[lo:lo + xi.shape[0]]
+        labels.append(li)
+        hist[i] = np.bincount(li, minlength=C)
+        lo += xi.shape[0]
+    return labels, rn2, hist
+
+
 def scores(x1, d, R: int):
     """Exact scores <S_r d_m, x> of one patch, shape (M, R)."""
     lib = _load()

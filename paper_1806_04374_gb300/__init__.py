@@ -33,7 +33,7 @@ EXPORTS = (
     "rsc_status_string", "rsc_last_cuda_error", "rsc_version", "rsc_encode_noalloc",
     "rsc_ksvd_update", "rsc_basis_create", "rsc_basis_destroy", "rsc_basis_info", "rsc_project",
     "rsc_encode_images", "rsc_ksvd_accumulate", "rsc_ksvd_finish", "rsc_reconstruct",
-    "rsc_synthesize",
+    "rsc_synthesize", "rsc_classify_images",
 )
 
 
@@ -79,6 +79,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_project.argtypes = [vp, vp, i32, i32, vp, vp]
     lib.rsc_reconstruct.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
     lib.rsc_synthesize.argtypes = [vp, vp, i64, vp, vp]
+    lib.rsc_classify_images.argtypes = [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(vp),
+                                        ctypes.POINTER(i32), ctypes.POINTER(i32), i32, i32, i32,
+                                        vp, vp, vp]
     lib.rsc_encode_images.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(i32),
                                       ctypes.POINTER(i32), i32, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.rsc_dict_check.argtypes = [vp, vp]
@@ -415,6 +418,32 @@ def synthesize(basis: Basis, coef, stream=None):
     if st != RSC_OK:
         raise RscError(st, "rsc_synthesize")
     return out
+
+
+def classify_images(dicts, basis: Basis, images, K: int, precision: str = "f16", stream=None):
+    """rsc_classify_images: windows of CUDA float32 images coded with each
+    Dictionary in `dicts`; returns (labels [P] int32, hist [n_images, C]
+    int32), the label being the index of the dictionary with the least
+    squared coding error."""
+    import torch
+    images = [im.contiguous() for im in images]
+    N = basis.N
+    P = sum(max(im.shape[0] - N + 1, 0) * max(im.shape[1] - N + 1, 0) for im in images)
+    dev = images[0].device if images else torch.device("cuda")
+    C, n = len(dicts), len(images)
+    labels = torch.empty((max(P, 1),), dtype=torch.int32, device=dev)
+    hist = torch.empty((max(n, 1), C), dtype=torch.int32, device=dev)
+    hs_ = (ctypes.c_void_p * C)(*[dd.handle for dd in dicts])
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[im.data_ptr() for im in images])
+    hs = (ctypes.c_int32 * max(n, 1))(*[im.shape[0] for im in images])
+    ws = (ctypes.c_int32 * max(n, 1))(*[im.shape[1] for im in images])
+    st = load_library().rsc_classify_images(
+        hs_, C, ctypes.c_void_p(basis.handle), ptrs, hs, ws, n, K, PRECISIONS[precision],
+        ctypes.c_void_p(labels.data_ptr()), ctypes.c_void_p(hist.data_ptr()),
+        ctypes.c_void_p(_stream_handle(stream)))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_classify_images")
+    return labels[:P], hist[:n]
 
 
 def encode_images(dic: Dictionary, basis: Basis, images, K: int, precision: str = "fp32",

@@ -684,6 +684,37 @@ __global__ void __launch_bounds__(kPwThreads, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, kPwNP);
 }
 
+// Multi-dictionary labelling (the paper's classifier, Sec. III-B): after
+// dictionary c has coded every patch, a patch whose squared coding error is
+// below the best so far takes label c (strict: ties keep the smaller index).
+__global__ void label_update_kernel(int64_t P, int c, const float *__restrict__ rn2,
+                                    float *__restrict__ best, int32_t *__restrict__ label) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float v = rn2[p];
+    if (c == 0 || v < best[p]) {
+      best[p] = v;
+      label[p] = c;
+    }
+  }
+}
+
+// One block per coded image: its patches' labels counted in shared memory,
+// then written as the image's row of the C-bin histogram.
+__global__ void label_hist_kernel(const ImageItem *__restrict__ items, const int *__restrict__ orig,
+                                  int N, const int32_t *__restrict__ label, int C,
+                                  int32_t *__restrict__ hist) {
+  extern __shared__ int counts[];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) counts[c] = 0;
+  __syncthreads();
+  const ImageItem it = items[blockIdx.x];
+  const int64_t n = (int64_t)(it.h - N + 1) * (it.w - N + 1);
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) atomicAdd(&counts[label[it.first + q]], 1);
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x)
+    hist[(int64_t)orig[blockIdx.x] * C + c] = counts[c];
+}
+
 // Reads and clears the basis's device error word (after a synchronisation).
 int take_error(const rsc_basis *b) {
   int v = 0;
@@ -1023,6 +1054,94 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *b, const float *con
     rc = rsc_encode(dict, xc, P, K, prec, atom, angle_idx, angle, coef, resid_norm2, stream);
   cudaFreeAsync(scratch, st);
   // the host work list must outlive its async copy
+  e = cudaStreamSynchronize(st);
+  if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
+  if (rc == RSC_OK) rc = take_error(b);
+  return rc;
+}
+
+int rsc_classify_images(const rsc_dict *const *dicts, int32_t C, const rsc_basis *b,
+                        const float *const *images, const int32_t *h, const int32_t *w,
+                        int32_t n_images, int32_t K, int32_t prec, int32_t *labels,
+                        int32_t *hist, void *stream) {
+  if (!dicts || C < 1 || C > 4096 || !b || n_images < 0 || !hist ||
+      (n_images > 0 && (!images || !h || !w)) || K < 1 || K > kMaxK)
+    return RSC_ERR_INVALID;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  if (dev != b->device) return RSC_ERR_INVALID;
+  for (int c = 0; c < C; ++c)
+    if (!dicts[c] || dicts[c]->J != b->J || dicts[c]->kmax != b->kmax || dicts[c]->device != dev)
+      return RSC_ERR_INVALID;
+  std::vector<ImageItem> items;
+  std::vector<int> orig;
+  int64_t P = 0;
+  for (int i = 0; i < n_images; ++i) {
+    if (h[i] < 0 || w[i] < 0) return RSC_ERR_INVALID;
+    if (h[i] < b->N || w[i] < b->N) continue;
+    if (!images[i]) return RSC_ERR_INVALID;
+    items.push_back(ImageItem{images[i], h[i], w[i], P});
+    orig.push_back(i);
+    P += (int64_t)(h[i] - b->N + 1) * (w[i] - b->N + 1);
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  e = cudaMemsetAsync(hist, 0, (size_t)n_images * C * sizeof(int32_t), st);
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  if (P == 0) return RSC_OK;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t bI = al(items.size() * sizeof(ImageItem)), bO = al(orig.size() * sizeof(int));
+  const size_t bX = al((size_t)P * b->nout * 4), bA = al((size_t)P * K * 4),
+               bC = al((size_t)P * K * 8), bP = al((size_t)P * 4);
+  unsigned char *scratch = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bI + bO + bX + 2 * bA + bC + 3 * bP, st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return RSC_ERR_OOM;
+  }
+  if (e != cudaSuccess) return rsc_cuda_fail(e);
+  unsigned char *q = scratch;
+  auto take = [&](size_t n) {
+    unsigned char *r = q;
+    q += n;
+    return r;
+  };
+  ImageItem *d_items = reinterpret_cast<ImageItem *>(take(bI));
+  int *d_orig = reinterpret_cast<int *>(take(bO));
+  float *xc = reinterpret_cast<float *>(take(bX));
+  int32_t *s_atom = reinterpret_cast<int32_t *>(take(bA));
+  int32_t *s_ang = reinterpret_cast<int32_t *>(take(bA));
+  double *s_coef = reinterpret_cast<double *>(take(bC));
+  float *s_rn2 = reinterpret_cast<float *>(take(bP));
+  float *s_best = reinterpret_cast<float *>(take(bP));
+  int32_t *s_label = reinterpret_cast<int32_t *>(take(bP));
+  int32_t *lab = labels ? labels : s_label;
+  int rc = RSC_OK;
+  e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(ImageItem),
+                      cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_orig, orig.data(), orig.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+  if (rc == RSC_OK) rc = launch_project(b, d_items, (int)items.size(), P, xc, st);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<int64_t>((P + 255) / 256, (int64_t)nsm * 8);
+  for (int c = 0; c < C && rc == RSC_OK; ++c) {
+    rc = rsc_encode(dicts[c], xc, P, K, prec, s_atom, s_ang, nullptr, s_coef, s_rn2, stream);
+    if (rc == RSC_OK) {
+      label_update_kernel<<<grid, 256, 0, st>>>(P, c, s_rn2, s_best, lab);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+    }
+  }
+  if (rc == RSC_OK) {
+    label_hist_kernel<<<(unsigned)items.size(), 256, (size_t)C * sizeof(int), st>>>(
+        d_items, d_orig, b->N, lab, C, hist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+  }
+  cudaFreeAsync(scratch, st);
+  // the host work lists must outlive their async copies
   e = cudaStreamSynchronize(st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
   if (rc == RSC_OK) rc = take_error(b);
