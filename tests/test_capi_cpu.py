@@ -44,3 +44,24 @@ def test_host_only_calls(lib):
     assert lib.rsc_dict_create(None, rsc.rsc_dims(0, 6, 8, 8), None,
                                ctypes.byref(h)) == rsc.RSC_ERR_INVALID
     assert rsc.rsc_encode_host(0, 0, 10, 3, 0, 0, 0, 0, 0, 0) == rsc.RSC_ERR_INVALID
+
+
+def test_way_back_and_classifier_reject_bad_arguments(lib):
+    """rsc_reconstruct, rsc_synthesize and rsc_classify_images validate their
+    arguments before any CUDA call (no GPU needed)."""
+    import paper_1806_04374_gb300 as rsc
+    inv = rsc.RSC_ERR_INVALID
+    vp = ctypes.c_void_p
+    # null dictionary / basis handles, bad sizes
+    assert lib.rsc_reconstruct(None, 10, 3, None, None, None, None, None) == inv
+    assert lib.rsc_reconstruct(None, -1, 3, None, None, None, None, None) == inv
+    assert lib.rsc_synthesize(None, None, 10, None, None) == inv
+    assert lib.rsc_synthesize(None, None, -1, None, None) == inv
+    # classifier: no dictionaries, C = 0, no histogram, bad K
+    one = (vp * 1)(None)
+    assert lib.rsc_classify_images(None, 1, None, None, None, None, 0, 3, 0, None, None,
+                                   None) == inv
+    assert lib.rsc_classify_images(one, 0, None, None, None, None, 0, 3, 0, None, None,
+                                   None) == inv
+    assert lib.rsc_classify_images(one, 1, None, None, None, None, 0, 0, 0, None, None,
+                                   None) == inv
