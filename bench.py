@@ -164,6 +164,10 @@ class ClockSampler:
 
 
 SCORE_SOURCES = ("romp_score.cu", "tc_ptx.cuh", "tc_common.cuh", "rsc_internal.h")
+REFINE_SOURCES = ("romp_refine.cu", "tc_common.cuh", "rsc_internal.h")
+# bytes a patch must move in one init or refine launch of the FP16 path: read
+# its coefficients x (kmax+1) x J x 2 floats, write its fp16 residual row of
+# L slots (the per-patch state in between is this design's, not the method's)
 
 
 def source_digest(names=SCORE_SOURCES) -> str:
@@ -176,13 +180,14 @@ def source_digest(names=SCORE_SOURCES) -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(P: float):
-    """DRAM bytes per launch of the scoring kernel for a launch over P patches, from the
+def recorded_traffic(P: float, profile: str = "romp_score_kernel_omp_1m.md",
+                     names=SCORE_SOURCES):
+    """DRAM bytes per launch of a kernel for a launch over P patches, from its
     committed ncu summary (dram__bytes_read.sum + dram__bytes_write.sum of one
     capture, per patch, scaled to P: the kernel's traffic is linear in the
     patches it reads and writes), or None when the kernel's sources changed
     since the capture."""
-    path = os.path.join(ROOT, "profiles", "romp_score_kernel_omp_1m.md")
+    path = os.path.join(ROOT, "profiles", profile)
     try:
         with open(path) as f:
             text = f.read()
@@ -193,7 +198,7 @@ def recorded_traffic(P: float):
         for key in ("dram_bytes_per_patch:", "source_sha1:"):
             if line.strip().startswith(key):
                 vals[key] = line.split(":", 1)[1].strip().strip("`")
-    if vals.get("source_sha1:") != source_digest():
+    if vals.get("source_sha1:") != source_digest(names):
         return None
     try:
         return float(vals["dram_bytes_per_patch:"]) * P
@@ -776,6 +781,24 @@ def main():
             "note": "same kernel, its launches timed with the two halves of the patches run one "
                     "after the other on one stream (the headline run overlaps them)"}
         if args.precision == "f16":
+            # the other half of the path: init + refine launches (one step each),
+            # timed alone in the serialised run (one group: P patches a launch)
+            n_ref = max(iso_run["kernel_launches"][2], 1)
+            ref_s = iso_run["kernel_ms"][2] / n_ref / 1e3
+            row_len = 112 if 2 * wl.J * wl.kmax + wl.J <= 112 else 256
+            ref_algo = (wl.kmax + 1) * wl.J * 2 * 4 + row_len * 2
+            hbm = peaks.get("hbm_gbs") or 6800.0
+            line["roofline_refine"] = {
+                "kernel": "romp_refine_kernel (with romp_init_kernel)", "bound": "hbm",
+                "achieved": ref_algo * P / ref_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": ref_algo * P / ref_s / 1e9 / hbm,
+                "traffic": recorded_traffic(P, "romp_refine_kernel_omp_1m.md", REFINE_SOURCES),
+                "bytes_per_launch": ref_algo * P, "bytes_per_patch": ref_algo,
+                "kernel_ms": ref_s * 1e3,
+                "peak_note": ("measured copy bandwidth" if peaks.get("hbm_gbs")
+                              else "fallback 6.8 TB/s"),
+                "note": "algorithmic bytes of a launch: read x, write the fp16 residual row; "
+                        "latency-bound (one thread per patch), far below the HBM bound"}
             mf = mma_flops_per_patch(wl)
             mtf = mf * P * args.steps / n_launch / launch_s / 1e12
             line["mma_executed"] = {"flops_per_patch": mf, "tflops": mtf,
