@@ -56,3 +56,20 @@ def test_classify_matches_oracle(rsc, precision):
     for dd in dics:
         dd.close()
     b.close()
+
+
+def test_classify_no_windows(rsc):
+    """Every image smaller than a window: no labels, an all-zero histogram."""
+    import torch
+    N, J, kmax = 11, 6, 8
+    b = rsc.Basis(N, J, kmax)
+    dics = [rsc.Dictionary(torch.from_numpy(synth.make_dictionary(6, J, kmax, 80 + c)).cuda(), 8)
+            for c in range(2)]
+    imgs = [torch.ones((5, 40), device="cuda"), torch.ones((10, 10), device="cuda")]
+    labels, hist = rsc.classify_images(dics, b, imgs, 3, "f16")
+    torch.cuda.synchronize()
+    assert labels.numel() == 0
+    assert hist.shape == (2, 2) and int(hist.abs().sum()) == 0
+    for dd in dics:
+        dd.close()
+    b.close()
