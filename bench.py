@@ -171,12 +171,18 @@ REFINE_SOURCES = ("romp_refine.cu", "tc_common.cuh", "rsc_internal.h")
 
 
 def source_digest(names=SCORE_SOURCES) -> str:
-    """sha1 over the CUDA sources a kernel is compiled from."""
+    """sha1 over the code of the CUDA sources a kernel is compiled from, with
+    comments, trailing blanks and empty lines removed (a comment edit does not
+    change the kernel, so it does not void a capture)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for nm in names:
-        with open(os.path.join(ROOT, "paper_1806_04374_gb300", "csrc", nm), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1806_04374_gb300", "csrc", nm), encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()
 
 

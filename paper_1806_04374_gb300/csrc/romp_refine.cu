@@ -7,13 +7,16 @@
 // of two chosen from a bound on their norm (rsc_internal.h), so that scores
 // come back as 2^(16 - e) times their true value.  romp_refine_kernel then,
 // after every scoring pass (romp_score.cu):
-//   * certifies the candidate list: E bounds the fp16 error of a score
-//     (rounding of both operands, accumulation, and the FP32 residual's own
-//     error); every row with |score| >= s1 - 2E is in the list unless the
-//     largest value left out (disc) is >= s1 - 2E, in which case the patch is
-//     handed to the FP32 path;
-//   * re-scores every candidate in the window exactly in double-float as
-//     <A_c, x> - sum_i a_i <A_c, A_i> (ties: smallest m*R + r);
+//   * certifies the two candidate lists (one per column half of the scoring
+//     pass): E bounds the fp16 error of a score (rounding of both operands,
+//     accumulation, and the FP32 residual's own error); every row with
+//     |score| >= s1 - 2E is in a list unless a list's largest value left out
+//     (disc) is >= s1 - 2E, in which case the patch is handed to the FP32
+//     path;
+//   * re-scores the candidates in the window exactly in double-float as
+//     <A_c, x> - sum_i a_i <A_c, A_i> (ties: smallest m*R + r): the one with
+//     the largest approximate value first, the others (K <= 5) only when
+//     their FP32 score plus its error bound reaches the exact best;
 //   * adds the Cholesky row of the winner (Gram entries and right-hand side
 //     in double-float, factor and solve in FP64) and writes the new residual.
 // Per-patch state lives in HBM as structure-of-arrays (coalesced over
