@@ -61,15 +61,23 @@ def test_two_atoms_exact_codes_recovered():
         assert abs(abs(ksvd.pack(d_new[m]) @ v) / np.linalg.norm(v) - 1.0) < 1e-12
 
 
-def _direct_columns(x, d, R, atom, angle, coef, m):
+def _direct_columns(x, d, R, atom, angle, coef, m, rule="largest"):
     """S_{-r0}(x - sum of a_i S_{r_i} d_{m_i} over the steps whose (atom,
-    angle) is not (m, r0)) for the patches using m."""
+    angle) is not (m, r0)) for the patches using m.  r0 is the occurrence of m
+    with the largest |weight|, ties to the earliest (rule "largest", the
+    reading of Sec. II-C's arbitrary choice), or, to show that the pins tell
+    the readings apart, the first ("first") or last ("last") occurrence."""
     cols = []
     for p in range(x.shape[0]):
         occ = [i for i in range(atom.shape[1]) if atom[p, i] == m]
         if not occ:
             continue
-        i0 = max(occ, key=lambda i: (abs(coef[p, i]), -i))
+        if rule == "first":
+            i0 = occ[0]
+        elif rule == "last":
+            i0 = occ[-1]
+        else:
+            i0 = max(occ, key=lambda i: (abs(coef[p, i]), -i))
         r0 = angle[p, i0]
         res = x[p].astype(np.float64).copy()
         for i in range(atom.shape[1]):
@@ -125,3 +133,58 @@ def test_repeated_atom_uses_largest_weight_and_unused_reset():
         errs.append(np.sum((X[p] - Aug @ b) ** 2))
     p_star = int(np.argmax(errs))
     assert np.allclose(ksvd.pack(d_new[2]), X[p_star] / np.linalg.norm(X[p_star]))
+    # the oracle's atom 0 is the leading singular direction of exactly these
+    # columns (sign reading applied), and not that of the columns a "first
+    # occurrence" reading would give
+    assert np.allclose(ksvd.pack(d_new[0]), _leading(Y), atol=1e-12)
+    Y_first = _direct_columns(x, d, R, atom, angle, coef, 0, rule="first")
+    assert not np.allclose(Y_first[:, 0], Y[:, 0], atol=1e-3)
+    assert np.abs(_leading(Y_first) - ksvd.pack(d_new[0])).max() > 1e-3
+
+
+def _leading(Y):
+    """Leading eigenvector of Y Y^T with its largest-magnitude entry positive."""
+    _, V = np.linalg.eigh(Y @ Y.T)
+    u = V[:, -1]
+    return -u if u[np.abs(u).argmax()] < 0 else u
+
+
+def _twin_case(first_is_larger):
+    """Two patches that use atom 0 twice at different angles, with inexact
+    codes (the residual is not aligned with the atom), so the angle r0 that
+    aligns a patch's column decides the updated atom."""
+    R = 16
+    d = synth.make_dictionary(2, J, KMAX, 41).astype(np.float64)
+    rng = np.random.default_rng(4)
+    P = 5
+    x = rng.standard_normal((P, H, J, 2))
+    x[:, 0, :, 1] = 0
+    big, small = -1.3, 0.4
+    w = [big, small] if first_is_larger else [small, big]
+    atom = np.array([[0, 0], [0, 0], [0, 1], [1, -1], [0, -1]])
+    angle = np.array([[3, 11], [14, 6], [9, 2], [5, -1], [0, -1]])
+    coef = np.array([w, w[::-1], [0.7, 0.2], [0.9, 0.0], [-0.6, 0.0]])
+    return x, d, R, atom, angle, coef
+
+
+def test_repeated_atom_twin_cases_pin_the_largest_weight_reading():
+    # twin A: in patch 0 the larger |weight| comes second, in patch 1 first;
+    # twin B swaps which occurrence is larger.  In both, the oracle's atom 0
+    # must be the leading direction of the columns aligned with the larger
+    # |weight|, which differs from the one a first-occurrence rule gives.
+    for first_is_larger in (False, True):
+        x, d, R, atom, angle, coef = _twin_case(first_is_larger)
+        d_new, n_used = ksvd.ksvd_update(x, d, R, atom, angle, coef)
+        assert n_used[0] == 4 and n_used[1] == 2
+        Y = _direct_columns(x, d, R, atom, angle, coef, 0)
+        assert np.allclose(ksvd.pack(d_new[0]), _leading(Y), atol=1e-12)
+        Y_first = _direct_columns(x, d, R, atom, angle, coef, 0, rule="first")
+        assert np.abs(_leading(Y_first) - ksvd.pack(d_new[0])).max() > 1e-3
+    # equal |weights|: the earliest occurrence aligns the column
+    x, d, R, atom, angle, coef = _twin_case(False)
+    coef[0] = [0.8, -0.8]
+    d_new, _ = ksvd.ksvd_update(x, d, R, atom, angle, coef)
+    Y = _direct_columns(x, d, R, atom, angle, coef, 0)
+    assert np.allclose(ksvd.pack(d_new[0]), _leading(Y), atol=1e-12)
+    Y_last = _direct_columns(x, d, R, atom, angle, coef, 0, rule="last")
+    assert np.abs(_leading(Y_last) - ksvd.pack(d_new[0])).max() > 1e-3
