@@ -327,6 +327,9 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
  *   clears its counter first): calls whose work may overlap on the GPU race
  *   and give wrong results, so issue them on one stream or synchronise
  *   between them.  The array stays allocated until the process exits.
+ *   The looked-up address is kept for the life of the process: a
+ *   cudaDeviceReset between calls is not supported (the next call would use
+ *   the address of the destroyed context).
  */
 int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
                        int32_t *atom, int32_t *angle_idx, float *angle, double *coef,

@@ -55,7 +55,9 @@ extern "C" int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t 
   if (P == 0) return RSC_OK;
   if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(x) & 15u) || (reinterpret_cast<uintptr_t>(coef) & 7u) ||
-      (reinterpret_cast<uintptr_t>(atom) & 3u) || (reinterpret_cast<uintptr_t>(angle_idx) & 3u))
+      (reinterpret_cast<uintptr_t>(atom) & 3u) || (reinterpret_cast<uintptr_t>(angle_idx) & 3u) ||
+      (angle && (reinterpret_cast<uintptr_t>(angle) & 3u)) ||
+      (resid_norm2 && (reinterpret_cast<uintptr_t>(resid_norm2) & 3u)))
     return RSC_ERR_INVALID;
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);

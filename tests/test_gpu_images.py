@@ -124,3 +124,36 @@ def test_encode_images_21x21(rsc, precision):
     print(precision, s)
     dic.close()
     b.close()
+
+
+@pytest.mark.parametrize("shape", [(11, 6, 8, 16, 32, 3), (21, 10, 12, 12, 16, 3)])
+@pytest.mark.parametrize("precision", ["fp32", "f16"])
+def test_code_gpu_projection_at_full_margin(rsc, shape, precision):
+    """The coder alone at the full parity bar on image windows: the GPU's own
+    projected coefficients (rsc_project) are coded with rsc_encode and checked
+    against the oracle run on those same coefficients, at the 1e-6 selection
+    margin and the 1e-5 (fp32) / 1e-3 (f16) weight tolerances; rsc_encode_images,
+    which projects and codes in one call, gives the same codes."""
+    import torch
+    N, J, kmax, M, R, K = shape
+    shapes = [(N + 20, N + 31), (N, N), (N + 3, N + 44), (N + 25, N + 9)]
+    imgs = [image(h, w, 90 + i) for i, (h, w) in enumerate(shapes)]
+    d = synth.make_dictionary(M, J, kmax, 91)
+    b = rsc.Basis(N, J, kmax)
+    dic = rsc.Dictionary(torch.from_numpy(d).cuda(), R)
+    ti = [torch.from_numpy(im).cuda() for im in imgs]
+    xs = torch.cat([rsc.project(b, t).reshape(-1, kmax + 1, J, 2) for t in ti])
+    out = rsc.encode(dic, xs, K, precision)
+    one = rsc.encode_images(dic, b, ti, K, precision)
+    torch.cuda.synchronize()
+    assert rsc.rsc_dict_check(dic.handle) == 0
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    g1 = {k: v.cpu().numpy() for k, v in one.items()}
+    x = xs.cpu().numpy()
+    s = check(x, d, R, K, g, coef_tol=1e-5 if precision == "fp32" else 1e-3, margin=1e-6)
+    print(shape, precision, s)
+    assert s["pinned_steps"] > 0.9 * x.shape[0] * K
+    assert np.array_equal(g1["atom"], g["atom"]) and np.array_equal(g1["angle_idx"], g["angle_idx"])
+    assert np.allclose(g1["coef"], g["coef"], rtol=0, atol=1e-12 * np.abs(g["coef"]).max())
+    dic.close()
+    b.close()
