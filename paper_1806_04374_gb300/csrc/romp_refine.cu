@@ -7,16 +7,17 @@
 // of two chosen from a bound on their norm (rsc_internal.h), so that scores
 // come back as 2^(16 - e) times their true value.  romp_refine_kernel then,
 // after every scoring pass (romp_score.cu):
-//   * certifies the two candidate lists (one per column half of the scoring
-//     pass): E bounds the fp16 error of a score (rounding of both operands,
-//     accumulation, and the FP32 residual's own error); every row with
-//     |score| >= s1 - 2E is in a list unless a list's largest value left out
+//   * certifies the scoring pass's candidates (per column half: kept blocks
+//     of 32 rows and a mask of columns): E bounds the fp16 error of a score
+//     (rounding of both operands, accumulation, and the FP32 residual's own
+//     error); every row with |score| >= s1 - 2E is row b + u of a kept block
+//     b and a masked column u, unless a half's bound on what it left out
 //     (disc) is >= s1 - 2E, in which case the patch is handed to the FP32
 //     path;
-//   * re-scores the candidates in the window exactly in double-float as
-//     <A_c, x> - sum_i a_i <A_c, A_i> (ties: smallest m*R + r): the one with
-//     the largest approximate value first, the others (K <= 5) only when
-//     their FP32 score plus its error bound reaches the exact best;
+//   * re-scores those rows exactly in double-float as
+//     <A_c, x> - sum_i a_i <A_c, A_i> (ties: smallest m*R + r): the half's
+//     best row first, the others (K <= 5) only when their FP32 score plus its
+//     error bound reaches the exact best;
 //   * adds the Cholesky row of the winner (Gram entries and right-hand side
 //     in double-float, factor and solve in FP64) and writes the new residual.
 // Per-patch state lives in HBM as structure-of-arrays (coalesced over
@@ -275,17 +276,17 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
     load_state<KK>(a, p, S, t, e, xnorm, rnorm, dr);
     // accumulator scores are 2^(16 - e) times the true scores
     const float unscale = ldexpf(1.0f, e - 16);
-    // the scoring pass's two candidate lists (one per column half of each
-    // chunk, each sorted in descending order): their heads give the best
-    // value; the entries are read again by the re-scoring loop below
+    // the scoring pass's two lists of kept blocks (one per column half of
+    // each chunk, each sorted by block maximum in descending order): their
+    // heads give the best value; the entries are read again by the
+    // re-scoring loop below
     const float *cvp = a.cand_val + p * kTcCand;
     const int *cip = a.cand_idx + p * kTcCand;
     const float2 dv = *reinterpret_cast<const float2 *>(a.cand_disc + 2 * p);
     const float disc = fmaxf(dv.x, dv.y) * unscale;
     const float stop_level = 1e-10f * xnorm;
     const float s1 = fmaxf(cvp[0], cvp[kTcTop]) * unscale;
-    // fp16 error of a score (score_err_base) plus 2^-16 s1 for the low
-    // mantissa bits the scoring kernel replaces by a column index
+    // fp16 error of a score (score_err_base) plus a spare 2^-16 s1
     const float E = score_err_base(rnorm, dr, e, a.L) + 1.52587890625e-5f * fabsf(s1);
     int outcome = 0;  // 0 continue, 1 finished/stopped, 2 hand-off
     bool have_factor = false;
@@ -298,21 +299,25 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
       } else {
         // a candidate unit is one steered atom (row r*M + m), or in the
         // paired layout the two angles r and r + R/2 of atom m (row r*M + m,
-        // r < R/2, scored by max(|s(r)|, |s(r + R/2)|)); every unit in the
-        // certified window is re-scored exactly (the window holds 1.1 units
-        // on average, so no cheaper screen pays for its divergence)
+        // r < R/2, scored by max(|s(r)|, |s(r + R/2)|)).  Every unit in the
+        // certified window is row b + u of a kept block b (slot q) whose
+        // maximum reaches the window and a column u in its half's class mask;
+        // the half's best unit (the block with the largest maximum and the
+        // half's best column) is re-scored exactly first.
         constexpr int NP = PAIRED ? 2 : 1;
         const int Rh = R / 2;
+        const int MR = PAIRED ? M * Rh : M * R;
         df best = df_make(0.0f), best_ax = df_make(0.0f);
         df bg[KK];
 #pragma unroll
         for (int i = 0; i < KK; ++i) bg[i] = df_make(0.0f);
         int bm = -1, br = 0, bflat = 0;
-        // the slots inside the window as a bit mask, so that the warp runs the
-        // re-scoring body max(units per lane) times, not once per slot
-        // position at which some lane has a unit
-        unsigned mask = 0;
-        int qf = -1;  // the slot with the largest approximate value: re-scored first
+        // the kept blocks inside the window as a bit mask; the loop below runs
+        // over (block, column) pairs, so that a warp runs the re-scoring body
+        // max(units per lane) times
+        unsigned bmask = 0;
+        int qf = -1;  // the block with the largest maximum
+        const uint4 mk = *reinterpret_cast<const uint4 *>(a.cand_mask + 4 * p);
         {
           const int4 i0 = *reinterpret_cast<const int4 *>(cip);
           const int4 i1 = *reinterpret_cast<const int4 *>(cip + 4);
@@ -324,13 +329,14 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
 #pragma unroll
           for (int q = 0; q < kTcCand; ++q)
             if (iv[q] >= 0 && vv[q] * unscale >= thr) {
-              mask |= 1u << q;
+              bmask |= 1u << q;
               if (vv[q] > vbest) {
                 vbest = vv[q];
                 qf = q;
               }
             }
         }
+        const int uf = qf < 0 ? 0 : (int)(qf < kTcTop ? mk.y : mk.w);
         // The other units are first scored in FP32 and re-scored exactly only
         // if they can reach the exact best so far.  Error of the FP32 score:
         // each per-harmonic dot product of J complex entries and the angle
@@ -346,13 +352,19 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
           if (i < t) asum += fabsf(S.ahi[i]) + fabsf(S.alo[i]);
         const float E32 = 4.0f * (float)(2 * J + 2 * H + 8) * kU32 * (xnorm + asum) + asum * kU32;
         static_assert(kTcCand == 8, "candidate slots are read as two int4 / float4");
+        // unit iterator: (q, u) starts at the half's best unit; the rest of
+        // its block's columns, then the other kept blocks' columns follow, so a
+        // lane with one unit runs the body once
+        int q = qf, u = qf < 0 ? 0 : uf;
+        unsigned uleft = qf < 0 ? 0u : ((qf < kTcTop ? mk.x : mk.z) & ~(1u << uf));
+        unsigned bleft = qf < 0 ? 0u : (bmask & ~(1u << qf));
+        bool more = qf >= 0, first = true;
 #pragma unroll 1
-        while (mask) {
-          const int q = qf >= 0 ? qf : __ffs(mask) - 1;
-          mask &= ~(1u << q);
-          const int id = cip[q];
+        while (more) {
+          const int id = cip[q] + u;
+          bool go = id < MR;
           const int m = id % M, r = id / M;
-          if (kScreen && qf < 0) {
+          if (kScreen && go && !first) {
             float f;
             if (PAIRED) {
               const float2 f2 = score32_pair<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H,
@@ -363,10 +375,10 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
                                     tw));
             }
             // cannot reach (or tie) the best: |best| >= |best.hi| (1 - 2^-22)
-            if (f + E32 < fabsf(best.hi) * 0.99999976f) continue;
+            go = !(f + E32 < fabsf(best.hi) * 0.99999976f);
           }
-          qf = -1;
-          {
+          first = false;
+          if (go) {
             df ax[NP], sc[NP], gq[NP][KK];
             if (PAIRED) {
               const DF2 x2 = score_x_pair(a.d + (size_t)m * HJ * 2, xp, J, H, r, tw);
@@ -407,6 +419,18 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
                 for (int i = 0; i < KK; ++i) bg[i] = gq[h][i];
               }
             }
+          }
+          // next unit: the next column of this block, else the first column
+          // of the next kept block with a non-empty mask
+          while (uleft == 0 && bleft != 0) {
+            q = __ffs(bleft) - 1;
+            bleft &= bleft - 1;
+            uleft = q < kTcTop ? mk.x : mk.z;
+          }
+          more = uleft != 0;
+          if (more) {
+            u = __ffs(uleft) - 1;
+            uleft &= uleft - 1;
           }
         }
         if (bm < 0 || !(fabsf(best.hi) > stop_level)) {

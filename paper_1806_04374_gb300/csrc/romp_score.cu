@@ -20,14 +20,18 @@
 //     so the widest N that two accumulator buffers allow is used;
 //   * warps 0-7 read each buffer back with tcgen05.ld: warp w reads TMEM
 //     lanes 32 (w mod 4) .. + 31 (one thread per patch) and one column half
-//     (w / 4, swapped on odd chunks).  Each warp keeps its own kTcTop largest block maxima of |score|
-//     (block = 32 columns: 32 atoms at one angle, or 32 atom pairs) with
-//     their rows, plus the largest value it left out (disc); the refine pass
-//     takes the union of the two lists, so the halves never synchronise.  A
-//     block whose maximum is more than the patch's window (>= 2 E, from the
-//     refine pass) below the half's running best can neither win nor fall
-//     inside the final window, so it is neither kept nor needs its second
-//     maximum.
+//     (w / 4, swapped on odd chunks).  Per patch, each warp keeps for every
+//     column u of a 32-column block (block = 32 atoms at one angle, or 32 atom
+//     pairs) the largest value column u had in any block ("class" u, in
+//     registers), and a ring of the blocks whose maximum came within the
+//     patch's window (>= 2 E, from the refine pass) of the running best.  At
+//     the end of the step every unit within the window of the half's best
+//     lies in a kept block and in a class whose maximum reaches the
+//     threshold, so the half hands over up to kTcTop blocks, the class mask
+//     and its best class, plus a bound on what it left out (disc); the refine
+//     expands blocks x classes.  Per value that is one add (paired), one max
+//     into its class and half a three-input max for its block, with no
+//     per-block branch; the two halves never synchronise.
 // All hand-offs are mbarriers; every wait is bounded (2 s of globaltimer) and
 // a failed wait records RSC_ERR_TIMEOUT, stops the CTA's loops, drains the
 // copies and MMAs it issued, and frees its TMEM.
@@ -44,6 +48,7 @@ constexpr int kSBufC = 256;             // accumulator columns per TMEM buffer
 constexpr uint32_t kSCols = 2 * kSBufC; // two buffers: all 512 TMEM columns
 constexpr int kSThreads = 320;          // 8 epilogue warps + TMA warp + MMA warp
 constexpr uint64_t kSWaitNs = 2000000000ull;
+constexpr int kRing = 8;                // blocks near the running best kept per step
 
 // Shape of one instantiation: NB 64-column blocks per packed row (2 for rows
 // of kTcKst, 4 for kTcKstLong).
@@ -235,14 +240,16 @@ __global__ void __launch_bounds__(kSThreads, 1)
       const int64_t p = tile * kSTile + row;
       const bool act = p < a.P && a.status[p] > 0;
       const float win = act ? a.win[p] : 0.0f;
-      float tv[kTcTop];
-      int ti[kTcTop];
+      // cmax[u]: largest value of column u of any 32-column block this half
+      // saw (a "class": the rows base + u of every block); the ring holds the
+      // blocks whose maximum came within `win` of the running best
+      float cmax[32];
 #pragma unroll
-      for (int q = 0; q < kTcTop; ++q) {
-        tv[q] = -INFINITY;
-        ti[q] = -1;
-      }
-      float disc = -INFINITY;
+      for (int u = 0; u < 32; ++u) cmax[u] = -1.0f;
+      float rbest = -1.0f, lost = -1.0f;
+      float rv[kRing];
+      int ri[kRing];
+      int cnt = 0;
       for (int c = 0; c < nch; ++c, ++g) {
         const uint32_t b = g & 1, ub = g >> 1;
         const bool done = !*s_abort && tc::mbar_wait_bounded(bar(kBarAccFull + b), ub & 1, kSWaitNs);
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
         tc::fence_after_sync();
         // this warp's column half of the buffer, hc = half xor (chunk parity),
         // so the same atom at consecutive angles (consecutive chunks when a
-        // chunk is one angle) alternates between the two lists: plain rows
+        // chunk is one angle) alternates between the two halves: plain rows
         // hc*N/2 .. + N/2 - 1 of the chunk; paired: pairs hc*N/2 .. + N/2 - 1,
         // their even parts in columns 0..N-1 and odd parts in N..2N-1
         const int hc = half ^ (c & 1);
@@ -262,74 +269,50 @@ __global__ void __launch_bounds__(kSThreads, 1)
         const int nvalid = min(N, a.MR - c * N) - hc * Sh::HALF;
 #pragma unroll 1
         for (int piece = 0; piece < Sh::PIECES; ++piece) {
-          uint32_t v[32];
-          tc::tmem_ld32(taddr + piece * 32, v);
-          if (PAIRED) {
-            // pair value |E| + |O| = max(|score(r)|, |score(r + R/2)|)
-            uint32_t o[32];
-            tc::tmem_ld32(taddr + N + piece * 32, o);
-            tc::tmem_wait_ld();
+          const int nv = nvalid - piece * 32;  // valid columns of this block
+          float hm[2];
 #pragma unroll
-            for (int u = 0; u < 32; ++u)
-              v[u] = __float_as_uint(fabsf(__uint_as_float(v[u])) + fabsf(__uint_as_float(o[u])));
-          } else {
-            tc::tmem_wait_ld();
-          }
-          if (act) {
-            // keys: |score| with the low 5 mantissa bits replaced by the
-            // column within the block; non-negative floats order like their
-            // bits, so one max gives the block maximum and its column (the
-            // truncation is < 2^-18 relative and covered by the refine's
-            // error bound)
-            const int base = c * N + hc * Sh::HALF + piece * 32;
-            const int nv = nvalid - piece * 32;
-            float key[32];
+          for (int sub = 0; sub < 2; ++sub) {
+            uint32_t v[16];
+            tc::tmem_ld16(taddr + piece * 32 + sub * 16, v);
+            float f[16];
+            if (PAIRED) {
+              // pair value |E| + |O| = max(|score(r)|, |score(r + R/2)|)
+              uint32_t o[16];
+              tc::tmem_ld16(taddr + N + piece * 32 + sub * 16, o);
+              tc::tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 32; ++u)
-              key[u] = __int_as_float((int)((v[u] & 0x7FFFFFE0u) | (uint32_t)u));
+              for (int u = 0; u < 16; ++u)
+                f[u] = fabsf(__uint_as_float(v[u])) + fabsf(__uint_as_float(o[u]));
+            } else {
+              tc::tmem_wait_ld();
+#pragma unroll
+              for (int u = 0; u < 16; ++u) f[u] = fabsf(__uint_as_float(v[u]));
+            }
             if (nv < 32) {
 #pragma unroll
-              for (int u = 0; u < 32; ++u)
-                if (u >= nv) key[u] = -1.0f;
+              for (int u = 0; u < 16; ++u)
+                if (sub * 16 + u >= nv) f[u] = -1.0f;
             }
-            // the block maximum as the larger of the two 16-column halves'
-            // maxima (two independent three-input max chains)
-            float h0 = -1.0f, h1 = -1.0f;
+            float h = -1.0f;
 #pragma unroll
-            for (int u = 0; u < 16; u += 2) {
-              h0 = fmax3(h0, key[u], key[u + 1]);
-              h1 = fmax3(h1, key[16 + u], key[17 + u]);
-            }
-            const float m1 = fmaxf(h0, h1);
-            // kept: the block maximum beats the last kept one and is not below
-            // the window under the running best (NaN-safe form)
-            if (m1 >= 0.0f && m1 > tv[kTcTop - 1] && !(m1 < tv[0] - win)) {
-              const int us = __float_as_int(m1) & 31;
-              // second value: the other half's maximum or the second largest
-              // key of the winning half (keys are distinct)
-              const bool w1 = us >= 16;
-              float m2 = w1 ? h0 : h1;
+            for (int u = 0; u < 16; u += 2) h = fmax3(h, f[u], f[u + 1]);
 #pragma unroll
-              for (int u = 0; u < 16; ++u) {
-                const float kv = w1 ? key[16 + u] : key[u];
-                m2 = fmaxf(m2, kv < m1 ? kv : -1.0f);
-              }
-              topn_insert(tv, ti, disc, m1, base + us);
-              if (m2 >= 0.0f && !(m2 < tv[0] - win)) {
-                // the block's second value may lie in the window too: keep it
-                // as a candidate and bound the rest by the third value
-                float m3 = -1.0f;
-#pragma unroll
-                for (int u = 0; u < 32; ++u) m3 = fmaxf(m3, key[u] < m2 ? key[u] : -1.0f);
-                topn_insert(tv, ti, disc, m2, base + (__float_as_int(m2) & 31));
-                disc = fmaxf(disc, m3);
-              } else {
-                disc = fmaxf(disc, m2);
-              }
-            } else {
-              disc = fmaxf(disc, m1);
-            }
+            for (int u = 0; u < 16; ++u) cmax[sub * 16 + u] = fmaxf(cmax[sub * 16 + u], f[u]);
+            hm[sub] = h;
           }
+          // the block maximum; a block within the window of the running best
+          // (NaN-safe form) goes into the ring, and the value it overwrites,
+          // if any, is bounded by `lost`
+          const float bm = fmaxf(hm[0], hm[1]);
+          if (!(bm < rbest - win)) {
+            const int sl = cnt & (kRing - 1);
+            if (cnt >= kRing) lost = fmaxf(lost, rv[sl]);
+            rv[sl] = bm;
+            ri[sl] = c * N + hc * Sh::HALF + piece * 32;
+            ++cnt;
+          }
+          rbest = fmaxf(rbest, bm);
         }
         tc::fence_before_sync();
         __syncwarp();
@@ -337,13 +320,43 @@ __global__ void __launch_bounds__(kSThreads, 1)
       }
       if (!ok) break;
       if (act) {
-        // this half's list: entries [half * kTcTop, half * kTcTop + kTcTop)
-        // of the patch's kTcCand candidates; the refine takes the union
+        // Every unit of this half with value >= thr = best - win lies in a
+        // block of the ring with maximum >= thr and in a class with
+        // cmax >= thr: the refine expands (kept blocks) x (class mask).  What
+        // is left out is below thr, or a block the list or the ring dropped
+        // (their values go to disc).
+        const float thr = rbest - win;
+        float tv[kTcTop];
+        int ti[kTcTop];
+#pragma unroll
+        for (int q = 0; q < kTcTop; ++q) {
+          tv[q] = -INFINITY;
+          ti[q] = -1;
+        }
+        float disc = fmaxf(thr, lost);
+        const int nr = min(cnt, kRing);
+#pragma unroll 1
+        for (int i = 0; i < nr; ++i)
+          if (rv[i] >= thr) topn_insert(tv, ti, disc, rv[i], ri[i]);
+        uint32_t um = 0;
+        int ubest = 0;
+        float cb = -1.0f;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          um |= (cmax[u] >= thr ? 1u : 0u) << u;
+          if (cmax[u] > cb) {
+            cb = cmax[u];
+            ubest = u;
+          }
+        }
+        // this half's entries [half * kTcTop, half * kTcTop + kTcTop) of the
+        // patch's kTcCand block slots, its class mask and best class
         int *ci = a.cand_idx + p * kTcCand + half * kTcTop;
         float *cv = a.cand_val + p * kTcCand + half * kTcTop;
         *reinterpret_cast<int4 *>(ci) = make_int4(ti[0], ti[1], ti[2], ti[3]);
         *reinterpret_cast<float4 *>(cv) = make_float4(tv[0], tv[1], tv[2], tv[3]);
         a.cand_disc[p * 2 + half] = disc;
+        *reinterpret_cast<uint2 *>(a.cand_mask + p * 4 + half * 2) = make_uint2(um, (uint32_t)ubest);
       }
     }
   }

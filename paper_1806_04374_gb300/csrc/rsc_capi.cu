@@ -319,6 +319,7 @@ size_t f16_scratch_bytes(int64_t P, int K, int L) {
   rsc_state_layout(K, &nD, &nF, &nI);
   auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
   return al256((size_t)P * L * 2) + 2 * al256((size_t)P * kTcCand * 4) + al256((size_t)P * 8) +
+         al256((size_t)P * 16) +
          2 * al256((size_t)P * 4) + al256((size_t)nD * P * 8) + al256((size_t)nF * P * 4) +
          al256((size_t)nI * P * 4) + al256((size_t)(P + 4) * 4);
 }
@@ -359,6 +360,7 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   ra.cand_idx = reinterpret_cast<int *>(take((size_t)P * kTcCand * 4));
   ra.cand_val = reinterpret_cast<float *>(take((size_t)P * kTcCand * 4));
   ra.cand_disc = reinterpret_cast<float *>(take((size_t)P * 8));
+  ra.cand_mask = reinterpret_cast<unsigned *>(take((size_t)P * 16));
   ra.status = reinterpret_cast<int *>(take((size_t)P * 4));
   ra.win = reinterpret_cast<float *>(take((size_t)P * 4));
   ra.sD = reinterpret_cast<double *>(take((size_t)nD * P * 8));
@@ -389,6 +391,7 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   sa.cand_idx = const_cast<int *>(ra.cand_idx);
   sa.cand_val = const_cast<float *>(ra.cand_val);
   sa.cand_disc = const_cast<float *>(ra.cand_disc);
+  sa.cand_mask = const_cast<unsigned *>(ra.cand_mask);
   sa.win = ra.win;
   sa.err = dict->err;
   CUtensorMap tmA;

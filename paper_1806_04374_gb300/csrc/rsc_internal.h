@@ -156,17 +156,21 @@ struct rsc_basis_view {
 };
 int rsc_basis_internals(const rsc_basis *basis, rsc_basis_view *view);
 
-// Candidates (block maxima and in-window second values) kept per patch and
-// greedy step by the tensor-core scoring: kTcTop per list; the split scoring
-// pass keeps one list per half of the accumulator columns, kTcCand in all.
+// Candidates kept per patch and greedy step by the tensor-core scoring:
+// kTcTop per list (the fused kernel: block maxima; the split scoring pass:
+// blocks of 32 rows within the window, one list per half of the accumulator
+// columns, kTcCand in all, expanded by a class mask, see ScoreArgs).
 constexpr int kTcTop = 4;
 constexpr int kTcCand = 2 * kTcTop;
 
 // One scoring pass of the split FP16 path (romp_score.cu): packed fp16
 // residual rows (TMA map tmA: [P][kTcKst]) times the steered dictionary
-// (tmB) -> per patch two lists (one per half of each chunk's rows) of the
-// kTcTop largest candidates of |score| with their rows (r*M + m), and the
-// largest value each list left out.
+// (tmB) -> per patch and half of each chunk's rows: up to kTcTop blocks of 32
+// rows (first row b, multiple of 32; rows b + u, u < 32) whose maximum |score|
+// lies within the window of the half's best, their maxima, the mask of the
+// columns u whose largest value over all blocks of the half lies within it,
+// the column of the half's best value, and a bound on every value left out.
+// Every row within the window is b + u for a kept b and a masked u.
 struct ScoreArgs {
   int64_t P;
   int ksteps, MR, nchunks;
@@ -175,9 +179,10 @@ struct ScoreArgs {
   int paired, ke, ko;
   int L;  // packed row length (kTcKst or kTcKstLong; the latter plain only)
   const int *status;  // > 0: patch still being coded
-  int *cand_idx;      // [P][kTcCand]
-  float *cand_val;    // [P][kTcCand]
-  float *cand_disc;   // [P][2]
+  int *cand_idx;      // [P][kTcCand] first rows of the kept blocks (-1: none)
+  float *cand_val;    // [P][kTcCand] their maxima (accumulator units)
+  float *cand_disc;   // [P][2] bound on the values each half left out
+  unsigned *cand_mask;  // [P][4] per half: column mask, column of the half's best
   // [P] per-patch certification window in accumulator units (written by the
   // refine pass with the row): a block maximum more than `win` below the
   // running best can neither win nor reach the window, so it is not kept
@@ -202,6 +207,7 @@ struct RefineArgs {
   const int *cand_idx;
   const float *cand_val;
   const float *cand_disc;
+  const unsigned *cand_mask;  // see ScoreArgs
   float *win;            // [P] window of the next scoring pass (see ScoreArgs)
   int paired;            // rows and candidates in the paired layout (rsc_slot_code)
   int *status;           // 1 active, 0 done, -1 handed to the FP32 path
