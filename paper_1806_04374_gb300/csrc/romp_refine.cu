@@ -7,15 +7,15 @@
 // of two chosen from a bound on their norm (rsc_internal.h), so that scores
 // come back as 2^(16 - e) times their true value.  romp_refine_kernel then,
 // after every scoring pass (romp_score.cu):
-//   * certifies the scoring pass's candidates (per column half: kept blocks
+//   * certifies the scoring pass's candidates (per column slice: kept blocks
 //     of 32 rows and a mask of columns): E bounds the fp16 error of a score
 //     (rounding of both operands, accumulation, and the FP32 residual's own
 //     error); every row with |score| >= s1 - 2E is row b + u of a kept block
-//     b and a masked column u, unless a half's bound on what it left out
+//     b and a masked column u, unless a slice's bound on what it left out
 //     (disc) is >= s1 - 2E, in which case the patch is handed to the FP32
 //     path;
 //   * re-scores those rows exactly in double-float as
-//     <A_c, x> - sum_i a_i <A_c, A_i> (ties: smallest m*R + r): the half's
+//     <A_c, x> - sum_i a_i <A_c, A_i> (ties: smallest m*R + r): the slice's
 //     best row first, the others (K <= 5) only when their FP32 score plus its
 //     error bound reaches the exact best;
 //   * adds the Cholesky row of the winner (Gram entries and right-hand side
@@ -261,13 +261,22 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
 // atoms) spills 1.8 KB a thread at that budget.  Measured on the 21 x 21-patch
 // image workload: 4 blocks (<= 128 registers, 0.8 KB of spills) 1.9% faster
 // than 3 (<= 168) and 4% faster than 2 (no spills).
-template <int KK, bool PAIRED>
+//
+// Two passes per step: a thread re-scores every unit of its patch in one loop,
+// so a warp runs that loop max(units per lane) times.  Nearly all patches have
+// one unit in the window, but among 32 lanes one with several is common, so
+// the first pass (PASS = 1) finishes only the patches with one unit and
+// appends the others to a list, which the second pass (PASS = 2) finishes with
+// every lane on a patch that needs the loop.
+template <int KK, bool PAIRED, int PASS>
 __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const RefineArgs a) {
   const int H = a.H, J = a.J, R = a.R, M = a.M, HJ = H * J;
   const int *qtab;
   const TwS tw = load_tw(a, qtab);
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
-       p += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nwork = PASS == 2 ? (int64_t)*a.slow_count : a.P;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwork;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = PASS == 2 ? (int64_t)a.slow_list[w] : w;
     if (a.status[p] <= 0) continue;
     const float *xp = a.x + p * (int64_t)(2 * HJ);
     Ls<KK> S;
@@ -276,16 +285,22 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
     load_state<KK>(a, p, S, t, e, xnorm, rnorm, dr);
     // accumulator scores are 2^(16 - e) times the true scores
     const float unscale = ldexpf(1.0f, e - 16);
-    // the scoring pass's two lists of kept blocks (one per column half of
-    // each chunk, each sorted by block maximum in descending order): their
-    // heads give the best value; the entries are read again by the
-    // re-scoring loop below
+    // the scoring pass's lists of kept blocks (one per column slice of each
+    // chunk, each sorted by block maximum in descending order): their heads
+    // give the best value; the entries are read again by the re-scoring loop
+    // below
+    static_assert(kTcTop == 4, "slots read as float4 / int4 per slice");
     const float *cvp = a.cand_val + p * kTcCand;
     const int *cip = a.cand_idx + p * kTcCand;
-    const float2 dv = *reinterpret_cast<const float2 *>(a.cand_disc + 2 * p);
-    const float disc = fmaxf(dv.x, dv.y) * unscale;
+    float discm = -INFINITY, head = -INFINITY;
+#pragma unroll
+    for (int sl = 0; sl < kTcSplit; ++sl) {
+      discm = fmaxf(discm, a.cand_disc[kTcSplit * p + sl]);
+      head = fmaxf(head, cvp[kTcTop * sl]);
+    }
+    const float disc = discm * unscale;
     const float stop_level = 1e-10f * xnorm;
-    const float s1 = fmaxf(cvp[0], cvp[kTcTop]) * unscale;
+    const float s1 = head * unscale;
     // fp16 error of a score (score_err_base) plus a spare 2^-16 s1
     const float E = score_err_base(rnorm, dr, e, a.L) + 1.52587890625e-5f * fabsf(s1);
     int outcome = 0;  // 0 continue, 1 finished/stopped, 2 hand-off
@@ -301,9 +316,9 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
         // paired layout the two angles r and r + R/2 of atom m (row r*M + m,
         // r < R/2, scored by max(|s(r)|, |s(r + R/2)|)).  Every unit in the
         // certified window is row b + u of a kept block b (slot q) whose
-        // maximum reaches the window and a column u in its half's class mask;
-        // the half's best unit (the block with the largest maximum and the
-        // half's best column) is re-scored exactly first.
+        // maximum reaches the window and a column u in its slice's class mask;
+        // the best slice's best unit (the block with the largest maximum and
+        // that slice's best column) is re-scored exactly first.
         constexpr int NP = PAIRED ? 2 : 1;
         const int Rh = R / 2;
         const int MR = PAIRED ? M * Rh : M * R;
@@ -312,31 +327,62 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
 #pragma unroll
         for (int i = 0; i < KK; ++i) bg[i] = df_make(0.0f);
         int bm = -1, br = 0, bflat = 0;
-        // the kept blocks inside the window as a bit mask; the loop below runs
-        // over (block, column) pairs, so that a warp runs the re-scoring body
-        // max(units per lane) times
+        // the kept blocks inside the window as a bit mask (slot q = slice q / 4);
+        // the loop below runs over (block, column) pairs, so that a warp runs
+        // the re-scoring body max(units per lane) times
         unsigned bmask = 0;
         int qf = -1;  // the block with the largest maximum
-        const uint4 mk = *reinterpret_cast<const uint4 *>(a.cand_mask + 4 * p);
+        // column mask and best column of slice sl
+        unsigned umk[kTcSplit], ubk[kTcSplit];
+#pragma unroll
+        for (int sl = 0; sl < kTcSplit; ++sl) {
+          const uint2 v = *reinterpret_cast<const uint2 *>(a.cand_mask + 2 * (kTcSplit * p + sl));
+          umk[sl] = v.x;
+          ubk[sl] = v.y;
+        }
+        auto umask_of = [&](int sl) {
+          unsigned r = umk[0];
+#pragma unroll
+          for (int i = 1; i < kTcSplit; ++i) r = sl == i ? umk[i] : r;
+          return r;
+        };
+        auto ubest_of = [&](int sl) {
+          unsigned r = ubk[0];
+#pragma unroll
+          for (int i = 1; i < kTcSplit; ++i) r = sl == i ? ubk[i] : r;
+          return (int)r;
+        };
         {
-          const int4 i0 = *reinterpret_cast<const int4 *>(cip);
-          const int4 i1 = *reinterpret_cast<const int4 *>(cip + 4);
-          const float4 v0 = *reinterpret_cast<const float4 *>(cvp);
-          const float4 v1 = *reinterpret_cast<const float4 *>(cvp + 4);
-          const int iv[kTcCand] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
-          const float vv[kTcCand] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
           float vbest = -1.0f;
 #pragma unroll
-          for (int q = 0; q < kTcCand; ++q)
-            if (iv[q] >= 0 && vv[q] * unscale >= thr) {
-              bmask |= 1u << q;
-              if (vv[q] > vbest) {
-                vbest = vv[q];
-                qf = q;
+          for (int sl = 0; sl < kTcSplit; ++sl) {
+            const int4 iq = *reinterpret_cast<const int4 *>(cip + kTcTop * sl);
+            const float4 vq = *reinterpret_cast<const float4 *>(cvp + kTcTop * sl);
+            const int iv[kTcTop] = {iq.x, iq.y, iq.z, iq.w};
+            const float vv[kTcTop] = {vq.x, vq.y, vq.z, vq.w};
+#pragma unroll
+            for (int j = 0; j < kTcTop; ++j)
+              if (iv[j] >= 0 && vv[j] * unscale >= thr) {
+                bmask |= 1u << (sl * kTcTop + j);
+                if (vv[j] > vbest) {
+                  vbest = vv[j];
+                  qf = sl * kTcTop + j;
+                }
               }
-            }
+          }
         }
-        const int uf = qf < 0 ? 0 : (int)(qf < kTcTop ? mk.y : mk.w);
+        const int uf = qf < 0 ? 0 : ubest_of(qf / kTcTop);
+        if (PASS == 1) {
+          // units in the window: columns of the masks over the kept blocks
+          int nunits = 0;
+#pragma unroll
+          for (int q = 0; q < kTcCand; ++q)
+            if (bmask & (1u << q)) nunits += __popc(umask_of(q / kTcTop));
+          if (nunits > 1) {
+            a.slow_list[atomicAdd(a.slow_count, 1)] = (int)p;
+            continue;
+          }
+        }
         // The other units are first scored in FP32 and re-scored exactly only
         // if they can reach the exact best so far.  Error of the FP32 score:
         // each per-harmonic dot product of J complex entries and the angle
@@ -351,12 +397,11 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
         for (int i = 0; i < KK; ++i)
           if (i < t) asum += fabsf(S.ahi[i]) + fabsf(S.alo[i]);
         const float E32 = 4.0f * (float)(2 * J + 2 * H + 8) * kU32 * (xnorm + asum) + asum * kU32;
-        static_assert(kTcCand == 8, "candidate slots are read as two int4 / float4");
         // unit iterator: (q, u) starts at the half's best unit; the rest of
         // its block's columns, then the other kept blocks' columns follow, so a
         // lane with one unit runs the body once
         int q = qf, u = qf < 0 ? 0 : uf;
-        unsigned uleft = qf < 0 ? 0u : ((qf < kTcTop ? mk.x : mk.z) & ~(1u << uf));
+        unsigned uleft = qf < 0 ? 0u : (umask_of(qf / kTcTop) & ~(1u << uf));
         unsigned bleft = qf < 0 ? 0u : (bmask & ~(1u << qf));
         bool more = qf >= 0, first = true;
 #pragma unroll 1
@@ -364,7 +409,7 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
           const int id = cip[q] + u;
           bool go = id < MR;
           const int m = id % M, r = id / M;
-          if (kScreen && go && !first) {
+          if (PASS != 1 && kScreen && go && !first) {
             float f;
             if (PAIRED) {
               const float2 f2 = score32_pair<KK>(a.d + (size_t)m * HJ * 2, xp, a.xgram, M, J, H,
@@ -420,12 +465,13 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
               }
             }
           }
+          if (PASS == 1) break;  // the first pass keeps one-unit patches only
           // next unit: the next column of this block, else the first column
           // of the next kept block with a non-empty mask
           while (uleft == 0 && bleft != 0) {
             q = __ffs(bleft) - 1;
             bleft &= bleft - 1;
-            uleft = q < kTcTop ? mk.x : mk.z;
+            uleft = umask_of(q / kTcTop);
           }
           more = uleft != 0;
           if (more) {
@@ -505,12 +551,22 @@ int launch_refine_t(const RefineArgs &a, bool init, cudaStream_t stream) {
   const int64_t cap = (int64_t)nsm * 32;
   const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
   const size_t shm = (size_t)((4 * a.H * a.R + 3) & ~3) * 4 + (size_t)a.L * 4;
-  if (init)
+  if (init) {
     romp_init_kernel<KK><<<grid, 128, shm, stream>>>(a);
-  else if (a.paired)
-    romp_refine_kernel<KK, true><<<grid, 128, shm, stream>>>(a);
-  else
-    romp_refine_kernel<KK, false><<<grid, 128, shm, stream>>>(a);
+  } else {
+    e = cudaMemsetAsync(a.slow_count, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return rsc_cuda_fail(e);
+    // the second pass's list holds a few percent of the patches: a grid of
+    // 4 blocks per SM walks it
+    const unsigned grid2 = (unsigned)(grid < (unsigned)(nsm * 4) ? grid : (unsigned)(nsm * 4));
+    if (a.paired) {
+      romp_refine_kernel<KK, true, 1><<<grid, 128, shm, stream>>>(a);
+      romp_refine_kernel<KK, true, 2><<<grid2, 128, shm, stream>>>(a);
+    } else {
+      romp_refine_kernel<KK, false, 1><<<grid, 128, shm, stream>>>(a);
+      romp_refine_kernel<KK, false, 2><<<grid2, 128, shm, stream>>>(a);
+    }
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return RSC_OK;

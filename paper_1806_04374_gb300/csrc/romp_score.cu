@@ -19,19 +19,19 @@
 //     to 64 on this part (measured: the same launch time at N = 16, 32, 64),
 //     so the widest N that two accumulator buffers allow is used;
 //   * warps 0-7 read each buffer back with tcgen05.ld: warp w reads TMEM
-//     lanes 32 (w mod 4) .. + 31 (one thread per patch) and one column half
-//     (w / 4, swapped on odd chunks).  Per patch, each warp keeps for every
+//     lanes 32 (w mod 4) .. + 31 (one thread per patch) and one column slice
+//     (one of kTcSplit, rotated by one per chunk).  Per patch, each warp keeps for every
 //     column u of a 32-column block (block = 32 atoms at one angle, or 32 atom
 //     pairs) the largest value column u had in any block ("class" u, in
 //     registers), and a ring of the blocks whose maximum came within the
 //     patch's window (>= 2 E, from the refine pass) of the running best.  At
-//     the end of the step every unit within the window of the half's best
+//     the end of the step every unit within the window of the slice's best
 //     lies in a kept block and in a class whose maximum reaches the
-//     threshold, so the half hands over up to kTcTop blocks, the class mask
+//     threshold, so the slice hands over up to kTcTop blocks, the class mask
 //     and its best class, plus a bound on what it left out (disc); the refine
 //     expands blocks x classes.  Per value that is one add (paired), one max
 //     into its class and half a three-input max for its block, with no
-//     per-block branch; the two halves never synchronise.
+//     per-block branch; the slices never synchronise.
 // All hand-offs are mbarriers; every wait is bounded (2 s of globaltimer) and
 // a failed wait records RSC_ERR_TIMEOUT, stops the CTA's loops, drains the
 // copies and MMAs it issued, and frees its TMEM.
@@ -46,9 +46,10 @@ constexpr int kSStagesMax = 6;          // barrier slots reserved for the B ring
 constexpr int kABlk = kSTile * 128;     // one 64-column block of an A tile (bytes)
 constexpr int kSBufC = 256;             // accumulator columns per TMEM buffer
 constexpr uint32_t kSCols = 2 * kSBufC; // two buffers: all 512 TMEM columns
-constexpr int kSThreads = 320;          // 8 epilogue warps + TMA warp + MMA warp
+constexpr int kSEpi = 4 * kTcSplit;     // epilogue warps: 4 lane quarters x kTcSplit slices
+constexpr int kSThreads = 32 * (kSEpi + 2);  // + TMA warp + MMA warp
 constexpr uint64_t kSWaitNs = 2000000000ull;
-constexpr int kRing = 8;                // blocks near the running best kept per step
+constexpr int kRing = 16;               // blocks near the running best kept per step
 
 // Shape of one instantiation: NB 64-column blocks per packed row (2 for rows
 // of kTcKst, 4 for kTcKstLong).
@@ -60,13 +61,14 @@ struct SShape {
   static constexpr int kABufs = NB > 2 ? 1 : 2;       // A tiles in flight
   static constexpr int kBStage = N * 128;             // one K-block of a chunk (bytes)
   static constexpr int kStages = NB > 2 ? 5 : (PAIRED ? 6 : 4);
-  static constexpr int HALF = N / 2;                  // B rows per epilogue column half
-  static constexpr int PIECES = HALF / 32;            // 32-column pieces per half
+  static constexpr int SLICE = N / kTcSplit;          // B rows per epilogue column slice
+  static constexpr int PIECES = SLICE / 32;           // 32-column pieces per slice
   static constexpr int a_off = 0, b_off = kABufs * kATile;
   static constexpr int bar_off = b_off + kStages * kBStage;
   static constexpr int total = bar_off + 256 + 1024;  // barriers + alignment slack
   static_assert(kStages <= kSStagesMax, "barrier slots");
   static_assert(PAIRED ? 2 * N == kSBufC : N == kSBufC, "accumulator buffer width");
+  static_assert(PIECES >= 1 && SLICE % 32 == 0, "slices of whole 32-column blocks");
 };
 
 // barrier slots (8 bytes each)
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       tc::mbar_init(bar(kBarAFull + i), 1);
       tc::mbar_init(bar(kBarAEmpty + i), 1);
       tc::mbar_init(bar(kBarAccFull + i), 1);
-      tc::mbar_init(bar(kBarAccEmpty + i), 8);  // one arrival per epilogue warp
+      tc::mbar_init(bar(kBarAccEmpty + i), kSEpi);  // one arrival per epilogue warp
     }
     for (int s = 0; s < kSStagesMax; ++s) {
       tc::mbar_init(bar(kBarBFull + s), 1);
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
     if (a.err) atomicCAS(a.err, 0, RSC_ERR_TIMEOUT);
   };
 
-  if (warp == 8) {
+  if (warp == kSEpi) {
     // ---------------------------------------------------------------- TMA
     if (lane == 0) {
       uint32_t gs = 0, it = 0;
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       for (int ab = 0; ab < kABufs; ++ab)
         if (issuedA[ab]) tc::mbar_wait_bounded(bar(kBarAFull + ab), (issuedA[ab] - 1) & 1, kSWaitNs);
     }
-  } else if (warp == 9) {
+  } else if (warp == kSEpi + 1) {
     // ---------------------------------------------------------------- MMA
     if (lane == 0) {
       uint32_t g = 0, gs = 0, it = 0, last = 0;
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, slice = warp >> 2;
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     uint32_t g = 0;
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       const int64_t p = tile * kSTile + row;
       const bool act = p < a.P && a.status[p] > 0;
       const float win = act ? a.win[p] : 0.0f;
-      // cmax[u]: largest value of column u of any 32-column block this half
+      // cmax[u]: largest value of column u of any 32-column block this slice
       // saw (a "class": the rows base + u of every block); the ring holds the
       // blocks whose maximum came within `win` of the running best
       float cmax[32];
@@ -259,14 +261,15 @@ __global__ void __launch_bounds__(kSThreads, 1)
           break;
         }
         tc::fence_after_sync();
-        // this warp's column half of the buffer, hc = half xor (chunk parity),
-        // so the same atom at consecutive angles (consecutive chunks when a
-        // chunk is one angle) alternates between the two halves: plain rows
-        // hc*N/2 .. + N/2 - 1 of the chunk; paired: pairs hc*N/2 .. + N/2 - 1,
-        // their even parts in columns 0..N-1 and odd parts in N..2N-1
-        const int hc = half ^ (c & 1);
-        const uint32_t taddr = tmem + lane_base + b * kSBufC + (uint32_t)(hc * Sh::HALF);
-        const int nvalid = min(N, a.MR - c * N) - hc * Sh::HALF;
+        // this warp's column slice of the buffer, hc = slice + chunk (mod
+        // kTcSplit), so the same atom at consecutive angles (consecutive
+        // chunks when a chunk is one angle; columns N/2 apart in a paired
+        // chunk) lands in different slices: plain rows hc*S .. + S - 1 of the
+        // chunk (S = N / kTcSplit); paired: pairs hc*S .. + S - 1, their even
+        // parts in columns 0..N-1 and odd parts in N..2N-1
+        const int hc = (slice + c) & (kTcSplit - 1);
+        const uint32_t taddr = tmem + lane_base + b * kSBufC + (uint32_t)(hc * Sh::SLICE);
+        const int nvalid = min(N, a.MR - c * N) - hc * Sh::SLICE;
 #pragma unroll 1
         for (int piece = 0; piece < Sh::PIECES; ++piece) {
           const int nv = nvalid - piece * 32;  // valid columns of this block
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
             const int sl = cnt & (kRing - 1);
             if (cnt >= kRing) lost = fmaxf(lost, rv[sl]);
             rv[sl] = bm;
-            ri[sl] = c * N + hc * Sh::HALF + piece * 32;
+            ri[sl] = c * N + hc * Sh::SLICE + piece * 32;
             ++cnt;
           }
           rbest = fmaxf(rbest, bm);
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       }
       if (!ok) break;
       if (act) {
-        // Every unit of this half with value >= thr = best - win lies in a
+        // Every unit of this slice with value >= thr = best - win lies in a
         // block of the ring with maximum >= thr and in a class with
         // cmax >= thr: the refine expands (kept blocks) x (class mask).  What
         // is left out is below thr, or a block the list or the ring dropped
@@ -349,14 +352,15 @@ __global__ void __launch_bounds__(kSThreads, 1)
             ubest = u;
           }
         }
-        // this half's entries [half * kTcTop, half * kTcTop + kTcTop) of the
-        // patch's kTcCand block slots, its class mask and best class
-        int *ci = a.cand_idx + p * kTcCand + half * kTcTop;
-        float *cv = a.cand_val + p * kTcCand + half * kTcTop;
+        // this slice's entries [slice * kTcTop, slice * kTcTop + kTcTop) of
+        // the patch's kTcCand block slots, its class mask and best class
+        int *ci = a.cand_idx + p * kTcCand + slice * kTcTop;
+        float *cv = a.cand_val + p * kTcCand + slice * kTcTop;
         *reinterpret_cast<int4 *>(ci) = make_int4(ti[0], ti[1], ti[2], ti[3]);
         *reinterpret_cast<float4 *>(cv) = make_float4(tv[0], tv[1], tv[2], tv[3]);
-        a.cand_disc[p * 2 + half] = disc;
-        *reinterpret_cast<uint2 *>(a.cand_mask + p * 4 + half * 2) = make_uint2(um, (uint32_t)ubest);
+        a.cand_disc[p * kTcSplit + slice] = disc;
+        *reinterpret_cast<uint2 *>(a.cand_mask + p * 2 * kTcSplit + slice * 2) =
+            make_uint2(um, (uint32_t)ubest);
       }
     }
   }

@@ -318,10 +318,10 @@ size_t f16_scratch_bytes(int64_t P, int K, int L) {
   int nD = 0, nF = 0, nI = 0;
   rsc_state_layout(K, &nD, &nF, &nI);
   auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  return al256((size_t)P * L * 2) + 2 * al256((size_t)P * kTcCand * 4) + al256((size_t)P * 8) +
-         al256((size_t)P * 16) +
+  return al256((size_t)P * L * 2) + 2 * al256((size_t)P * kTcCand * 4) +
+         al256((size_t)P * kTcSplit * 4) + al256((size_t)P * kTcSplit * 8) +
          2 * al256((size_t)P * 4) + al256((size_t)nD * P * 8) + al256((size_t)nF * P * 4) +
-         al256((size_t)nI * P * 4) + al256((size_t)(P + 4) * 4);
+         al256((size_t)nI * P * 4) + 2 * al256((size_t)(P + 4) * 4);
 }
 
 // Enqueues the FP16 path for the patches of `a` on `st`: init, K x (scoring,
@@ -359,8 +359,8 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   ra.A = take((size_t)P * ra.L * 2);
   ra.cand_idx = reinterpret_cast<int *>(take((size_t)P * kTcCand * 4));
   ra.cand_val = reinterpret_cast<float *>(take((size_t)P * kTcCand * 4));
-  ra.cand_disc = reinterpret_cast<float *>(take((size_t)P * 8));
-  ra.cand_mask = reinterpret_cast<unsigned *>(take((size_t)P * 16));
+  ra.cand_disc = reinterpret_cast<float *>(take((size_t)P * kTcSplit * 4));
+  ra.cand_mask = reinterpret_cast<unsigned *>(take((size_t)P * kTcSplit * 8));
   ra.status = reinterpret_cast<int *>(take((size_t)P * 4));
   ra.win = reinterpret_cast<float *>(take((size_t)P * 4));
   ra.sD = reinterpret_cast<double *>(take((size_t)nD * P * 8));
@@ -369,6 +369,9 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   int *redo = reinterpret_cast<int *>(take((size_t)(P + 4) * 4));
   ra.redo_count = redo;
   ra.redo_list = redo + 4;
+  int *slow = reinterpret_cast<int *>(take((size_t)(P + 4) * 4));
+  ra.slow_count = slow;
+  ra.slow_list = slow + 4;
   ra.paired = dict->paired_f16 != nullptr ? 1 : 0;
   ra.atom = base.atom;
   ra.angle_idx = base.angle_idx;

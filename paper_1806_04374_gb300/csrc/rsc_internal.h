@@ -158,19 +158,22 @@ int rsc_basis_internals(const rsc_basis *basis, rsc_basis_view *view);
 
 // Candidates kept per patch and greedy step by the tensor-core scoring:
 // kTcTop per list (the fused kernel: block maxima; the split scoring pass:
-// blocks of 32 rows within the window, one list per half of the accumulator
-// columns, kTcCand in all, expanded by a class mask, see ScoreArgs).
+// blocks of 32 rows within the window, one list per slice of the accumulator
+// columns, kTcSplit slices, kTcCand in all, expanded by a class mask, see
+// ScoreArgs).
 constexpr int kTcTop = 4;
-constexpr int kTcCand = 2 * kTcTop;
+constexpr int kTcSplit = 2;
+constexpr int kTcCand = kTcSplit * kTcTop;
 
 // One scoring pass of the split FP16 path (romp_score.cu): packed fp16
 // residual rows (TMA map tmA: [P][kTcKst]) times the steered dictionary
-// (tmB) -> per patch and half of each chunk's rows: up to kTcTop blocks of 32
-// rows (first row b, multiple of 32; rows b + u, u < 32) whose maximum |score|
-// lies within the window of the half's best, their maxima, the mask of the
-// columns u whose largest value over all blocks of the half lies within it,
-// the column of the half's best value, and a bound on every value left out.
-// Every row within the window is b + u for a kept b and a masked u.
+// (tmB) -> per patch and slice (kTcSplit per chunk of rows): up to kTcTop
+// blocks of 32 rows (first row b, multiple of 32; rows b + u, u < 32) whose
+// maximum |score| lies within the window of the slice's best, their maxima,
+// the mask of the columns u whose largest value over all blocks of the slice
+// lies within it, the column of the slice's best value, and a bound on every
+// value left out.  Every row within the window is b + u for a kept b and a
+// masked u of the same slice.
 struct ScoreArgs {
   int64_t P;
   int ksteps, MR, nchunks;
@@ -181,8 +184,8 @@ struct ScoreArgs {
   const int *status;  // > 0: patch still being coded
   int *cand_idx;      // [P][kTcCand] first rows of the kept blocks (-1: none)
   float *cand_val;    // [P][kTcCand] their maxima (accumulator units)
-  float *cand_disc;   // [P][2] bound on the values each half left out
-  unsigned *cand_mask;  // [P][4] per half: column mask, column of the half's best
+  float *cand_disc;   // [P][kTcSplit] bound on the values each slice left out
+  unsigned *cand_mask;  // [P][2 kTcSplit] per slice: column mask, column of its best
   // [P] per-patch certification window in accumulator units (written by the
   // refine pass with the row): a block maximum more than `win` below the
   // running best can neither win nor reach the window, so it is not kept
@@ -221,6 +224,10 @@ struct RefineArgs {
   float *resid_norm2;
   int *redo_list;
   int *redo_count;
+  // [P] + counter: patches whose window holds more than one unit, finished by
+  // the refine's second pass (see romp_refine.cu)
+  int *slow_list;
+  int *slow_count;
   unsigned long long *fallbacks;
 };
 int rsc_launch_refine(const RefineArgs &a, bool init, cudaStream_t stream);
