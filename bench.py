@@ -544,82 +544,89 @@ def run_c2(args) -> None:
     basis.close()
 
 
+SERVE_DIMS = dict(N=11, J=6, kmax=8, M=128, R=64, K=5)
+
+
+def serving_pool(n: int, seed: int = 20180620):
+    """Request images of the serving workload: n square line textures
+    (synth.make_line_image) of side U{128..1024}."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(128, 1025, size=n)
+    return [synth.make_line_image(int(s_), int(s_), 0.01, seed + i) for i, s_ in enumerate(sides)]
+
+
+def offered(srv, pool, arrivals, which):
+    """Submits pool[which[i]] at arrivals[i] seconds after the start (host
+    clock) and waits for every request; returns the requests."""
+    t0 = time.perf_counter()
+    reqs = []
+    for a_, q in zip(arrivals, which):
+        dt = t0 + a_ - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        reqs.append(srv.submit(pool[q]))
+    for r in reqs:
+        r.wait()
+    return reqs
+
+
+def measure_serving(rsc, torch, dev, rates, seconds: float, n_pool: int,
+                    mem_budget: int = 16 << 30, slots: int = 3) -> dict:
+    """The serving workload through serve.Server: requests are images of side
+    U{128..1024} coded at 11 x 11 (J = 6, kmax = 8) with a resident dictionary
+    of M = 128 atoms, R = 64, K = 5, FP16 path, codes copied to the host.
+    Runs: every pool image at t = 0 (capacity), then Poisson arrivals at each
+    rate for `seconds`.  Latency = completion - submission (host clock)."""
+    from paper_1806_04374_gb300 import serve
+    dm = SERVE_DIMS
+    basis = rsc.Basis(dm["N"], dm["J"], dm["kmax"])
+    dic = rsc.Dictionary(torch.from_numpy(
+        synth.make_dictionary(dm["M"], dm["J"], dm["kmax"], 20180619)).to(dev), dm["R"])
+    pool = serving_pool(n_pool)
+    windows = [(im.shape[0] - dm["N"] + 1) * (im.shape[1] - dm["N"] + 1) for im in pool]
+    rng = np.random.default_rng(20180623)
+    runs = []
+    with serve.Server(dic, basis, dm["K"], "f16", mem_budget=mem_budget, slots=slots) as srv:
+        for r in [srv.submit(pool[0]), srv.submit(pool[1])]:  # warm-up
+            r.result()
+        rsc.rsc_dict_fallback_count(dic.handle)
+        cap = serve.latency_summary(offered(srv, pool, np.zeros(n_pool), np.arange(n_pool)))
+        cap["arrivals"] = f"all {n_pool} pool images at t = 0 (capacity)"
+        runs.append(cap)
+        for rate in rates:
+            n = max(8, int(rate * seconds))
+            arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
+            reqs = offered(srv, pool, arr, rng.integers(0, n_pool, size=n))
+            run = serve.latency_summary(reqs)
+            run["arrivals"] = f"Poisson {rate:g} req/s for {seconds:g} s"
+            run["offered_windows_per_s"] = rate * float(np.mean(windows))
+            runs.append(run)
+        handoffs = rsc.rsc_dict_fallback_count(dic.handle)
+        peak = srv.peak_reserved
+    dic.close()
+    basis.close()
+    return {"metric": "request latency p50/p99 and sustained patches/s (continuous batching)",
+            "config": {"workload": "images side U{128..1024} (line textures), 11x11 windows "
+                                   "(97 px), J=6, kmax=8, M=128, R=64, K=5, f16; codes copied "
+                                   "to the host",
+                       "server": f"serve.Server: {slots} slots (streams), device-memory budget "
+                                 f"{mem_budget >> 30} GiB, batches up to 2^20 windows",
+                       "pool_images": n_pool},
+            "capacity_windows_per_s": runs[0]["windows_per_s"],
+            "nominal_offered_200_req_per_s": 200 * float(np.mean(windows)),
+            "peak_reserved_bytes": peak, "handoffs": handoffs, "runs": runs}
+
+
 def run_serving(args) -> None:
-    """Serving loop of the request workload: images of side ~ U{128..1024}
-    (square line textures, synth.make_line_image), 11 x 11 patches, M = 128
-    resident atoms, R = 64, K = 5, FP16 path; requests arrive as a Poisson
-    process; the server takes every request that has arrived (up to
-    `--serve-batch` patches) into one rsc_encode_images call and copies the codes back to the host.  Latency =
-    host-visible completion - arrival.  Runs: all requests at t = 0
-    (capacity), then Poisson arrivals at each rate of `--rates`."""
+    """`--serve`: the serving measurement alone, longer runs."""
     import torch
     import paper_1806_04374_gb300 as rsc
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     rsc.load_library()
-    N, J, kmax, M, R, K = 11, 6, 8, 128, 64, 5
-    basis = rsc.Basis(N, J, kmax)
-    dic = rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180619)).to(dev), R)
-    rng = np.random.default_rng(20180620)
-    sides = rng.integers(128, 1025, size=64)
-    pool = [torch.from_numpy(synth.make_line_image(int(s_), int(s_), 0.01, 20180620 + i)).to(dev)
-            for i, s_ in enumerate(sides)]
-    windows = [(int(s_) - N + 1) ** 2 for s_ in sides]
-
-    def serve(arrivals, which):
-        n = len(arrivals)
-        lat = np.zeros(n)
-        i, t0 = 0, time.perf_counter()
-        calls = 0
-        while i < n:
-            now = time.perf_counter() - t0
-            if arrivals[i] > now:
-                time.sleep(min(arrivals[i] - now, 0.01))
-                continue
-            j, P = i, 0
-            while j < n and arrivals[j] <= now and (P == 0 or P + windows[which[j]] <= args.serve_batch):
-                P += windows[which[j]]
-                j += 1
-            out = rsc.encode_images(dic, basis, [pool[q] for q in which[i:j]], K, "f16")
-            host = {k: v.cpu() for k, v in out.items()}
-            del host, out
-            done = time.perf_counter() - t0
-            lat[i:j] = done - arrivals[i:j]
-            calls += 1
-            i = j
-        total = sum(windows[q] for q in which)
-        return {"requests": n, "patches": int(total), "calls": calls,
-                "handoffs": rsc.rsc_dict_fallback_count(dic.handle),
-                "wall_s": done, "patches_per_s": total / done,
-                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99))}
-
-    # warm-up
-    serve(np.zeros(4), rng.integers(0, 64, size=4))
-    rsc.rsc_dict_fallback_count(dic.handle)
-    runs = []
-    nreq = max(16, int(args.serve_requests))
-    which = rng.integers(0, 64, size=nreq)
-    cap = serve(np.zeros(nreq), which)
-    cap["arrivals"] = "all at t = 0 (capacity)"
-    runs.append(cap)
-    mean_windows = float(np.mean(windows))
-    for rate in args.rates:
-        n = max(16, int(rate * args.serve_seconds))
-        arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
-        r = serve(arr, rng.integers(0, 64, size=n))
-        r["arrivals"] = f"Poisson {rate:g} req/s for {args.serve_seconds:g} s"
-        r["offered_patches_per_s"] = rate * mean_windows
-        runs.append(r)
-    dic.close()
-    basis.close()
-    print(json.dumps({
-        "metric": "request latency p50/p99 and sustained patches/s (serving loop)",
-        "unit": "ms / patches/s", "n_gpus": 1, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": "images side U{128..1024}, 11x11 patches (97 px), J=6, kmax=8, "
-                               "M=128, R=64, K=5; codes copied to the host",
-                   "batch_cap_patches": args.serve_batch},
-        "runs": runs}))
+    res = measure_serving(rsc, torch, dev, args.rates, args.serve_seconds, args.serve_pool)
+    res.update({"unit": "ms / patches/s", "n_gpus": 1, "dtype": "f16", "data": "synthetic"})
+    print(json.dumps(res))
 
 
 def main():
@@ -639,8 +646,7 @@ def main():
                     help="run the request-serving loop instead of the throughput bench")
     ap.add_argument("--rates", type=float, nargs="*", default=[200.0, 50.0])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-batch", type=int, default=4_000_000)
+    ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--c2", action="store_true",
                     help="code the full 21x21-patch image workload once instead")
     ap.add_argument("--c2-images", type=int, default=512,
@@ -906,6 +912,12 @@ def main():
             line["images_c2_sizes"] = measure_images_c2(rsc, torch, dev)
             line["roundtrip"] = measure_roundtrip(rsc, torch, dev, stream, dic, out)
             line["classify"] = measure_classify(rsc, torch, dev)
+            line["serving"] = measure_serving(rsc, torch, dev, rates=[200.0, 50.0], seconds=3.0,
+                                              n_pool=24)
+            line["latency_ms"]["requests"] = {
+                k: {"p50": r["p50_ms"], "p99": r["p99_ms"], "arrivals": r["arrivals"]}
+                for k, r in zip(("capacity", "poisson_200", "poisson_50"),
+                                line["serving"]["runs"])}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(d, x, wl, parity_outputs=parity_outputs)
             # the timed outputs against the oracle, on the same sample

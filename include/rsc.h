@@ -235,6 +235,20 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *basis, const float 
                       double *coef, float *resid_norm2, void *stream);
 
 /*
+ * rsc_workspace_bytes -- device memory that one rsc_encode (basis = NULL) or
+ * rsc_encode_images (basis given; P = the windows of its n_images images)
+ * call takes from the stream-ordered allocator for its own scratch while it
+ * runs, for P patches, K steps and precision prec.  The paper has no
+ * counterpart: a server uses it to admit requests by the device memory they
+ * need (inputs and outputs, which the caller allocates, come on top).
+ *   bytes : HOST, receives the count (0 when the call needs no scratch).
+ *   RSC_ERR_INVALID for null handles or pointers, P < 0, n_images < 0, K
+ *   outside 1..16 or an unknown precision.  Touches no device memory.
+ */
+int rsc_workspace_bytes(const rsc_dict *dict, const rsc_basis *basis, int64_t P, int32_t n_images,
+                        int32_t K, int32_t prec, uint64_t *bytes);
+
+/*
  * rsc_classify_images -- the coding stage of the paper's texture classifier
  * (Sec. III-B): every stride-1 window of each image is projected once and
  * coded with each of C dictionaries (one learned per class); its label is

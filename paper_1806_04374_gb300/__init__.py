@@ -33,7 +33,7 @@ EXPORTS = (
     "rsc_status_string", "rsc_last_cuda_error", "rsc_version", "rsc_encode_noalloc",
     "rsc_ksvd_update", "rsc_basis_create", "rsc_basis_destroy", "rsc_basis_info", "rsc_project",
     "rsc_encode_images", "rsc_ksvd_accumulate", "rsc_ksvd_finish", "rsc_reconstruct",
-    "rsc_synthesize", "rsc_classify_images",
+    "rsc_synthesize", "rsc_classify_images", "rsc_workspace_bytes",
 )
 
 
@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                         vp, vp, vp]
     lib.rsc_encode_images.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(i32),
                                       ctypes.POINTER(i32), i32, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.rsc_workspace_bytes.argtypes = [vp, vp, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.rsc_workspace_bytes.restype = ctypes.c_int
     lib.rsc_dict_check.argtypes = [vp, vp]
     lib.rsc_dict_fallback_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.rsc_dict_set_timing.argtypes = [vp, ctypes.c_int]
@@ -164,6 +166,18 @@ def rsc_ksvd_update(handle: int, x_ptr: int, P: int, K: int, atom_ptr: int, angl
     return load_library().rsc_ksvd_update(vp(handle), vp(x_ptr), int(P), int(K), vp(atom_ptr),
                                           vp(angle_idx_ptr), vp(coef_ptr), vp(new_coef_ptr),
                                           vp(n_used_ptr or None), vp(stream))
+
+
+def rsc_workspace_bytes(handle: int, basis_handle, P: int, n_images: int, K: int, prec: int) -> int:
+    """Device scratch (bytes) one rsc_encode (basis_handle None) or
+    rsc_encode_images call on P patches takes; raises RscError."""
+    v = ctypes.c_uint64()
+    st = load_library().rsc_workspace_bytes(ctypes.c_void_p(handle),
+                                            ctypes.c_void_p(basis_handle or None), int(P),
+                                            int(n_images), int(K), int(prec), ctypes.byref(v))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_workspace_bytes")
+    return v.value
 
 
 def rsc_dict_check(handle: int, stream: int = 0) -> int:

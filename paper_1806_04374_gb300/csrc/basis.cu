@@ -1150,6 +1150,15 @@ int rsc_classify_images(const rsc_dict *const *dicts, int32_t C, const rsc_basis
 
 }  // extern "C"
 
+int rsc_images_scratch_bytes(const rsc_basis *b, int64_t P, int32_t n_images, uint64_t *bytes) {
+  if (!b || !bytes || P < 0 || n_images < 0) return RSC_ERR_INVALID;
+  // as rsc_encode_images takes it: the work list (256-byte aligned), then the
+  // projected windows
+  const uint64_t bI = ((uint64_t)n_images * sizeof(ImageItem) + 255) & ~(uint64_t)255;
+  *bytes = P > 0 ? bI + (uint64_t)P * b->nout * 4 : 0;
+  return RSC_OK;
+}
+
 int rsc_basis_internals(const rsc_basis *b, rsc_basis_view *v) {
   if (!b || !v) return RSC_ERR_INVALID;
   *v = rsc_basis_view{b->device, b->npix, b->n, b->J, b->nout, b->Xs};

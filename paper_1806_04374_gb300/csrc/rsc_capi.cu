@@ -313,6 +313,10 @@ int check_device(const rsc_dict *d) {
 constexpr int kMaxGroups = 2;
 constexpr int64_t kGroupMin = 65536;
 
+// Splits P patches of the FP16 path into G groups (one stream each); returns G
+// and fills Pg[] and the scratch bytes of each group.
+int f16_groups(const rsc_dict *dict, int64_t P, int K, int64_t Pg[], size_t bytes[]);
+
 // Scratch of the FP16 path for P patches and K steps (256-byte aligned parts).
 size_t f16_scratch_bytes(int64_t P, int K, int L) {
   int nD = 0, nF = 0, nI = 0;
@@ -322,6 +326,19 @@ size_t f16_scratch_bytes(int64_t P, int K, int L) {
          al256((size_t)P * kTcSplit * 4) + al256((size_t)P * kTcSplit * 8) +
          2 * al256((size_t)P * 4) + al256((size_t)nD * P * 8) + al256((size_t)nF * P * 4) +
          al256((size_t)nI * P * 4) + 2 * al256((size_t)(P + 4) * 4);
+}
+
+int f16_groups(const rsc_dict *dict, int64_t P, int K, int64_t Pg[], size_t bytes[]) {
+  int G = (int)(P / kGroupMin);
+  G = G < 1 ? 1 : (G > kMaxGroups ? kMaxGroups : G);
+  if (dict->timing == 2) G = 1;  // timing of each kernel alone
+  int64_t done = 0;
+  for (int g = 0, left = G; g < G; ++g, --left) {
+    Pg[g] = left == 1 ? P - done : (((P - done) / left + 255) & ~(int64_t)255);
+    bytes[g] = f16_scratch_bytes(Pg[g], K, dict->row_len);
+    done += Pg[g];
+  }
+  return G;
 }
 
 // Enqueues the FP16 path for the patches of `a` on `st`: init, K x (scoring,
@@ -612,21 +629,10 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   // Independent groups of patches on their own streams: the scoring pass of
   // one group (tensor and ALU pipes, one CTA per SM) runs beside the refine
   // pass of another (latency-bound), so each hides part of the other.
-  int G = (int)(P / kGroupMin);
-  G = G < 1 ? 1 : (G > kMaxGroups ? kMaxGroups : G);
-  if (dict->timing == 2) G = 1;  // timing of each kernel alone
   int64_t Pg[kMaxGroups] = {};
   size_t bytes[kMaxGroups] = {}, total = 0;
-  for (int g = 0, left = G; g < G; ++g, --left) {
-    const int64_t done = [&] {
-      int64_t v = 0;
-      for (int h = 0; h < g; ++h) v += Pg[h];
-      return v;
-    }();
-    Pg[g] = left == 1 ? P - done : (((P - done) / left + 255) & ~(int64_t)255);
-    bytes[g] = f16_scratch_bytes(Pg[g], K, dict->row_len);
-    total += bytes[g];
-  }
+  const int G = f16_groups(dict, P, K, Pg, bytes);
+  for (int g = 0; g < G; ++g) total += bytes[g];
   unsigned char *scratch = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
   if (e == cudaErrorMemoryAllocation) {
@@ -678,6 +684,27 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   e = cudaFreeAsync(scratch, st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
   return rc;
+}
+
+int rsc_workspace_bytes(const rsc_dict *dict, const rsc_basis *basis, int64_t P, int32_t n_images,
+                        int32_t K, int32_t prec, uint64_t *bytes) {
+  if (!dict || !bytes || P < 0 || n_images < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
+  uint64_t total = 0;
+  if (P > 0 && prec == RSC_F16_RESCORE) {
+    int64_t Pg[kMaxGroups] = {};
+    size_t b[kMaxGroups] = {};
+    const int G = f16_groups(dict, P, K, Pg, b);
+    for (int g = 0; g < G; ++g) total += b[g];
+  }
+  if (basis && P > 0) {
+    uint64_t img = 0;
+    const int rc = rsc_images_scratch_bytes(basis, P, n_images, &img);
+    if (rc != RSC_OK) return rc;
+    total += img;
+  }
+  *bytes = total;
+  return RSC_OK;
 }
 
 int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,

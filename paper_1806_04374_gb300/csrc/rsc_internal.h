@@ -155,6 +155,9 @@ struct rsc_basis_view {
   const float *X;  // device [n][npix]: real synthesis matrix, packed column order
 };
 int rsc_basis_internals(const rsc_basis *basis, rsc_basis_view *view);
+// Scratch bytes rsc_encode_images takes for its work list and projected
+// windows (basis.cu).
+int rsc_images_scratch_bytes(const rsc_basis *basis, int64_t P, int32_t n_images, uint64_t *bytes);
 
 // Candidates kept per patch and greedy step by the tensor-core scoring:
 // kTcTop per list (the fused kernel: block maxima; the split scoring pass:

@@ -65,3 +65,13 @@ def test_way_back_and_classifier_reject_bad_arguments(lib):
                                    None) == inv
     assert lib.rsc_classify_images(one, 1, None, None, None, None, 0, 0, 0, None, None,
                                    None) == inv
+
+
+def test_workspace_query_argument_checks(lib):
+    import paper_1806_04374_gb300 as rsc
+    out = ctypes.c_uint64()
+    vp = ctypes.c_void_p
+    assert lib.rsc_workspace_bytes(vp(None), vp(None), 10, 1, 5, rsc.RSC_F16_RESCORE,
+                                   ctypes.byref(out)) == rsc.RSC_ERR_INVALID
+    with pytest.raises(rsc.RscError):
+        rsc.rsc_workspace_bytes(0, None, 10, 1, 5, rsc.RSC_FP32)
