@@ -356,6 +356,21 @@ int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t P, int32_t 
  */
 int rsc_dict_check(const rsc_dict *dict, void *stream);
 
+/*
+ * rsc_dict_set_limits -- diagnostic limits on `dict`, for testing the error
+ * paths (a property of this library; the paper has no counterpart).
+ *   pipeline_wait_ns : limit of the waits between the FP16 scoring kernel's
+ *            producer, MMA and epilogue warps; a wait that runs out records
+ *            RSC_ERR_TIMEOUT (reported by rsc_dict_check), stops the kernel's
+ *            loops and drains what it issued (those waits keep the default 2 s).
+ *            The outputs of an rsc_encode that ran into it are undefined.
+ *            0 = the default, 2 s.
+ *   scratch_limit : largest per-call scratch (bytes) the FP16 path may take;
+ *            a call that needs more returns RSC_ERR_OOM before any device
+ *            work, as if the allocator had refused.  0 = no limit.
+ */
+int rsc_dict_set_limits(rsc_dict *dict, uint64_t pipeline_wait_ns, uint64_t scratch_limit);
+
 /* Diagnostic count since the last call (resets): on the FP32 path, the
  * patch-steps in which a lane discarded a candidate inside the error bound,
  * so that the step was decided by an exact re-scan of all M*R candidates; on

@@ -33,7 +33,7 @@ EXPORTS = (
     "rsc_status_string", "rsc_last_cuda_error", "rsc_version", "rsc_encode_noalloc",
     "rsc_ksvd_update", "rsc_basis_create", "rsc_basis_destroy", "rsc_basis_info", "rsc_project",
     "rsc_encode_images", "rsc_ksvd_accumulate", "rsc_ksvd_finish", "rsc_reconstruct",
-    "rsc_synthesize", "rsc_classify_images", "rsc_workspace_bytes",
+    "rsc_synthesize", "rsc_classify_images", "rsc_workspace_bytes", "rsc_dict_set_limits",
 )
 
 
@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_dict_check.argtypes = [vp, vp]
     lib.rsc_dict_fallback_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.rsc_dict_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.rsc_dict_set_limits.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64]
+    lib.rsc_dict_set_limits.restype = ctypes.c_int
     lib.rsc_dict_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.rsc_status_string.argtypes = [ctypes.c_int]
     lib.rsc_status_string.restype = ctypes.c_char_p
@@ -196,6 +198,13 @@ def rsc_dict_set_timing(handle: int, enable) -> int:
     """enable: False/0 off, True/1 on, 2 on with the FP16 path's halves run
     one after the other (each kernel timed alone)."""
     return load_library().rsc_dict_set_timing(ctypes.c_void_p(handle), int(enable))
+
+
+def rsc_dict_set_limits(handle: int, pipeline_wait_ns: int = 0, scratch_limit: int = 0) -> int:
+    """Diagnostic limits for testing the error paths (0 = default): the FP16
+    scoring kernel's pipeline wait limit and the FP16 path's scratch budget."""
+    return load_library().rsc_dict_set_limits(ctypes.c_void_p(handle), int(pipeline_wait_ns),
+                                              int(scratch_limit))
 
 
 def rsc_dict_timing(handle: int):

@@ -371,7 +371,10 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
               }
           }
         }
-        const int uf = qf < 0 ? 0 : ubest_of(qf / kTcTop);
+        // (the masks' columns are < 32 by construction; the best column is
+        // masked too, so that candidates left undefined by a scoring pass that
+        // gave up cannot name a row outside the table)
+        const int uf = qf < 0 ? 0 : (ubest_of(qf / kTcTop) & 31);
         if (PASS == 1) {
           // units in the window: columns of the masks over the kept blocks
           int nunits = 0;
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
 #pragma unroll 1
         while (more) {
           const int id = cip[q] + u;
-          bool go = id < MR;
+          bool go = cip[q] >= 0 && cip[q] < MR && id < MR;
           const int m = id % M, r = id / M;
           if (PASS != 1 && kScreen && go && !first) {
             float f;

@@ -32,9 +32,11 @@
 //     expands blocks x classes.  Per value that is one add (paired), one max
 //     into its class and half a three-input max for its block, with no
 //     per-block branch; the slices never synchronise.
-// All hand-offs are mbarriers; every wait is bounded (2 s of globaltimer) and
-// a failed wait records RSC_ERR_TIMEOUT, stops the CTA's loops, drains the
-// copies and MMAs it issued, and frees its TMEM.
+// All hand-offs are mbarriers; every wait is bounded (2 s of globaltimer, or
+// a shorter limit for the pipeline waits set on the dictionary to test this
+// path) and a failed wait records RSC_ERR_TIMEOUT, stops the CTA's loops,
+// drains the copies and MMAs it issued (with the 2 s limit), and frees its
+// TMEM.
 #include "rsc_internal.h"
 #include "tc_common.cuh"
 #include "tc_ptx.cuh"
@@ -48,7 +50,7 @@ constexpr int kSBufC = 256;             // accumulator columns per TMEM buffer
 constexpr uint32_t kSCols = 2 * kSBufC; // two buffers: all 512 TMEM columns
 constexpr int kSEpi = 4 * kTcSplit;     // epilogue warps: 4 lane quarters x kTcSplit slices
 constexpr int kSThreads = 32 * (kSEpi + 2);  // + TMA warp + MMA warp
-constexpr uint64_t kSWaitNs = 2000000000ull;
+constexpr uint64_t kSWaitNs = 2000000000ull;  // drain waits (and the default pipeline limit)
 constexpr int kRing = 16;               // blocks near the running best kept per step
 
 // Shape of one instantiation: NB 64-column blocks per packed row (2 for rows
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       for (int64_t tile = blockIdx.x; ok && tile < ntiles && !*s_abort; tile += gridDim.x, ++it) {
         const int ab = (int)(it % kABufs);
         const uint32_t ua = it / kABufs;
-        if (ua > 0 && !tc::mbar_wait_bounded(bar(kBarAEmpty + ab), (ua - 1) & 1, kSWaitNs)) {
+        if (ua > 0 && !tc::mbar_wait_bounded(bar(kBarAEmpty + ab), (ua - 1) & 1, a.wait_ns)) {
           fail();
           break;
         }
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
           for (int j = 0; j < NKB; ++j, ++gs) {
             const int s = (int)(gs % kStages);
             if (gs >= (uint32_t)kStages &&
-                !tc::mbar_wait_bounded(bar(kBarBEmpty + s), ((gs / kStages) - 1) & 1, kSWaitNs)) {
+                !tc::mbar_wait_bounded(bar(kBarBEmpty + s), ((gs / kStages) - 1) & 1, a.wait_ns)) {
               fail();
               ok = false;
               break;
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       for (int64_t tile = blockIdx.x; ok && tile < ntiles && !*s_abort; tile += gridDim.x, ++it) {
         const int ab = (int)(it % kABufs);
         const uint32_t ua = it / kABufs;
-        if (!tc::mbar_wait_bounded(bar(kBarAFull + ab), ua & 1, kSWaitNs)) {
+        if (!tc::mbar_wait_bounded(bar(kBarAFull + ab), ua & 1, a.wait_ns)) {
           fail();
           break;
         }
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
         const uint32_t a0 = tc::smem_u32(sA + ab * Sh::kATile);
         for (int c = 0; c < nch; ++c, ++g) {
           const uint32_t b = g & 1, ub = g >> 1;
-          if (ub > 0 && !tc::mbar_wait_bounded(bar(kBarAccEmpty + b), (ub - 1) & 1, kSWaitNs)) {
+          if (ub > 0 && !tc::mbar_wait_bounded(bar(kBarAccEmpty + b), (ub - 1) & 1, a.wait_ns)) {
             ok = false;
             break;
           }
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
           const uint32_t d = tmem + b * kSBufC;
           for (int j = 0; j < NKB; ++j, ++gs) {
             const int s = (int)(gs % kStages);
-            if (!tc::mbar_wait_bounded(bar(kBarBFull + s), (gs / kStages) & 1, kSWaitNs)) {
+            if (!tc::mbar_wait_bounded(bar(kBarBFull + s), (gs / kStages) & 1, a.wait_ns)) {
               ok = false;
               break;
             }
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       int cnt = 0;
       for (int c = 0; c < nch; ++c, ++g) {
         const uint32_t b = g & 1, ub = g >> 1;
-        const bool done = !*s_abort && tc::mbar_wait_bounded(bar(kBarAccFull + b), ub & 1, kSWaitNs);
+        const bool done = !*s_abort && tc::mbar_wait_bounded(bar(kBarAccFull + b), ub & 1, a.wait_ns);
         if (!__all_sync(0xffffffffu, done)) {
           if (lane == 0) fail();
           ok = false;

@@ -414,6 +414,7 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   sa.cand_mask = const_cast<unsigned *>(ra.cand_mask);
   sa.win = ra.win;
   sa.err = dict->err;
+  sa.wait_ns = dict->wait_ns ? dict->wait_ns : 2000000000ull;
   CUtensorMap tmA;
   int rc = encode_rows_map(&tmA, ra.A, (size_t)P, kTcBN, ra.L);
   if (rc == RSC_OK) {
@@ -633,6 +634,9 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   size_t bytes[kMaxGroups] = {}, total = 0;
   const int G = f16_groups(dict, P, K, Pg, bytes);
   for (int g = 0; g < G; ++g) total += bytes[g];
+  // a scratch budget set on the dictionary stands in for the allocator's
+  // refusal (testing the error path without exhausting device memory)
+  if (dict->scratch_limit && total > dict->scratch_limit) return RSC_ERR_OOM;
   unsigned char *scratch = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
   if (e == cudaErrorMemoryAllocation) {
@@ -775,6 +779,13 @@ int rsc_dict_check(const rsc_dict *dict, void *stream) {
   if (e == cudaSuccess) e = cudaMemset(dict->err, 0, sizeof(int));
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return v;
+}
+
+int rsc_dict_set_limits(rsc_dict *dict, uint64_t pipeline_wait_ns, uint64_t scratch_limit) {
+  if (!dict) return RSC_ERR_INVALID;
+  dict->wait_ns = pipeline_wait_ns;
+  dict->scratch_limit = scratch_limit;
+  return RSC_OK;
 }
 
 int rsc_dict_set_timing(rsc_dict *dict, int enable) {

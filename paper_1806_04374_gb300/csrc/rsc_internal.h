@@ -46,6 +46,11 @@ struct rsc_dict {
   // device buffers and streams of rsc_encode_host (rsc_capi.cu), made on its
   // first call and kept until rsc_dict_destroy
   mutable void *host_stage;
+  // diagnostic limits (rsc_dict_set_limits; 0 = default): the wait limit of
+  // the FP16 scoring kernel's pipeline waits (ns) and a budget for the FP16
+  // path's per-call scratch (bytes)
+  uint64_t wait_ns;
+  uint64_t scratch_limit;
 };
 
 // Packed real coordinates of a half spectrum, shared by the tensor-core
@@ -194,6 +199,9 @@ struct ScoreArgs {
   // running best can neither win nor reach the window, so it is not kept
   const float *win;
   int *err;
+  // limit of the pipeline waits (ns); the waits that drain issued copies and
+  // MMAs before the CTA exits keep their own limit
+  uint64_t wait_ns;
 };
 int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
                      cudaStream_t stream);

@@ -75,3 +75,4 @@ def test_workspace_query_argument_checks(lib):
                                    ctypes.byref(out)) == rsc.RSC_ERR_INVALID
     with pytest.raises(rsc.RscError):
         rsc.rsc_workspace_bytes(0, None, 10, 1, 5, rsc.RSC_FP32)
+    assert lib.rsc_dict_set_limits(vp(None), 1, 1) == rsc.RSC_ERR_INVALID
