@@ -13,21 +13,28 @@
 // descending error for several, ties: smaller index); the eigenvector's
 // largest-magnitude packed entry is made positive.
 //
-// Kernels: per patch (count samples per atom, fill the per-atom sample lists,
-// packed FP32 residuals and coding errors); per atom kCovSplit CTAs
-// accumulating C_m over slices of its samples (4 x 4 register tiles, FP32
-// partial sums over 32 samples folded into FP64, FP64 atomics) and one CTA
-// running an FP64 power iteration from the old atom; one CTA for the resets.  All
-// vectors are packed reals (k = 0 real parts, sqrt(2) Re/Im of k >= 1).
+// Kernels: per chunk of patches (count samples per atom; then the per-atom
+// sample lists in patch order and the packed residuals in double-float); per
+// atom kCovSplit CTAs accumulating partial sums of C_m over slices of its
+// samples (4 x 4 register tiles; the columns y in double-float, each product
+// y_i y_j as an exact FP32 product plus its cross terms, summed Dot2-style
+// over 32 samples and folded into FP64), then the kCovSplit partials added in
+// a fixed order, so that the update is FP64-grade and the same on every run;
+// one CTA per atom running an FP64 power iteration from the old atom; one CTA
+// for the resets.  All vectors are packed reals (k = 0 real parts, sqrt(2)
+// Re/Im of k >= 1).
 #include <math.h>
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "rsc_internal.h"
 
 namespace {
 
-constexpr int kCovThreads = 256;
+constexpr int kCovThreads = 384;  // one 4 x 4 tile each: all 351 tiles of n = 102 in one round
+constexpr int kFillChunk = 256;   // patches per chunk of the sample lists
+constexpr int kMaxAtomsKsvd = 12288;  // per-atom cursors of a chunk in shared memory
 constexpr int kCovBatch = 32;
 constexpr int kEigThreads = 256;
 constexpr int kMaxPacked = 2 * kMaxEntries;
@@ -41,13 +48,16 @@ struct KsvdArgs {
   const int32_t *atom;
   const int32_t *angle;
   const double *coef;
-  float *E;         // [P][ldE] packed residuals
+  float *E;         // [2][P][ldE] packed residuals, double-float (hi plane, lo plane)
   float *err;       // [P]
   int *count;       // [M]
   int *offset;      // [M + 1]
-  int *cursor;      // [M]
-  int2 *samples;    // [sum count] (patch, occurrence)
+  int *chunk_cnt;   // [nchunk][M] samples of each atom in each chunk of patches
+  int *chunk_base;  // [nchunk][M] first slot of each atom's samples of each chunk
+  int nchunk;
+  int2 *samples;    // [sum count] (patch, occurrence), patch order within an atom
   double *C;        // [M][n][n]
+  double *Cpart;    // [kCovSplit][M][n][n] partial sums (every entry written)
   float *new_coef;  // [M][H][J][2]
   int32_t *n_used;  // [M] or null
   // the patches of largest coding error (descending, ties: smaller index),
@@ -75,86 +85,148 @@ __device__ __forceinline__ bool chosen(const KsvdArgs &a, int64_t p, int i) {
   return true;
 }
 
-__global__ void ksvd_count_kernel(const KsvdArgs a) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
-       p += (int64_t)gridDim.x * blockDim.x)
+// Samples of each atom in each chunk of kFillChunk patches (shared-memory
+// histogram; integer counts do not depend on the order of the additions).
+__global__ void ksvd_chunk_count_kernel(const KsvdArgs a) {
+  extern __shared__ int hist[];  // [M]
+  for (int m = threadIdx.x; m < a.M; m += blockDim.x) hist[m] = 0;
+  __syncthreads();
+  const int64_t p0 = (int64_t)blockIdx.x * kFillChunk;
+  const int64_t p1 = min(a.P, p0 + kFillChunk);
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x)
     for (int i = 0; i < a.K; ++i)
-      if (chosen(a, p, i)) atomicAdd(&a.count[a.atom[p * a.K + i]], 1);
+      if (chosen(a, p, i)) atomicAdd(&hist[a.atom[p * a.K + i]], 1);
+  __syncthreads();
+  for (int m = threadIdx.x; m < a.M; m += blockDim.x)
+    a.chunk_cnt[(size_t)blockIdx.x * a.M + m] = hist[m];
 }
 
-__global__ void ksvd_scan_kernel(const KsvdArgs a) {
+// Per atom: its count, its first slot (offset, atoms in order) and the first
+// slot of its samples from each chunk (chunks in order).  One CTA.
+__global__ void ksvd_chunk_scan_kernel(const KsvdArgs a) {
+  for (int m = threadIdx.x; m < a.M; m += blockDim.x) {
+    int t = 0;
+    for (int c = 0; c < a.nchunk; ++c) t += a.chunk_cnt[(size_t)c * a.M + m];
+    a.count[m] = t;
+    if (a.n_used) a.n_used[m] = t;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int s = 0;
     for (int m = 0; m < a.M; ++m) {
       a.offset[m] = s;
-      a.cursor[m] = s;
       s += a.count[m];
-      if (a.n_used) a.n_used[m] = a.count[m];
     }
     a.offset[a.M] = s;
   }
+  __syncthreads();
+  for (int m = threadIdx.x; m < a.M; m += blockDim.x) {
+    int b = a.offset[m];
+    for (int c = 0; c < a.nchunk; ++c) {
+      a.chunk_base[(size_t)c * a.M + m] = b;
+      b += a.chunk_cnt[(size_t)c * a.M + m];
+    }
+  }
 }
 
-// Fills the sample lists and writes each patch's packed FP32 residual.
+// Per chunk: the packed residuals e_p = x_p - sum_i a_i S_{r_i} d_{m_i} of
+// its patches in double-float (one thread per patch; the weights are FP64,
+// the steering factors double-float) with their coding errors, and the
+// chunk's sample slots in patch order (one thread walks the chunk, so every
+// atom's list is in patch order on every run).
 __global__ void ksvd_fill_kernel(const KsvdArgs a) {
+  // [M] next slot of each atom in this chunk, then [kFillChunk][K] the atom
+  // of each chosen occurrence (-1: not chosen), filled in parallel
+  extern __shared__ int cur[];
+  int *occ = cur + a.M;
   const int J = a.J, H = a.H, HJ = H * J, R = a.R;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P;
-       p += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t p0 = (int64_t)blockIdx.x * kFillChunk;
+  const int64_t p1 = min(a.P, p0 + kFillChunk);
+  for (int m = threadIdx.x; m < a.M; m += blockDim.x)
+    cur[m] = a.chunk_base[(size_t)blockIdx.x * a.M + m];
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x)
     for (int i = 0; i < a.K; ++i)
-      if (chosen(a, p, i)) {
-        const int slot = atomicAdd(&a.cursor[a.atom[p * a.K + i]], 1);
-        a.samples[slot] = make_int2((int)p, i);
-      }
+      occ[(p - p0) * a.K + i] = chosen(a, p, i) ? a.atom[p * a.K + i] : -1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int n = (int)(p1 - p0) * a.K;
+    for (int w = 0; w < n; ++w) {
+      const int m = occ[w];
+      if (m >= 0) a.samples[cur[m]++] = make_int2((int)(p0 + w / a.K), w % a.K);
+    }
+  }
+  const df sqrt2 = df_from_d(1.4142135623730951);
+  const size_t plane = (size_t)a.P * a.ldE;
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     const float2 *xp = reinterpret_cast<const float2 *>(a.x + p * (int64_t)(2 * HJ));
-    float *ep = a.E + p * (int64_t)a.ldE;
-    float n2 = 0.0f;
+    float *eh = a.E + p * (int64_t)a.ldE;
+    float *el = eh + plane;
+    double n2 = 0.0;
     for (int e = 0; e < HJ; ++e) {
       const int k = e / J;
-      float2 v = xp[e];
-      float re = v.x, im = k ? v.y : 0.0f;
+      const float2 v = xp[e];
+      df re = df_make(v.x), im = df_make(k ? v.y : 0.0f);
       for (int i = 0; i < a.K; ++i) {
         const int m = a.atom[p * a.K + i];
         if (m < 0) continue;
         const int r = a.angle[p * a.K + i];
-        const float c = a.tw[(0 * H + k) * R + r], s = a.tw[(2 * H + k) * R + r];
+        const df c = {a.tw[(0 * H + k) * R + r], a.tw[(1 * H + k) * R + r]};
+        const df sn = {a.tw[(2 * H + k) * R + r], a.tw[(3 * H + k) * R + r]};
         const float2 dv = reinterpret_cast<const float2 *>(a.d)[(size_t)m * HJ + e];
         const float dim = k ? dv.y : 0.0f;
-        const float w = (float)a.coef[p * a.K + i];
-        re = fmaf(-w, fmaf(c, dv.x, s * dim), re);
-        im = fmaf(-w, fmaf(c, dim, -s * dv.x), im);
+        const df w = df_from_d(a.coef[p * a.K + i]);
+        // S_r d: harmonic k times exp(-i k theta_r)
+        const df sre = df_add(df_mul_f(c, dv.x), df_mul_f(sn, dim));
+        const df sim = df_sub(df_mul_f(c, dim), df_mul_f(sn, dv.x));
+        re = df_sub(re, df_mul(w, sre));
+        im = df_sub(im, df_mul(w, sim));
       }
       if (k == 0) {
-        ep[e] = re;
-        n2 = fmaf(re, re, n2);
+        eh[e] = re.hi;
+        el[e] = re.lo;
+        const double r0 = df_to_d(re);
+        n2 = fma(r0, r0, n2);
       } else {
         const int q = 2 * e - J;
-        ep[q] = 1.41421356237309515f * re;
-        ep[q + 1] = 1.41421356237309515f * im;
-        n2 = fmaf(2.0f * re, re, fmaf(2.0f * im, im, n2));
+        const df pr = df_mul(re, sqrt2), pi = df_mul(im, sqrt2);
+        eh[q] = pr.hi;
+        el[q] = pr.lo;
+        eh[q + 1] = pi.hi;
+        el[q + 1] = pi.lo;
+        const double r0 = df_to_d(pr), i0 = df_to_d(pi);
+        n2 = fma(r0, r0, fma(i0, i0, n2));
       }
     }
-    a.err[p] = n2;
+    a.err[p] = (float)n2;
   }
 }
 
-// C_m = sum over the atom's samples of y y^T.  The samples of atom m are
-// split over kCovSplit CTAs; each thread owns 4 x 4 tiles of the upper
-// triangle (two float4 reads of a sample row feed 16 FMAs), sums 32 samples
-// in FP32, folds them into FP64, and adds its tiles to C with FP64 atomics
-// (C starts at zero).
+// C_m = sum over the atom's samples of y y^T, y = S_{-r0} e_p + a_{i0} d_m.
+// The samples of atom m are split over kCovSplit CTAs (slices in list order);
+// each thread owns 4 x 4 tiles of the upper triangle.  The columns y of a
+// batch of kCovBatch samples are built in double-float in shared memory; a
+// product y_i y_j is the exact product of the hi parts (TwoProd) plus the
+// cross terms hi_i lo_j + lo_i hi_j, and the batch's products are summed
+// Dot2-style (TwoSum of the hi parts, the errors and lo parts summed apart),
+// then added to FP64 accumulators.  Each CTA writes its partial sums to its
+// own slice of Cpart (every entry, zero when it has no samples); a second
+// kernel adds the kCovSplit slices in order.
 constexpr int kCovSplit = 8;
 
 __global__ void __launch_bounds__(kCovThreads) ksvd_cov_kernel(const KsvdArgs a) {
-  extern __shared__ __align__(16) float ysm[];  // kCovBatch rows of ldy floats
+  extern __shared__ __align__(16) float ysm[];  // 2 x kCovBatch rows of ldy floats
+  __shared__ int s_p[kCovBatch], s_r0[kCovBatch];
+  __shared__ df s_w[kCovBatch];
   const int m = blockIdx.x / kCovSplit, part = blockIdx.x - m * kCovSplit;
   const int n = a.n, J = a.J, H = a.H, HJ = H * J, R = a.R;
   const int nb4 = (n + 3) / 4, ldy = 4 * nb4 + 4;  // +4: rows start in different banks
-  auto ys = [&](int s, int q) -> float & { return ysm[s * ldy + q]; };
+  float *yhi = ysm, *ylo = ysm + kCovBatch * ldy;
   const int beg0 = a.offset[m], cnt = a.offset[m + 1] - beg0;
   const int per = (cnt + kCovSplit - 1) / kCovSplit;
   const int beg = beg0 + part * per, end = min(beg0 + cnt, beg + per);
-  if (beg >= end) return;
-  double *Cm = a.C + (size_t)m * n * n;
+  double *Cm = a.Cpart + ((size_t)part * a.M + m) * n * n;
+  const size_t plane = (size_t)a.P * a.ldE;
+  const df sqrt2 = df_from_d(1.4142135623730951);
   const int ntiles = nb4 * (nb4 + 1) / 2;
   for (int t = threadIdx.x; t - threadIdx.x < ntiles; t += kCovThreads) {
     // tile (bi, bj), bi <= bj, of the upper triangle (row bi starts at
@@ -175,51 +247,76 @@ __global__ void __launch_bounds__(kCovThreads) ksvd_cov_kernel(const KsvdArgs a)
     for (int b0 = beg; b0 < end; b0 += kCovBatch) {
       const int nb = min(kCovBatch, end - b0);
       __syncthreads();
-      // build y for the batch: y = S_{-r0} e_p + a_{i0} d_m (packed; zero pad)
-      for (int w = threadIdx.x; w < nb * ldy; w += blockDim.x) ysm[w] = 0.0f;
-      __syncthreads();
-      for (int w = threadIdx.x; w < nb * HJ; w += blockDim.x) {
-        const int s = w / HJ, e = w - s * HJ;
-        const int2 smp = a.samples[b0 + s];
+      for (int w = threadIdx.x; w < nb * ldy; w += blockDim.x) {
+        yhi[w] = 0.0f;
+        ylo[w] = 0.0f;
+      }
+      if (threadIdx.x < nb) {
+        const int2 smp = a.samples[b0 + threadIdx.x];
         const int64_t p = smp.x;
-        const int i0 = smp.y;
-        const int r0 = a.angle[p * a.K + i0];
+        const int r0 = a.angle[p * a.K + smp.y];
         // the code entry of (m, r0): every occurrence of that pair (Fig.
         // "code" zeroes the whole entry b_{r0}[m])
         double wsum = 0.0;
         for (int i = 0; i < a.K; ++i)
           if (a.atom[p * a.K + i] == m && a.angle[p * a.K + i] == r0) wsum += a.coef[p * a.K + i];
-        const float w0 = (float)wsum;
+        s_p[threadIdx.x] = smp.x;
+        s_r0[threadIdx.x] = r0;
+        s_w[threadIdx.x] = df_from_d(wsum);
+      }
+      __syncthreads();
+      for (int w = threadIdx.x; w < nb * HJ; w += blockDim.x) {
+        const int s = w / HJ, e = w - s * HJ;
+        const int64_t p = s_p[s];
+        const int r0 = s_r0[s];
+        const df w0 = s_w[s];
         const int k = e / J;
-        const float *ep = a.E + p * (int64_t)a.ldE;
+        const float *eh = a.E + p * (int64_t)a.ldE, *el = eh + plane;
         const float2 dv = reinterpret_cast<const float2 *>(a.d)[(size_t)m * HJ + e];
         if (k == 0) {
-          ys(s, e) = ep[e] + w0 * dv.x;
+          const df y = df_add(df{eh[e], el[e]}, df_mul_f(w0, dv.x));
+          yhi[s * ldy + e] = y.hi;
+          ylo[s * ldy + e] = y.lo;
         } else {
           const int q = 2 * e - J;
-          const float re = ep[q], im = ep[q + 1];
+          const df re = {eh[q], el[q]}, im = {eh[q + 1], el[q + 1]};
           // S_{-theta}: harmonic k times exp(+i k theta)
-          const float c = a.tw[(0 * H + k) * R + r0], sn = a.tw[(2 * H + k) * R + r0];
-          ys(s, q) = fmaf(re, c, -im * sn) + 1.41421356237309515f * w0 * dv.x;
-          ys(s, q + 1) = fmaf(re, sn, im * c) + 1.41421356237309515f * w0 * dv.y;
+          const df c = {a.tw[(0 * H + k) * R + r0], a.tw[(1 * H + k) * R + r0]};
+          const df sn = {a.tw[(2 * H + k) * R + r0], a.tw[(3 * H + k) * R + r0]};
+          const df w2 = df_mul(w0, sqrt2);
+          const df yr = df_add(df_sub(df_mul(re, c), df_mul(im, sn)), df_mul_f(w2, dv.x));
+          const df yi = df_add(df_add(df_mul(re, sn), df_mul(im, c)), df_mul_f(w2, dv.y));
+          yhi[s * ldy + q] = yr.hi;
+          ylo[s * ldy + q] = yr.lo;
+          yhi[s * ldy + q + 1] = yi.hi;
+          ylo[s * ldy + q + 1] = yi.lo;
         }
       }
       __syncthreads();
       if (bi >= 0) {
-        float part16[16];
+        float sh[16], sl[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) part16[u] = 0.0f;
+        for (int u = 0; u < 16; ++u) sh[u] = sl[u] = 0.0f;
         for (int s = 0; s < nb; ++s) {
-          const float4 yi = *reinterpret_cast<const float4 *>(&ysm[s * ldy + 4 * bi]);
-          const float4 yj = *reinterpret_cast<const float4 *>(&ysm[s * ldy + 4 * bj]);
-          const float vi[4] = {yi.x, yi.y, yi.z, yi.w}, vj[4] = {yj.x, yj.y, yj.z, yj.w};
+          const float4 hi4 = *reinterpret_cast<const float4 *>(&yhi[s * ldy + 4 * bi]);
+          const float4 hj4 = *reinterpret_cast<const float4 *>(&yhi[s * ldy + 4 * bj]);
+          const float4 li4 = *reinterpret_cast<const float4 *>(&ylo[s * ldy + 4 * bi]);
+          const float4 lj4 = *reinterpret_cast<const float4 *>(&ylo[s * ldy + 4 * bj]);
+          const float hi[4] = {hi4.x, hi4.y, hi4.z, hi4.w}, hj[4] = {hj4.x, hj4.y, hj4.z, hj4.w};
+          const float li[4] = {li4.x, li4.y, li4.z, li4.w}, lj[4] = {lj4.x, lj4.y, lj4.z, lj4.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) part16[u * 4 + v] = fmaf(vi[u], vj[v], part16[u * 4 + v]);
+            for (int v = 0; v < 4; ++v) {
+              const df pp = two_prod(hi[u], hj[v]);
+              const float cross = __fmaf_rn(hi[u], lj[v], __fmaf_rn(li[u], hj[v], pp.lo));
+              const df ts = two_sum(sh[u * 4 + v], pp.hi);
+              sh[u * 4 + v] = ts.hi;
+              sl[u * 4 + v] = __fadd_rn(sl[u * 4 + v], __fadd_rn(ts.lo, cross));
+            }
         }
 #pragma unroll
-        for (int u = 0; u < 16; ++u) acc[u] += (double)part16[u];
+        for (int u = 0; u < 16; ++u) acc[u] += (double)sh[u] + (double)sl[u];
       }
     }
     if (bi >= 0) {
@@ -228,12 +325,26 @@ __global__ void __launch_bounds__(kCovThreads) ksvd_cov_kernel(const KsvdArgs a)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int i = 4 * bi + u, j = 4 * bj + v;
-          if (i < n && j < n && i <= j) {
-            atomicAdd(Cm + (size_t)i * n + j, acc[u * 4 + v]);
-            if (i != j) atomicAdd(Cm + (size_t)j * n + i, acc[u * 4 + v]);
-          }
+          if (i < n && j < n && i <= j) Cm[(size_t)i * n + j] = acc[u * 4 + v];
         }
     }
+  }
+}
+
+// C_m[i][j] = sum over the kCovSplit partial sums in slice order (upper
+// triangle), mirrored to the lower triangle.
+__global__ void ksvd_cov_sum_kernel(const KsvdArgs a) {
+  const int n = a.n;
+  const size_t nn = (size_t)n * n, per_part = (size_t)a.M * nn;
+  for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < per_part;
+       w += (size_t)gridDim.x * blockDim.x) {
+    const size_t m = w / nn, ij = w - m * nn;
+    const int i = (int)(ij / n), j = (int)(ij - (size_t)i * n);
+    if (i > j) continue;
+    double s = 0.0;
+    for (int part = 0; part < kCovSplit; ++part) s += a.Cpart[part * per_part + w];
+    a.C[w] = s;
+    if (i != j) a.C[m * nn + (size_t)j * n + i] = s;
   }
 }
 
@@ -443,56 +554,62 @@ int ksvd_setup(const rsc_dict *dict, int64_t P, int K, KsvdArgs &a) {
   a.H = dict->H;
   a.R = dict->R;
   a.n = dict->J + 2 * dict->kmax * dict->J;
-  if (a.n > kMaxPacked) return RSC_ERR_UNSUPPORTED;
+  if (a.n > kMaxPacked || a.M > kMaxAtomsKsvd) return RSC_ERR_UNSUPPORTED;
   a.ldE = (a.n + 3) & ~3;
   a.d = dict->d;
   a.tw = dict->tw;
   return RSC_OK;
 }
 
-// Accumulation: sample lists, residuals, C (zeroed here) and counts, and the
+// Accumulation: sample lists, residuals, C (written here) and counts, and the
 // top list of a.ntop patches; the per-patch scratch comes from one
 // stream-ordered allocation freed on `st`.
 int ksvd_accumulate(KsvdArgs &a, cudaStream_t st) {
   const int64_t P = a.P;
   const int M = a.M, n = a.n;
+  a.nchunk = (int)((P + kFillChunk - 1) / kFillChunk);
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t bE = al((size_t)P * a.ldE * 4), bErr = al((size_t)P * 4), bCur = al((size_t)M * 4),
-               bOff = al((size_t)(M + 1) * 4), bSmp = al((size_t)P * a.K * 8);
+  const size_t bE = al((size_t)2 * P * a.ldE * 4), bErr = al((size_t)P * 4),
+               bOff = al((size_t)(M + 1) * 4), bCh = al((size_t)a.nchunk * M * 4),
+               bSmp = al((size_t)P * a.K * 8), bCp = al((size_t)kCovSplit * M * n * n * 8);
   unsigned char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bE + bErr + bCur + bOff + bSmp,
-                                  st);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch),
+                                  bE + bErr + bOff + 2 * bCh + bSmp + bCp, st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
   }
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   unsigned char *q = scratch;
-  a.E = reinterpret_cast<float *>(q);
-  q += bE;
-  a.err = reinterpret_cast<float *>(q);
-  q += bErr;
-  a.cursor = reinterpret_cast<int *>(q);
-  q += bCur;
-  a.offset = reinterpret_cast<int *>(q);
-  q += bOff;
-  a.samples = reinterpret_cast<int2 *>(q);
-  int nsm = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::min<int64_t>((P + 255) / 256, (int64_t)nsm * 8);
-  e = cudaMemsetAsync(a.count, 0, (size_t)M * 4, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.C, 0, (size_t)M * n * n * 8, st);
+  auto take = [&](size_t b) {
+    unsigned char *r = q;
+    q += b;
+    return r;
+  };
+  a.E = reinterpret_cast<float *>(take(bE));
+  a.err = reinterpret_cast<float *>(take(bErr));
+  a.offset = reinterpret_cast<int *>(take(bOff));
+  a.chunk_cnt = reinterpret_cast<int *>(take(bCh));
+  a.chunk_base = reinterpret_cast<int *>(take(bCh));
+  a.samples = reinterpret_cast<int2 *>(take(bSmp));
+  a.Cpart = reinterpret_cast<double *>(take(bCp));
+  const size_t hist_smem = (size_t)M * 4;
+  const size_t cov_smem = (size_t)2 * kCovBatch * (4 * ((n + 3) / 4) + 4) * 4;
+  e = cudaFuncSetAttribute(ksvd_cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cov_smem);
   if (e == cudaSuccess) {
-    ksvd_count_kernel<<<grid, 256, 0, st>>>(a);
-    ksvd_scan_kernel<<<1, 32, 0, st>>>(a);
-    ksvd_fill_kernel<<<grid, 256, 0, st>>>(a);
-    const size_t cov_smem = (size_t)kCovBatch * (4 * ((n + 3) / 4) + 4) * 4;
-    e = cudaFuncSetAttribute(ksvd_cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cov_smem);
-    if (e == cudaSuccess) ksvd_cov_kernel<<<M * kCovSplit, kCovThreads, cov_smem, st>>>(a);
-    if (e == cudaSuccess && a.ntop > 0) ksvd_top_kernel<<<1, 1024, 0, st>>>(a);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    ksvd_chunk_count_kernel<<<a.nchunk, 256, hist_smem, st>>>(a);
+    ksvd_chunk_scan_kernel<<<1, 1024, 0, st>>>(a);
+    ksvd_fill_kernel<<<a.nchunk, kFillChunk, hist_smem + (size_t)kFillChunk * a.K * 4, st>>>(a);
+    ksvd_cov_kernel<<<M * kCovSplit, kCovThreads, cov_smem, st>>>(a);
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t work = (size_t)M * n * n;
+    const unsigned gsum = (unsigned)std::min<size_t>((work + 255) / 256, (size_t)nsm * 8);
+    ksvd_cov_sum_kernel<<<gsum, 256, 0, st>>>(a);
+    if (a.ntop > 0) ksvd_top_kernel<<<1, 1024, 0, st>>>(a);
+    e = cudaGetLastError();
   }
   int rc = e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
   const cudaError_t e2 = cudaFreeAsync(scratch, st);

@@ -9,6 +9,9 @@ only sequences the calls, the collectives and the merge of a short list;
 the arithmetic runs in librsc's kernels."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 from . import KSVD_TOP, Dictionary, encode, ksvd_accumulate, ksvd_finish, ksvd_update
@@ -79,19 +82,51 @@ def gather_top(err, idx, vec, offset: int, group):
     return merge_top(gathered["err"], gathered["gidx"], gathered["vec"], ntop=int(err.shape[0]))
 
 
+def save_checkpoint(path: str, d: np.ndarray, it: int, history: list, R: int, K: int):
+    """Writes the loop's state after `it` updates (dictionary [M, kmax+1, J,
+    2] float32, the iteration count, the history, R and K) to `path` (npz,
+    written beside it and renamed, so a crash leaves the previous one)."""
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, d=np.asarray(d, np.float32), iter=np.int64(it), R=np.int64(R), K=np.int64(K),
+             history=np.array(json.dumps(history)))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str, R: int, K: int):
+    """(dictionary, iterations done, history) from `path`; raises ValueError
+    when it was written for another R or K."""
+    with np.load(path, allow_pickle=False) as z:
+        if int(z["R"]) != R or int(z["K"]) != K:
+            raise ValueError(f"checkpoint {path} is for R={int(z['R'])}, K={int(z['K'])}")
+        return z["d"].copy(), int(z["iter"]), json.loads(str(z["history"]))
+
+
 def learn(x, d0, R: int, K: int, iters: int, precision: str = "f16", callback=None,
-          group=None, offset: int = 0):
+          group=None, offset: int = 0, checkpoint: str | None = None, resume: bool = False):
     """x: CUDA float32 [P, kmax+1, J, 2] patches; d0: CUDA float32 initial
     unit-norm atoms [M, kmax+1, J, 2].  Returns (d, codes, history) with
     history[i] = {"iter", "mse", "unused"} where mse is the mean squared
     coding error per real coefficient before the i-th update (this rank's
     patches).  With a process group, x holds this rank's patches (global
-    indices from `offset`) and every rank ends with the same dictionary."""
+    indices from `offset`) and every rank ends with the same dictionary.
+
+    checkpoint: a file written after every update with the dictionary, the
+    iteration count and the history (save_checkpoint; give each rank its own
+    file).  The loop draws no random numbers and its kernels give the same
+    result on every run, so that is its whole state: with resume=True and an
+    existing file, learning continues after the saved iteration and ends
+    with the atoms of an uninterrupted run, bit for bit."""
     import torch
     d = d0.contiguous()
     n = d.shape[2] * (2 * (d.shape[1] - 1) + 1)
     history = []
-    for it in range(iters):
+    start = 0
+    if resume and checkpoint and os.path.exists(checkpoint):
+        dn, start, history = load_checkpoint(checkpoint, R, K)
+        if dn.shape != tuple(d.shape):
+            raise ValueError(f"checkpoint {checkpoint} holds atoms of shape {dn.shape}")
+        d = torch.from_numpy(dn).to(d.device)
+    for it in range(start, iters):
         dic = Dictionary(d, R)
         codes = encode(dic, x, K, precision)
         if group is None:
@@ -106,6 +141,8 @@ def learn(x, d0, R: int, K: int, iters: int, precision: str = "f16", callback=No
             callback(rec, new)
         dic.close()
         d = new
+        if checkpoint:
+            save_checkpoint(checkpoint, d.cpu().numpy(), it + 1, history, R, K)
     dic = Dictionary(d, R)
     codes = encode(dic, x, K, precision)
     torch.cuda.current_stream().synchronize()

@@ -98,3 +98,26 @@ def test_two_rank_learning_matches_one_gpu(cuda_ok):
     d = d.cpu().numpy()
     assert np.abs(res[0][1] - res[1][1]).max() == 0.0   # every rank holds the same atoms
     assert np.abs(res[0][1] - d).max() < 1e-4, np.abs(res[0][1] - d).max()
+
+
+def test_checkpoint_resume_is_bit_identical(cuda_ok, tmp_path):
+    """Four R-K-SVD iterations in one run, and the same loop stopped after two
+    (its checkpoint written) and resumed from the file: the same atoms bit
+    for bit and the same history."""
+    import torch
+    from paper_1806_04374_gb300 import rksvd
+    R, K, M = 16, 3, 8
+    d_true = synth.make_dictionary(M, 6, 8, 931)
+    x, _ = synth.make_patches(d_true, 5000, 3, 0.05, 932)
+    xd = torch.from_numpy(x).cuda()
+    d0 = torch.from_numpy(synth.make_dictionary(M, 6, 8, 933)).cuda()
+    d_full, _, h_full = rksvd.learn(xd, d0, R, K, iters=4, precision="f16")
+    ck = str(tmp_path / "rksvd.npz")
+    rksvd.learn(xd, d0, R, K, iters=2, precision="f16", checkpoint=ck)
+    d_saved, it, _ = rksvd.load_checkpoint(ck, R, K)
+    assert it == 2
+    d_res, _, h_res = rksvd.learn(xd, d0, R, K, iters=4, precision="f16", checkpoint=ck,
+                                  resume=True)
+    assert np.array_equal(d_res.cpu().numpy(), d_full.cpu().numpy())
+    assert h_res == h_full
+    assert rksvd.load_checkpoint(ck, R, K)[1] == 4
