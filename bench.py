@@ -341,6 +341,30 @@ def run_reference(args) -> None:
     print(json.dumps(line))
 
 
+def measure_fused(rsc, torch, dic, xd, K, stream, out, split_value, reps: int = 5) -> dict:
+    """The same workload through rsc_encode_noalloc, whose FP16 path is one
+    persistent kernel for all K steps (scoring, re-scoring, least squares and
+    residual per 128-patch tile) plus the FP32 hand-off launch, timed with
+    CUDA events on the launching stream beside the split path's value."""
+    P = int(xd.shape[0])
+    sh = int(stream.cuda_stream)
+    args = (dic.handle, xd.data_ptr(), P, K, out["atom"].data_ptr(), out["angle_idx"].data_ptr(),
+            out["angle"].data_ptr(), out["coef"].data_ptr(), out["resid_norm2"].data_ptr(), sh)
+    for _ in range(2):
+        assert rsc.rsc_encode_noalloc(*args) == rsc.RSC_OK
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        rsc.rsc_encode_noalloc(*args)
+    ev[1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    return {"value": P / (ms / 1e3), "unit": "patches/s", "ms_per_step": ms,
+            "split_over_fused": split_value / (P / (ms / 1e3)),
+            "note": "one persistent launch for all K steps (rsc_encode_noalloc) against the "
+                    "headline's split path (a scoring and a refine launch per step, two streams)"}
+
+
 def measure_projection(rsc, torch, dev, stream, reps: int = 5) -> dict:
     """rsc_project over one 2048 x 2048 image (4.15 M windows of 11 x 11,
     n = 102): windows/s from CUDA events on the launching stream; the
@@ -747,6 +771,7 @@ def main():
 
     main_run = timed(args.precision, True)
     parity_outputs = {args.precision: sample_outputs()}
+    tuning = rsc.rsc_dict_tuning(dic.handle, K)
     # the same steps with the two halves serialised: each kernel timed alone
     iso_run = timed(args.precision, False, timing_mode=2, steps=min(args.steps, 10))
     cmp_run = None
@@ -829,6 +854,8 @@ def main():
                          + ") + double-float re-scoring + FP64 Cholesky"),
                 "l2": "inputs (432 MB) larger than L2, no flush",
                 "parallelism": f"dp{world} (patches sharded, no collective)",
+                "tuning": dict(tuning, source={0: "default", 1: "autotuned table",
+                                               2: "override"}[tuning["source"]]),
             },
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                            "p99": float(np.percentile(step_ms, 99)),
@@ -901,6 +928,9 @@ def main():
             mtf = mf * P * args.steps / n_launch / launch_s / 1e12
             line["mma_executed"] = {"flops_per_patch": mf, "tflops": mtf,
                                     "frac_of_peak": mtf / peak}
+        if args.precision == "f16" and P <= (1 << 20) and world == 1:
+            line["single_launch_fused"] = measure_fused(rsc, torch, dic, xd, K, stream, out,
+                                                        value)
         if cmp_run is not None:
             v32 = world * P * args.steps / (cmp_run["total_ms"] / 1e3)
             line["fp32_path"] = {"value": v32, "unit": "patches/s",

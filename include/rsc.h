@@ -357,6 +357,49 @@ int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t P, int32_t 
 int rsc_dict_check(const rsc_dict *dict, void *stream);
 
 /*
+ * Tuning of the FP16 path (a property of this library; the paper has no
+ * counterpart).  None of these changes a result: every patch is coded the
+ * same way whatever the grouping or the pipeline depth.
+ *   groups               : concurrent stream groups the patches of one call
+ *                          are split into (1..4; default 2);
+ *   group_min            : fewest patches per group (default 65536);
+ *   refine_blocks_per_sm : grid cap of the per-patch kernels per SM (1..64;
+ *                          default 32);
+ *   score_stages         : depth of the scoring kernel's dictionary ring, one
+ *                          of the two built per layout (rows of 112 slots,
+ *                          paired: 6 or 4; plain: 4 or 6; rows of 256 slots:
+ *                          5 or 4; the first is the default);
+ *   source               : output of rsc_dict_tuning: 0 default, 1 table,
+ *                          2 set by rsc_dict_set_tuning (the most specific
+ *                          source of any field).
+ * A field of 0 means "not set".  librsc reads a table of measured winners
+ * (written by the package's autotuner) when a dictionary is created: the
+ * file rsc_tuning.txt beside librsc.so, or the file named by the
+ * environment variable RSC_TUNING_TABLE.  Each line reads
+ * "n M R K groups group_min refine_blocks_per_sm score_stages" (n = packed
+ * length J (2 kmax + 1)); '#' starts a comment.  Fields are taken in the
+ * order: rsc_dict_set_tuning, the table entry of the dictionary's (n, M, R)
+ * and the call's K, the default.
+ */
+typedef struct {
+  int32_t groups, group_min, refine_blocks_per_sm, score_stages, source;
+} rsc_tuning;
+
+/* Sets (t) or clears (t = NULL) the tuning overrides of `dict`; values out
+ * of range give RSC_ERR_INVALID and leave the overrides unchanged. */
+int rsc_dict_set_tuning(rsc_dict *dict, const rsc_tuning *t);
+
+/* The tuning an rsc_encode with K steps on `dict` uses (every field filled;
+ * `source` as above).  HOST output. */
+int rsc_dict_tuning(const rsc_dict *dict, int32_t K, rsc_tuning *out);
+
+/* Looks up (n, M, R, K) in the table file `path` (format above): fills `out`
+ * with source = 1 when an entry matches, source = 0 (fields 0) when none
+ * does; RSC_ERR_INVALID when the file cannot be read.  Host only. */
+int rsc_tuning_table_lookup(const char *path, int32_t n, int32_t M, int32_t R, int32_t K,
+                            rsc_tuning *out);
+
+/*
  * rsc_dict_set_limits -- diagnostic limits on `dict`, for testing the error
  * paths (a property of this library; the paper has no counterpart).
  *   pipeline_wait_ns : limit of the waits between the FP16 scoring kernel's

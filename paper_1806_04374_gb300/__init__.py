@@ -34,12 +34,22 @@ EXPORTS = (
     "rsc_ksvd_update", "rsc_basis_create", "rsc_basis_destroy", "rsc_basis_info", "rsc_project",
     "rsc_encode_images", "rsc_ksvd_accumulate", "rsc_ksvd_finish", "rsc_reconstruct",
     "rsc_synthesize", "rsc_classify_images", "rsc_workspace_bytes", "rsc_dict_set_limits",
+    "rsc_dict_set_tuning", "rsc_dict_tuning", "rsc_tuning_table_lookup",
 )
 
 
 class rsc_dims(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("J", ctypes.c_int32), ("kmax", ctypes.c_int32),
                 ("R", ctypes.c_int32)]
+
+
+class rsc_tuning(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int32), ("group_min", ctypes.c_int32),
+                ("refine_blocks_per_sm", ctypes.c_int32), ("score_stages", ctypes.c_int32),
+                ("source", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class RscError(RuntimeError):
@@ -91,6 +101,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsc_dict_set_timing.argtypes = [vp, ctypes.c_int]
     lib.rsc_dict_set_limits.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64]
     lib.rsc_dict_set_limits.restype = ctypes.c_int
+    lib.rsc_dict_set_tuning.argtypes = [vp, ctypes.POINTER(rsc_tuning)]
+    lib.rsc_dict_set_tuning.restype = ctypes.c_int
+    lib.rsc_dict_tuning.argtypes = [vp, i32, ctypes.POINTER(rsc_tuning)]
+    lib.rsc_dict_tuning.restype = ctypes.c_int
+    lib.rsc_tuning_table_lookup.argtypes = [ctypes.c_char_p, i32, i32, i32, i32,
+                                            ctypes.POINTER(rsc_tuning)]
+    lib.rsc_tuning_table_lookup.restype = ctypes.c_int
     lib.rsc_dict_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.rsc_status_string.argtypes = [ctypes.c_int]
     lib.rsc_status_string.restype = ctypes.c_char_p
@@ -205,6 +222,33 @@ def rsc_dict_set_limits(handle: int, pipeline_wait_ns: int = 0, scratch_limit: i
     scoring kernel's pipeline wait limit and the FP16 path's scratch budget."""
     return load_library().rsc_dict_set_limits(ctypes.c_void_p(handle), int(pipeline_wait_ns),
                                               int(scratch_limit))
+
+
+def rsc_dict_set_tuning(handle: int, groups: int = 0, group_min: int = 0,
+                        refine_blocks_per_sm: int = 0, score_stages: int = 0, clear: bool = False):
+    """Tuning overrides of a dictionary (0 = not set); clear=True removes them."""
+    t = None if clear else rsc_tuning(groups, group_min, refine_blocks_per_sm, score_stages, 0)
+    st = load_library().rsc_dict_set_tuning(ctypes.c_void_p(handle),
+                                            None if t is None else ctypes.byref(t))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_dict_set_tuning")
+
+
+def rsc_dict_tuning(handle: int, K: int) -> dict:
+    """The tuning an encode with K steps uses (fields and their source)."""
+    t = rsc_tuning()
+    st = load_library().rsc_dict_tuning(ctypes.c_void_p(handle), int(K), ctypes.byref(t))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_dict_tuning")
+    return t.as_dict()
+
+
+def rsc_tuning_table_lookup(path: str, n: int, M: int, R: int, K: int) -> dict:
+    t = rsc_tuning()
+    st = load_library().rsc_tuning_table_lookup(path.encode(), n, M, R, K, ctypes.byref(t))
+    if st != RSC_OK:
+        raise RscError(st, "rsc_tuning_table_lookup")
+    return t.as_dict()
 
 
 def rsc_dict_timing(handle: int):

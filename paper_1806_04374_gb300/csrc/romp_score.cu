@@ -54,15 +54,15 @@ constexpr uint64_t kSWaitNs = 2000000000ull;  // drain waits (and the default pi
 constexpr int kRing = 16;               // blocks near the running best kept per step
 
 // Shape of one instantiation: NB 64-column blocks per packed row (2 for rows
-// of kTcKst, 4 for kTcKstLong).
-template <bool PAIRED, int NB>
+// of kTcKst, 4 for kTcKstLong) and STAGES stages of the dictionary ring.
+template <bool PAIRED, int NB, int STAGES>
 struct SShape {
   static constexpr int N = PAIRED ? kTcSNP : kTcSN;   // B rows per chunk = MMA N
   static constexpr int NKB = NB;                      // K-blocks (ring stages) per chunk
   static constexpr int kATile = NB * kABlk;           // one A tile (bytes)
   static constexpr int kABufs = NB > 2 ? 1 : 2;       // A tiles in flight
   static constexpr int kBStage = N * 128;             // one K-block of a chunk (bytes)
-  static constexpr int kStages = NB > 2 ? 5 : (PAIRED ? 6 : 4);
+  static constexpr int kStages = STAGES;
   static constexpr int SLICE = N / kTcSplit;          // B rows per epilogue column slice
   static constexpr int PIECES = SLICE / 32;           // 32-column pieces per slice
   static constexpr int a_off = 0, b_off = kABufs * kATile;
@@ -85,11 +85,11 @@ enum : int {
 };
 static_assert(kBarCount * 8 + 8 <= 256, "barrier area");
 
-template <bool PAIRED, int NB>
+template <bool PAIRED, int NB, int STAGES>
 __global__ void __launch_bounds__(kSThreads, 1)
     romp_score_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const ScoreArgs a) {
-  using Sh = SShape<PAIRED, NB>;
+  using Sh = SShape<PAIRED, NB, STAGES>;
   constexpr int N = Sh::N, NKB = Sh::NKB, kStages = Sh::kStages, kABufs = Sh::kABufs;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
 }  // namespace
 
 namespace {
-template <bool PAIRED, int NB>
+template <bool PAIRED, int NB, int STAGES>
 int launch_score_t(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
                    cudaStream_t stream) {
   int dev = 0;
@@ -385,9 +385,9 @@ int launch_score_t(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap
   int max_optin = 0, nsm = 0;
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  constexpr int total = SShape<PAIRED, NB>::total;
+  constexpr int total = SShape<PAIRED, NB, STAGES>::total;
   if (total > max_optin) return RSC_ERR_UNSUPPORTED;
-  auto kern = romp_score_kernel<PAIRED, NB>;
+  auto kern = romp_score_kernel<PAIRED, NB, STAGES>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, total);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   const int64_t tiles = (a.P + kSTile - 1) / kSTile;
@@ -399,12 +399,29 @@ int launch_score_t(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap
 }
 }  // namespace
 
+int rsc_score_stage_options(int L, int paired, int *dflt, int *other) {
+  // the instantiated ring depths; the first is the default
+  if (L == kTcKst) {
+    *dflt = paired ? 6 : 4;
+    *other = paired ? 4 : 6;
+  } else {
+    *dflt = 5;
+    *other = 4;
+  }
+  return RSC_OK;
+}
+
 int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
                      cudaStream_t stream) {
   if (a.P == 0) return RSC_OK;
+  if (a.L == kTcKst && a.paired)
+    return a.stages == 4 ? launch_score_t<true, 2, 4>(a, tmA, tmB, stream)
+                         : launch_score_t<true, 2, 6>(a, tmA, tmB, stream);
   if (a.L == kTcKst)
-    return a.paired ? launch_score_t<true, 2>(a, tmA, tmB, stream)
-                    : launch_score_t<false, 2>(a, tmA, tmB, stream);
-  if (a.L == kTcKstLong && !a.paired) return launch_score_t<false, 4>(a, tmA, tmB, stream);
+    return a.stages == 6 ? launch_score_t<false, 2, 6>(a, tmA, tmB, stream)
+                         : launch_score_t<false, 2, 4>(a, tmA, tmB, stream);
+  if (a.L == kTcKstLong && !a.paired)
+    return a.stages == 4 ? launch_score_t<false, 4, 4>(a, tmA, tmB, stream)
+                         : launch_score_t<false, 4, 5>(a, tmA, tmB, stream);
   return RSC_ERR_UNSUPPORTED;
 }

@@ -1,13 +1,16 @@
 // rsc_capi.cu -- host side of the librsc C ABI (declared in include/rsc.h):
 // argument checks, dictionary set-up (the once-per-dictionary tables of the
 // steering matrix of Eq. (Sr)) and dispatch of the coding kernels.
+#include <dlfcn.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <cuda_fp16.h>
 
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "rsc_internal.h"
@@ -308,10 +311,107 @@ int check_device(const rsc_dict *d) {
   return dev == d->device ? RSC_OK : RSC_ERR_INVALID;
 }
 
-// The FP16 path splits its patches into at most kMaxGroups groups of at
-// least kGroupMin patches, one stream each.
-constexpr int kMaxGroups = 2;
+// The FP16 path splits its patches into at most `groups` (tuning, <=
+// kMaxGroups) groups of at least `group_min` patches, one stream each.
+constexpr int kMaxGroups = 4;
+constexpr int kDefaultGroups = 2;
 constexpr int64_t kGroupMin = 65536;
+constexpr int kDefaultRefineBlocks = 32;
+
+// ---------------------------------------------------------------- tuning
+struct TuneEntry {
+  int n, M, R, K;
+  rsc_tuning t;
+};
+
+bool tuning_in_range(const rsc_tuning &t) {
+  return t.groups >= 0 && t.groups <= kMaxGroups && t.group_min >= 0 &&
+         t.refine_blocks_per_sm >= 0 && t.refine_blocks_per_sm <= 64 &&
+         (t.score_stages == 0 || (t.score_stages >= 4 && t.score_stages <= 6));
+}
+
+// Reads a table of "n M R K groups group_min refine_blocks_per_sm
+// score_stages" lines ('#' starts a comment); false when unreadable.
+bool read_tuning_table(const char *path, std::vector<TuneEntry> &out) {
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  while (fgets(line, sizeof line, f)) {
+    char *hash = strchr(line, '#');
+    if (hash) *hash = 0;
+    TuneEntry e{};
+    int v[8];
+    if (sscanf(line, "%d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+               &v[7]) != 8)
+      continue;
+    e.n = v[0];
+    e.M = v[1];
+    e.R = v[2];
+    e.K = v[3];
+    e.t = rsc_tuning{v[4], v[5], v[6], v[7], 1};
+    if (tuning_in_range(e.t)) out.push_back(e);
+  }
+  fclose(f);
+  return true;
+}
+
+std::once_flag g_table_once;
+std::vector<TuneEntry> g_table;
+
+// The process-wide table: RSC_TUNING_TABLE, else rsc_tuning.txt beside this
+// library (found with dladdr); absent or unreadable means no entries.
+void load_default_table() {
+  std::string path;
+  const char *env = getenv("RSC_TUNING_TABLE");
+  if (env && *env) {
+    path = env;
+  } else {
+    Dl_info info;
+    if (dladdr(reinterpret_cast<void *>(&rsc_version), &info) && info.dli_fname) {
+      path = info.dli_fname;
+      const size_t slash = path.rfind('/');
+      path = (slash == std::string::npos ? std::string(".") : path.substr(0, slash)) +
+             "/rsc_tuning.txt";
+    }
+  }
+  if (!path.empty()) read_tuning_table(path.c_str(), g_table);
+}
+
+// A ring depth the dictionary's layout has, or 0.
+int valid_stages(const rsc_dict *d, int st) {
+  if (!d->steered_f16 || st == 0) return 0;
+  int a = 0, b = 0;
+  rsc_score_stage_options(d->row_len, d->paired_f16 != nullptr, &a, &b);
+  return (st == a || st == b) ? st : 0;
+}
+
+// Field by field: the override, the table entry for K, the default.
+rsc_tuning effective_tuning(const rsc_dict *d, int K) {
+  const rsc_tuning &ov = d->tune_override;
+  const rsc_tuning tb = (K >= 1 && K <= kMaxK) ? d->tune_table[K] : rsc_tuning{};
+  rsc_tuning r{};
+  int src = 0;
+  auto pick = [&](int32_t o, int32_t t, int32_t dflt) {
+    if (o > 0) {
+      src = 2;
+      return o;
+    }
+    if (t > 0) {
+      if (src < 1) src = 1;
+      return t;
+    }
+    return dflt;
+  };
+  r.groups = pick(ov.groups, tb.groups, kDefaultGroups);
+  r.group_min = pick(ov.group_min, tb.group_min, (int32_t)kGroupMin);
+  r.refine_blocks_per_sm = pick(ov.refine_blocks_per_sm, tb.refine_blocks_per_sm,
+                                kDefaultRefineBlocks);
+  int dflt_st = 0, other = 0;
+  if (d->steered_f16) rsc_score_stage_options(d->row_len, d->paired_f16 != nullptr, &dflt_st, &other);
+  r.score_stages = pick(valid_stages(d, ov.score_stages), valid_stages(d, tb.score_stages), dflt_st);
+  r.source = src;
+  return r;
+}
 
 // Splits P patches of the FP16 path into G groups (one stream each); returns G
 // and fills Pg[] and the scratch bytes of each group.
@@ -329,8 +429,10 @@ size_t f16_scratch_bytes(int64_t P, int K, int L) {
 }
 
 int f16_groups(const rsc_dict *dict, int64_t P, int K, int64_t Pg[], size_t bytes[]) {
-  int G = (int)(P / kGroupMin);
-  G = G < 1 ? 1 : (G > kMaxGroups ? kMaxGroups : G);
+  const rsc_tuning tu = effective_tuning(dict, K);
+  int G = (int)(P / (tu.group_min > 0 ? tu.group_min : kGroupMin));
+  const int gmax = tu.groups < 1 ? 1 : (tu.groups > kMaxGroups ? kMaxGroups : tu.groups);
+  G = G < 1 ? 1 : (G > gmax ? gmax : G);
   if (dict->timing == 2) G = 1;  // timing of each kernel alone
   int64_t done = 0;
   for (int g = 0, left = G; g < G; ++g, --left) {
@@ -415,6 +517,9 @@ int encode_f16_group(const rsc_dict *dict, const RompArgs &base, unsigned char *
   sa.win = ra.win;
   sa.err = dict->err;
   sa.wait_ns = dict->wait_ns ? dict->wait_ns : 2000000000ull;
+  const rsc_tuning tu = effective_tuning(dict, K);
+  sa.stages = tu.score_stages;
+  ra.blocks_per_sm = tu.refine_blocks_per_sm;
   CUtensorMap tmA;
   int rc = encode_rows_map(&tmA, ra.A, (size_t)P, kTcBN, ra.L);
   if (rc == RSC_OK) {
@@ -566,6 +671,11 @@ int rsc_dict_create(const float *coef, rsc_dims dims, void *stream, rsc_dict **o
     free_dict(d);
     return rc;
   }
+  // the measured tunings of this (n, M, R), per K
+  std::call_once(g_table_once, load_default_table);
+  for (const TuneEntry &te : g_table)
+    if (te.n == d->n && te.M == M && te.R == R && te.K >= 1 && te.K <= kMaxK)
+      d->tune_table[te.K] = te.t;
   *out = d;
   return RSC_OK;
 }
@@ -779,6 +889,37 @@ int rsc_dict_check(const rsc_dict *dict, void *stream) {
   if (e == cudaSuccess) e = cudaMemset(dict->err, 0, sizeof(int));
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return v;
+}
+
+int rsc_dict_set_tuning(rsc_dict *dict, const rsc_tuning *t) {
+  if (!dict) return RSC_ERR_INVALID;
+  if (!t) {
+    dict->tune_override = rsc_tuning{};
+    return RSC_OK;
+  }
+  rsc_tuning v = *t;
+  v.source = 0;
+  if (!tuning_in_range(v) || (v.score_stages != 0 && !valid_stages(dict, v.score_stages)))
+    return RSC_ERR_INVALID;
+  dict->tune_override = v;
+  return RSC_OK;
+}
+
+int rsc_dict_tuning(const rsc_dict *dict, int32_t K, rsc_tuning *out) {
+  if (!dict || !out || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
+  *out = effective_tuning(dict, K);
+  return RSC_OK;
+}
+
+int rsc_tuning_table_lookup(const char *path, int32_t n, int32_t M, int32_t R, int32_t K,
+                            rsc_tuning *out) {
+  if (!path || !out) return RSC_ERR_INVALID;
+  std::vector<TuneEntry> tab;
+  if (!read_tuning_table(path, tab)) return RSC_ERR_INVALID;
+  *out = rsc_tuning{};
+  for (const TuneEntry &e : tab)
+    if (e.n == n && e.M == M && e.R == R && e.K == K) *out = e.t;
+  return RSC_OK;
 }
 
 int rsc_dict_set_limits(rsc_dict *dict, uint64_t pipeline_wait_ns, uint64_t scratch_limit) {

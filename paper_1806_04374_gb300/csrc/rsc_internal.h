@@ -51,6 +51,10 @@ struct rsc_dict {
   // path's per-call scratch (bytes)
   uint64_t wait_ns;
   uint64_t scratch_limit;
+  // tuning (rsc_tuning): the overrides set by rsc_dict_set_tuning, and the
+  // table entries of this dictionary's (n, M, R) read at creation, per K
+  rsc_tuning tune_override;
+  rsc_tuning tune_table[kMaxK + 1];
 };
 
 // Packed real coordinates of a half spectrum, shared by the tensor-core
@@ -202,9 +206,13 @@ struct ScoreArgs {
   // limit of the pipeline waits (ns); the waits that drain issued copies and
   // MMAs before the CTA exits keep their own limit
   uint64_t wait_ns;
+  int stages;  // dictionary-ring stages (one of rsc_score_stage_options; else the default)
 };
 int rsc_launch_score(const ScoreArgs &a, const CUtensorMap &tmA, const CUtensorMap &tmB,
                      cudaStream_t stream);
+// The two ring depths instantiated for a row length and layout (the first
+// is the default).
+int rsc_score_stage_options(int L, int paired, int *dflt, int *other);
 
 // Per-patch steps of the split FP16 path (romp_refine.cu): init (packed x,
 // state) or one refine (certify, re-score, Cholesky, residual).
@@ -240,6 +248,7 @@ struct RefineArgs {
   int *slow_list;
   int *slow_count;
   unsigned long long *fallbacks;
+  int blocks_per_sm;  // grid cap of the init/refine launches per SM (0: 32)
 };
 int rsc_launch_refine(const RefineArgs &a, bool init, cudaStream_t stream);
 // Number of double / float / int state arrays for K steps; returns the
