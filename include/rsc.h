@@ -366,9 +366,9 @@ int rsc_dict_check(const rsc_dict *dict, void *stream);
  *   refine_blocks_per_sm : grid cap of the per-patch kernels per SM (1..64;
  *                          default 32);
  *   score_stages         : depth of the scoring kernel's dictionary ring, one
- *                          of the two built per layout (rows of 112 slots,
- *                          paired: 6 or 4; plain: 4 or 6; rows of 256 slots:
- *                          5 or 4; the first is the default);
+ *                          of the two built per layout (rows of 112 slots:
+ *                          4 or 2; rows of 256 slots: 4 or 3; the first is
+ *                          the default; other values give RSC_ERR_INVALID);
  *   source               : output of rsc_dict_tuning: 0 default, 1 table,
  *                          2 set by rsc_dict_set_tuning (the most specific
  *                          source of any field).

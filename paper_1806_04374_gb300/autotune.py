@@ -32,12 +32,29 @@ WORKLOADS = {
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "rsc_tuning.txt")
 
 
+def stage_options(dic) -> list[int]:
+    """The ring depths the dictionary's layout is built with, default first
+    (found by asking librsc to set each depth; clears the dictionary's tuning
+    overrides)."""
+    rsc.rsc_dict_set_tuning(dic.handle, clear=True)
+    dflt = rsc.rsc_dict_tuning(dic.handle, 1)["score_stages"]
+    out = [dflt]
+    for s in range(2, 7):
+        if s == dflt:
+            continue
+        try:
+            rsc.rsc_dict_set_tuning(dic.handle, score_stages=s)
+            out.append(s)
+        except rsc.RscError:
+            pass
+    rsc.rsc_dict_set_tuning(dic.handle, clear=True)
+    return out
+
+
 def candidates(dic) -> list[dict]:
     """The grid searched: groups 1-3, refine blocks per SM 8/16/32, both ring
     depths the dictionary's layout is built with."""
-    dflt = rsc.rsc_dict_tuning(dic.handle, 1)["score_stages"]
-    other = {6: 4, 4: 6, 5: 4}[dflt] if dflt in (4, 5, 6) else dflt
-    stages = [dflt, other] if dflt != other else [dflt]
+    stages = stage_options(dic)
     return [{"groups": g, "refine_blocks_per_sm": b, "score_stages": s}
             for g, b, s in itertools.product((1, 2, 3), (8, 16, 32), stages)]
 

@@ -1000,12 +1000,12 @@ int rsc_project(const rsc_basis *b, const float *image, int32_t h, int32_t w, fl
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   ImageItem it{image, h, w, 0};
   ImageItem *d_it = nullptr;
-  e = cudaMallocAsync(reinterpret_cast<void **>(&d_it), sizeof(ImageItem), st);
+  e = rsc_scratch_alloc(reinterpret_cast<void **>(&d_it), sizeof(ImageItem), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_it, &it, sizeof it, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   const int64_t P = (int64_t)(h - b->N + 1) * (w - b->N + 1);
   int rc = launch_project(b, d_it, 1, P, coef, st);
-  cudaFreeAsync(d_it, st);
+  rsc_scratch_free(d_it, st);
   // the host copy of `it` must outlive the async copy
   e = cudaStreamSynchronize(st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
@@ -1037,7 +1037,7 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *b, const float *con
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t bI = (items.size() * sizeof(ImageItem) + 255) & ~(size_t)255;
   unsigned char *scratch = nullptr;
-  e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bI + (size_t)P * b->nout * 4, st);
+  e = rsc_scratch_alloc(reinterpret_cast<void **>(&scratch), bI + (size_t)P * b->nout * 4, st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
@@ -1052,7 +1052,7 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *b, const float *con
   if (rc == RSC_OK) rc = launch_project(b, d_items, (int)items.size(), P, xc, st);
   if (rc == RSC_OK)
     rc = rsc_encode(dict, xc, P, K, prec, atom, angle_idx, angle, coef, resid_norm2, stream);
-  cudaFreeAsync(scratch, st);
+  rsc_scratch_free(scratch, st);
   // the host work list must outlive its async copy
   e = cudaStreamSynchronize(st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
@@ -1094,7 +1094,7 @@ int rsc_classify_images(const rsc_dict *const *dicts, int32_t C, const rsc_basis
   const size_t bX = al((size_t)P * b->nout * 4), bA = al((size_t)P * K * 4),
                bC = al((size_t)P * K * 8), bP = al((size_t)P * 4);
   unsigned char *scratch = nullptr;
-  e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bI + bO + bX + 2 * bA + bC + 3 * bP, st);
+  e = rsc_scratch_alloc(reinterpret_cast<void **>(&scratch), bI + bO + bX + 2 * bA + bC + 3 * bP, st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
@@ -1140,7 +1140,7 @@ int rsc_classify_images(const rsc_dict *const *dicts, int32_t C, const rsc_basis
     e = cudaGetLastError();
     if (e != cudaSuccess) rc = rsc_cuda_fail(e);
   }
-  cudaFreeAsync(scratch, st);
+  rsc_scratch_free(scratch, st);
   // the host work lists must outlive their async copies
   e = cudaStreamSynchronize(st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);

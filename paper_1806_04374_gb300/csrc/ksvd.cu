@@ -573,7 +573,7 @@ int ksvd_accumulate(KsvdArgs &a, cudaStream_t st) {
                bOff = al((size_t)(M + 1) * 4), bCh = al((size_t)a.nchunk * M * 4),
                bSmp = al((size_t)P * a.K * 8), bCp = al((size_t)kCovSplit * M * n * n * 8);
   unsigned char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch),
+  cudaError_t e = rsc_scratch_alloc(reinterpret_cast<void **>(&scratch),
                                   bE + bErr + bOff + 2 * bCh + bSmp + bCp, st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
@@ -612,7 +612,7 @@ int ksvd_accumulate(KsvdArgs &a, cudaStream_t st) {
     e = cudaGetLastError();
   }
   int rc = e == cudaSuccess ? RSC_OK : rsc_cuda_fail(e);
-  const cudaError_t e2 = cudaFreeAsync(scratch, st);
+  const cudaError_t e2 = rsc_scratch_free(scratch, st);
   if (rc == RSC_OK && e2 != cudaSuccess) rc = rsc_cuda_fail(e2);
   return rc;
 }
@@ -648,7 +648,7 @@ extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, 
   const size_t bC = al((size_t)M * n * n * 8), bCnt = al((size_t)M * 4),
                bTe = al(kTopMax * 4), bTi = al(kTopMax * 8), bTv = al((size_t)kTopMax * HJ * 8);
   unsigned char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bC + bCnt + bTe + bTi + bTv,
+  cudaError_t e = rsc_scratch_alloc(reinterpret_cast<void **>(&scratch), bC + bCnt + bTe + bTi + bTv,
                                   st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
@@ -675,7 +675,7 @@ extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, 
   a.n_used = n_used;
   rc = ksvd_accumulate(a, st);
   if (rc == RSC_OK) rc = ksvd_finish(a, st);
-  e = cudaFreeAsync(scratch, st);
+  e = rsc_scratch_free(scratch, st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
   return rc;
 }

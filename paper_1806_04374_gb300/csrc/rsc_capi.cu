@@ -73,7 +73,7 @@ void timing_end(const rsc_dict *d, int slot, cudaStream_t st) {
 struct HostStage {
   std::mutex mu;  // one rsc_encode_host at a time per dictionary
   int64_t chunk = 0;
-  int K = 0, vec = 0;
+  int K = 0, vec = 0, nbuf = 0;
   cudaStream_t s[2] = {nullptr, nullptr};
   struct Buf {
     float *x = nullptr;
@@ -94,20 +94,22 @@ struct HostStage {
     }
     chunk = 0;
     K = 0;
+    nbuf = 0;
   }
   ~HostStage() {
     release();
     for (int i = 0; i < 2; ++i)
       if (s[i]) cudaStreamDestroy(s[i]);
   }
-  // Buffers for chunks of `n` patches of K steps and `v` floats each.
-  cudaError_t reserve(int64_t n, int k, int v) {
+  // `nb` buffers (1 or 2) for chunks of `n` patches of K steps and `v` floats each.
+  cudaError_t reserve(int64_t n, int k, int v, int nb) {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)
       if (!s[i]) e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
-    if (e != cudaSuccess || (n <= chunk && k <= K && v == vec)) return e;
+    if (e != cudaSuccess || (n <= chunk && k <= K && v == vec && nb <= nbuf)) return e;
     release();
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    nbuf = nb;
+    for (int i = 0; i < nb && e == cudaSuccess; ++i) {
       Buf &B = b[i];
       e = cudaMalloc(&B.x, (size_t)n * v * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&B.atom, (size_t)n * k * sizeof(int32_t));
@@ -257,7 +259,7 @@ __global__ void anorm_kernel(const float *__restrict__ d, int M, int J, int H,
 // per-harmonic cross-Gram table H_k(a, b) in double-float and the TMA map.
 // Returns RSC_OK also when the sizes are outside the path (tables left null).
 int build_tc_tables(rsc_dict *d, cudaStream_t st) {
-  const int M = d->M, J = d->J, H = d->H, R = d->R, HJ = H * J;
+  const int M = d->M, J = d->J, H = d->H, R = d->R;
   const int n = J + 2 * d->kmax * J;
   d->n = n;
   const size_t rows = (size_t)M * R;
@@ -327,7 +329,7 @@ struct TuneEntry {
 bool tuning_in_range(const rsc_tuning &t) {
   return t.groups >= 0 && t.groups <= kMaxGroups && t.group_min >= 0 &&
          t.refine_blocks_per_sm >= 0 && t.refine_blocks_per_sm <= 64 &&
-         (t.score_stages == 0 || (t.score_stages >= 4 && t.score_stages <= 6));
+         (t.score_stages == 0 || (t.score_stages >= 2 && t.score_stages <= 6));
 }
 
 // Reads a table of "n M R K groups group_min refine_blocks_per_sm
@@ -566,6 +568,53 @@ int rsc_cuda_fail(cudaError_t e) {
   return RSC_ERR_CUDA;
 }
 
+// The scratch pools.  The device's default pool has a release threshold of
+// 0: it gives freed memory back at every synchronisation, and the next call's
+// allocation maps it again (measured at 10^6 patches: 1.5 ms of a 10.9 ms
+// call, and a host-to-device copy on another stream did not overlap it).  The
+// library's own pool keeps what it has handed out; other users of the
+// default pool are not affected.
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+}  // namespace
+
+cudaError_t rsc_scratch_alloc(void **p, size_t bytes, cudaStream_t st) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pool[dev], &props);
+      if (e != cudaSuccess) {
+        g_pool[dev] = nullptr;
+        return e;
+      }
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+cudaError_t rsc_scratch_free(void *p, cudaStream_t st) { return cudaFreeAsync(p, st); }
+
+void rsc_scratch_trim() {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  for (int i = 0; i < kMaxPoolDevices; ++i)
+    if (g_pool[i]) cudaMemPoolTrimTo(g_pool[i], 0);
+}
+
 extern "C" {
 
 const char *rsc_last_cuda_error(void) { return g_cuda_msg; }
@@ -682,6 +731,8 @@ int rsc_dict_create(const float *coef, rsc_dims dims, void *stream, rsc_dict **o
 
 int rsc_dict_destroy(rsc_dict *dict) {
   free_dict(dict);
+  // scratch the pool keeps beyond what calls in flight hold goes back
+  rsc_scratch_trim();
   return RSC_OK;
 }
 
@@ -694,19 +745,20 @@ int rsc_dict_dims(const rsc_dict *dict, rsc_dims *dims) {
   return RSC_OK;
 }
 
-int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
-               int32_t *atom, int32_t *angle_idx, float *angle, double *coef, float *resid_norm2,
-               void *stream) {
-  if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
-  if (prec != RSC_FP32 && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
-  if (P == 0) return RSC_OK;
-  if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
-  if (!aligned16(x) || !aligned_as<int32_t>(atom) || !aligned_as<int32_t>(angle_idx) ||
-      !aligned_as<double>(coef) || (angle && !aligned_as<float>(angle)) ||
-      (resid_norm2 && !aligned_as<float>(resid_norm2)))
-    return RSC_ERR_INVALID;
-  int rc = check_device(dict);
-  if (rc != RSC_OK) return rc;
+namespace {
+
+// Host buffers of rsc_encode_host for one call of encode_impl: the patches
+// and the outputs, laid out as rsc_encode's device arguments.
+struct HostIO {
+  const float *x;
+  int32_t *atom, *angle_idx;
+  float *angle;
+  double *coef;
+  float *resid_norm2;
+};
+
+RompArgs base_args(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t *atom,
+                   int32_t *angle_idx, float *angle, double *coef, float *resid_norm2) {
   RompArgs a;
   a.x = x;
   a.P = P;
@@ -726,11 +778,52 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   a.resid_norm2 = resid_norm2;
   a.err = dict->err;
   a.fallbacks = dict->fallbacks;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return a;
+}
+
+// Copies of patches [off, off + n) of a call with host buffers: the patches
+// in (to the device slice at ad.x), or the outputs out (from ad's slices).
+cudaError_t copy_in(const HostIO &h, const RompArgs &ad, int64_t off, int64_t n, int64_t vec,
+                    cudaStream_t st) {
+  return cudaMemcpyAsync(const_cast<float *>(ad.x), h.x + off * vec, (size_t)(n * vec) * sizeof(float),
+                         cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t copy_out(const HostIO &h, const RompArgs &ad, int64_t off, int64_t n, int K,
+                     cudaStream_t st) {
+  const size_t nk = (size_t)(n * K);
+  cudaError_t e = cudaMemcpyAsync(h.atom + off * K, ad.atom, nk * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.angle_idx + off * K, ad.angle_idx, nk * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && h.angle)
+    e = cudaMemcpyAsync(h.angle + off * K, ad.angle, nk * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.coef + off * K, ad.coef, nk * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && h.resid_norm2)
+    e = cudaMemcpyAsync(h.resid_norm2 + off, ad.resid_norm2, (size_t)n * sizeof(float),
+                        cudaMemcpyDeviceToHost, st);
+  return e;
+}
+
+// The coder on `st` (arguments validated).  With host buffers `h`, a's
+// pointers are device staging buffers: each stream group copies its own
+// patches in before its first kernel and its outputs out after its last, so
+// that one group's copies overlap another group's kernels.
+int encode_impl(const rsc_dict *dict, const RompArgs &a, int32_t prec, cudaStream_t st,
+                const HostIO *h) {
+  const int64_t P = a.P, vec = (int64_t)dict->H * dict->J * 2;
+  const int K = a.K;
+  int rc = RSC_OK;
+  cudaError_t e = cudaSuccess;
   if (prec == RSC_FP32) {
+    if (h && (e = copy_in(*h, a, 0, P, vec, st)) != cudaSuccess) return rsc_cuda_fail(e);
     const int slot = timing_begin(dict, 0, st);
     rc = rsc_launch_f32(a, st);
     timing_end(dict, slot, st);
+    if (rc == RSC_OK && h && (e = copy_out(*h, a, 0, P, K, st)) != cudaSuccess)
+      rc = rsc_cuda_fail(e);
     return rc;
   }
 
@@ -748,14 +841,14 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
   // refusal (testing the error path without exhausting device memory)
   if (dict->scratch_limit && total > dict->scratch_limit) return RSC_ERR_OOM;
   unsigned char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), total, st);
+  e = rsc_scratch_alloc(reinterpret_cast<void **>(&scratch), total, st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
   }
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   cudaStream_t sg[kMaxGroups] = {};
-  cudaEvent_t fork = nullptr, join[kMaxGroups] = {};
+  cudaEvent_t fork = nullptr, join[kMaxGroups] = {}, cin[kMaxGroups] = {};
   sg[0] = st;
   if (G > 1) {
     e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
@@ -765,20 +858,33 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[g], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(sg[g], fork, 0);
     }
+    // with host buffers the groups' copies in go one after the other, so
+    // that group 0 starts once its own patches are in rather than once all
+    // groups' copies, sharing the link, are done
+    for (int g = 0; h && g + 1 < G && e == cudaSuccess; ++g)
+      e = cudaEventCreateWithFlags(&cin[g], cudaEventDisableTiming);
     if (e != cudaSuccess) rc = rsc_cuda_fail(e);
   }
   int64_t off = 0;
   size_t soff = 0;
   for (int g = 0; g < G && rc == RSC_OK; ++g) {
     RompArgs ag = a;
-    ag.x = x + off * dict->H * dict->J * 2;
+    ag.x = a.x + off * vec;
     ag.P = Pg[g];
-    ag.atom = atom + off * K;
-    ag.angle_idx = angle_idx + off * K;
-    ag.angle = angle ? angle + off * K : nullptr;
-    ag.coef = coef + off * K;
-    ag.resid_norm2 = resid_norm2 ? resid_norm2 + off : nullptr;
-    rc = encode_f16_group(dict, ag, scratch + soff, sg[g]);
+    ag.atom = a.atom + off * K;
+    ag.angle_idx = a.angle_idx + off * K;
+    ag.angle = a.angle ? a.angle + off * K : nullptr;
+    ag.coef = a.coef + off * K;
+    ag.resid_norm2 = a.resid_norm2 ? a.resid_norm2 + off : nullptr;
+    if (h) {
+      if (g > 0 && cin[g - 1]) e = cudaStreamWaitEvent(sg[g], cin[g - 1], 0);
+      if (e == cudaSuccess) e = copy_in(*h, ag, off, Pg[g], vec, sg[g]);
+      if (e == cudaSuccess && cin[g]) e = cudaEventRecord(cin[g], sg[g]);
+      if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+    }
+    if (rc == RSC_OK) rc = encode_f16_group(dict, ag, scratch + soff, sg[g]);
+    if (rc == RSC_OK && h && (e = copy_out(*h, ag, off, Pg[g], K, sg[g])) != cudaSuccess)
+      rc = rsc_cuda_fail(e);
     off += Pg[g];
     soff += bytes[g];
   }
@@ -791,13 +897,34 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
     if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
   }
   if (fork) cudaEventDestroy(fork);
+  for (int g = 0; g < G; ++g)
+    if (cin[g]) cudaEventDestroy(cin[g]);
   for (int g = 1; g < G; ++g) {
     if (join[g]) cudaEventDestroy(join[g]);
     if (sg[g]) cudaStreamDestroy(sg[g]);
   }
-  e = cudaFreeAsync(scratch, st);
+  e = rsc_scratch_free(scratch, st);
   if (rc == RSC_OK && e != cudaSuccess) rc = rsc_cuda_fail(e);
   return rc;
+}
+
+}  // namespace
+
+int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
+               int32_t *atom, int32_t *angle_idx, float *angle, double *coef, float *resid_norm2,
+               void *stream) {
+  if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
+  if (P == 0) return RSC_OK;
+  if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
+  if (!aligned16(x) || !aligned_as<int32_t>(atom) || !aligned_as<int32_t>(angle_idx) ||
+      !aligned_as<double>(coef) || (angle && !aligned_as<float>(angle)) ||
+      (resid_norm2 && !aligned_as<float>(resid_norm2)))
+    return RSC_ERR_INVALID;
+  const int rc = check_device(dict);
+  if (rc != RSC_OK) return rc;
+  const RompArgs a = base_args(dict, x, P, K, atom, angle_idx, angle, coef, resid_norm2);
+  return encode_impl(dict, a, prec, reinterpret_cast<cudaStream_t>(stream), nullptr);
 }
 
 int rsc_workspace_bytes(const rsc_dict *dict, const rsc_basis *basis, int64_t P, int32_t n_images,
@@ -831,7 +958,11 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
   int rc = check_device(dict);
   if (rc != RSC_OK) return rc;
   const int64_t vec = (int64_t)dict->H * dict->J * 2;
-  const int64_t chunk = P < (1 << 18) ? P : (1 << 18);
+  // chunks of up to 2^20 patches, two in flight when there are more; within
+  // a chunk the stream groups overlap their copies with each other's kernels
+  const int64_t cap = (int64_t)1 << 20;
+  const int64_t chunk = P < cap ? P : cap;
+  const int nb = P > chunk ? 2 : 1;
   HostStage *hs = nullptr;
   {
     std::lock_guard<std::mutex> g(g_stage_mu);
@@ -839,7 +970,7 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
     hs = static_cast<HostStage *>(dict->host_stage);
   }
   std::lock_guard<std::mutex> lock(hs->mu);
-  cudaError_t e = hs->reserve(chunk, K, (int)vec);
+  cudaError_t e = hs->reserve(chunk, K, (int)vec, nb);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return RSC_ERR_OOM;
@@ -848,29 +979,12 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
   rc = RSC_OK;
   for (int64_t lo = 0, ci = 0; rc == RSC_OK && lo < P; lo += chunk, ++ci) {
     const int64_t n = (P - lo) < chunk ? (P - lo) : chunk;
-    HostStage::Buf &B = hs->b[ci & 1];
-    cudaStream_t st = hs->s[ci & 1];
-    e = cudaMemcpyAsync(B.x, x + lo * vec, n * vec * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-      rc = rsc_cuda_fail(e);
-      break;
-    }
-    rc = rsc_encode(dict, B.x, n, K, prec, B.atom, B.ang, angle ? B.angf : nullptr, B.coef,
-                    resid_norm2 ? B.rn2 : nullptr, st);
-    if (rc != RSC_OK) break;
-    e = cudaMemcpyAsync(atom + lo * K, B.atom, n * K * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(angle_idx + lo * K, B.ang, n * K * sizeof(int32_t),
-                          cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && angle)
-      e = cudaMemcpyAsync(angle + lo * K, B.angf, n * K * sizeof(float), cudaMemcpyDeviceToHost,
-                          st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(coef + lo * K, B.coef, n * K * sizeof(double), cudaMemcpyDeviceToHost,
-                          st);
-    if (e == cudaSuccess && resid_norm2)
-      e = cudaMemcpyAsync(resid_norm2 + lo, B.rn2, n * sizeof(float), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) rc = rsc_cuda_fail(e);
+    HostStage::Buf &B = hs->b[ci % nb];
+    const RompArgs a = base_args(dict, B.x, n, K, B.atom, B.ang, angle ? B.angf : nullptr, B.coef,
+                                 resid_norm2 ? B.rn2 : nullptr);
+    const HostIO h{x + lo * vec, atom + lo * K, angle_idx + lo * K, angle ? angle + lo * K : nullptr,
+                   coef + lo * K, resid_norm2 ? resid_norm2 + lo : nullptr};
+    rc = encode_impl(dict, a, prec, hs->s[ci % nb], &h);
   }
   for (int i = 0; i < 2; ++i) {
     const cudaError_t se = cudaStreamSynchronize(hs->s[i]);

@@ -286,3 +286,11 @@ int rsc_launch_f32(const RompArgs &a, cudaStream_t stream);
 
 // Records a CUDA error text for rsc_last_cuda_error and returns RSC_ERR_CUDA.
 int rsc_cuda_fail(cudaError_t e);
+
+// Per-call device scratch of the coders and the K-SVD update: stream-ordered
+// allocations from a memory pool per device that the library owns and that
+// keeps its memory between calls (rsc_capi.cu).  rsc_scratch_trim gives the
+// unused part back (rsc_dict_destroy calls it).
+cudaError_t rsc_scratch_alloc(void **p, size_t bytes, cudaStream_t st);
+cudaError_t rsc_scratch_free(void *p, cudaStream_t st);
+void rsc_scratch_trim();

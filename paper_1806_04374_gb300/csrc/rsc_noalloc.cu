@@ -3,7 +3,7 @@
 //
 // rsc_encode's FP16 path needs one scratch buffer per call: the list of
 // patches the tensor-core kernel hands to the FP32 kernel, plus its counter.
-// It takes that buffer from the stream-ordered allocator (cudaMallocAsync).
+// It takes that buffer from the library's stream-ordered memory pool.
 // Some callers cannot allocate while they code: a serving process that
 // reserves all of its device memory up front and forbids allocation in its
 // steady state, code running under another framework's memory pool, or a

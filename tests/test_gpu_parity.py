@@ -242,12 +242,15 @@ def test_empty_and_errors(rsc):
         rsc.Dictionary(torch.from_numpy(d).cuda(), 129)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "f16"])
-def test_host_entry_point_matches_device(rsc, precision):
-    """rsc_encode_host (chunked copies + coding on two streams) returns the
-    same codes as rsc_encode on device buffers."""
+@pytest.mark.parametrize("precision,P", [("fp32", 300_000), ("f16", 300_000),
+                                         ("f16", (1 << 20) + 5_000)])
+def test_host_entry_point_matches_device(rsc, precision, P):
+    """rsc_encode_host (chunks of up to 2^20 patches on two streams, each
+    stream group copying its own patches in and its outputs out) returns the
+    same codes as rsc_encode on device buffers; the larger case takes two
+    chunks."""
     import torch
-    d, x, _, wl = synth.workload_inputs("omp_1m", P=300_000)
+    d, x, _, wl = synth.workload_inputs("omp_1m", P=P)
     dic = rsc.Dictionary(torch.from_numpy(d).cuda(), wl.R)
     xd = torch.from_numpy(x).cuda()
     a = rsc.encode(dic, xd, wl.K, precision)

@@ -28,8 +28,10 @@ def test_every_tuning_gives_the_same_codes(rsc, sizes):
     dic = rsc.Dictionary(torch.from_numpy(d).cuda(), R)
     xd = torch.from_numpy(x).cuda()
     base = {k: v.cpu().numpy() for k, v in rsc.encode(dic, xd, K, "f16").items()}
-    dflt = rsc.rsc_dict_tuning(dic.handle, K)["score_stages"]
-    other = {6: 4, 4: 6, 5: 4}[dflt]
+    from paper_1806_04374_gb300 import autotune
+    opts = autotune.stage_options(dic)
+    assert len(opts) == 2, opts
+    dflt, other = opts
     for t in ({"groups": 1}, {"groups": 3, "group_min": 20000},
               {"refine_blocks_per_sm": 8, "score_stages": other},
               {"groups": 2, "refine_blocks_per_sm": 64, "score_stages": dflt}):
@@ -42,7 +44,8 @@ def test_every_tuning_gives_the_same_codes(rsc, sizes):
         for k in base:
             assert np.array_equal(out[k], base[k]), (t, k)
     with pytest.raises(rsc.RscError):
-        rsc.rsc_dict_set_tuning(dic.handle, score_stages=5 if dflt != 5 else 6)
+        rsc.rsc_dict_set_tuning(dic.handle, score_stages=next(v for v in range(2, 7)
+                                                            if v not in opts))
     with pytest.raises(rsc.RscError):
         rsc.rsc_dict_set_tuning(dic.handle, groups=7)
     rsc.rsc_dict_set_tuning(dic.handle, clear=True)
