@@ -26,6 +26,14 @@
  * every buffer it passes; the library owns only the rsc_dict handle and the
  * device memory behind it.  There is no CPU fallback: without a usable CUDA
  * device the calls return RSC_ERR_CUDA.
+ *
+ * Scratch: calls that need device scratch (rsc_encode's FP16 path, the image
+ * calls, the K-SVD update) take it in stream order from a memory pool per
+ * device that the library creates and owns.  The pool keeps the memory it has
+ * handed out between calls, so that a call does not map it again (it is not
+ * the device's default pool, whose settings the library leaves alone);
+ * rsc_dict_destroy gives the unused part back.  An allocation the pool
+ * cannot make gives RSC_ERR_OOM.
  */
 #ifndef RSC_H
 #define RSC_H
@@ -141,7 +149,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
  *               (pass it to rsc_dict_create for the next iteration).
  *   n_used    : device int32 [M] or NULL: patches that used each atom.
  *   stream    : cudaStream_t.  Returns after launch; scratch comes from the
- *               stream-ordered allocator.
+ *               library's scratch pool (see the top of this file).
  */
 int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
                     const int32_t *atom, const int32_t *angle_idx, const double *coef,
@@ -176,7 +184,7 @@ int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
  *               their old value.
  *   new_coef, n_used : as rsc_ksvd_update (n_used = count).
  * Both return after launch; rsc_ksvd_accumulate takes its per-patch scratch
- * from the stream-ordered allocator, rsc_ksvd_finish allocates nothing.
+ * from the library's scratch pool, rsc_ksvd_finish allocates nothing.
  */
 int rsc_ksvd_accumulate(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
                         const int32_t *atom, const int32_t *angle_idx, const double *coef,
@@ -237,7 +245,7 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *basis, const float 
 /*
  * rsc_workspace_bytes -- device memory that one rsc_encode (basis = NULL) or
  * rsc_encode_images (basis given; P = the windows of its n_images images)
- * call takes from the stream-ordered allocator for its own scratch while it
+ * call takes from the library's scratch pool for its own scratch while it
  * runs, for P patches, K steps and precision prec.  The paper has no
  * counterpart: a server uses it to admit requests by the device memory they
  * need (inputs and outputs, which the caller allocates, come on top).
@@ -262,7 +270,7 @@ int rsc_workspace_bytes(const rsc_dict *dict, const rsc_basis *basis, int64_t P,
  *   hist   : device, n_images x C int32: row i counts the labels of image
  *            i's windows (zero for images smaller than a window).
  *   Device scratch: about P x ((kmax+1) J 8 + K 16 + 12) bytes from the
- *   stream-ordered allocator.  Synchronises `stream` before returning.
+ *   library's scratch pool.  Synchronises `stream` before returning.
  */
 int rsc_classify_images(const rsc_dict *const *dicts, int32_t C, const rsc_basis *basis,
                         const float *const *images, const int32_t *h, const int32_t *w,
@@ -305,14 +313,16 @@ int rsc_synthesize(const rsc_basis *basis, const float *coef, int64_t P, float *
 /*
  * rsc_encode_host -- rsc_encode on HOST buffers (same shapes and meaning as
  * above, all pointers host memory; pinned memory gives the fastest copies).
- * Copies the patches to the device in chunks, codes them and copies the
- * results back, overlapping the copies of one chunk with the coding of the
- * next on two internal streams.  Blocks until every output is written.
- * Device memory for two chunks (up to 2^18 patches each) and the two streams
- * are made on the first call and kept with the dictionary, grown when a call
- * needs more, and released by rsc_dict_destroy: later calls allocate and
- * free nothing.  Calls on one dictionary from several host threads run one
- * at a time.
+ * Copies the patches to the device in chunks of up to 2^20, codes them and
+ * copies the results back; inside a chunk each of the FP16 path's stream
+ * groups copies its own patches in (one group after another) and its outputs
+ * out, so that copies overlap the other groups' kernels, and with more than
+ * one chunk the next chunk's work goes on a second internal stream.  Blocks
+ * until every output is written.  Device staging memory (one chunk's inputs
+ * and outputs, two chunks' when P > 2^20) and the two streams are made on
+ * the first call and kept with the dictionary, grown when a call needs more,
+ * and released by rsc_dict_destroy.  Calls on one dictionary from several
+ * host threads run one at a time.
  */
 int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
                     int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
@@ -326,7 +336,7 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
  * that must not meet an allocation failure or an allocator synchronisation
  * mid-request).  rsc_encode takes its one per-call scratch buffer (the list
  * of patches the tensor-core kernel hands to the FP32 kernel) from the
- * stream-ordered allocator; this call uses a fixed 4 MiB device array inside
+ * library's scratch pool; this call uses a fixed 4 MiB device array inside
  * the library instead and calls no cudaMalloc, cudaFree or other allocating
  * routine.  The paper has no counterpart: it is a property of this library.
  *   Arguments and outputs: as rsc_encode with prec = RSC_F16_RESCORE.
