@@ -400,9 +400,10 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
         // transform over H harmonics round at most 2J + 2H + 8 times, on
         // terms bounded by ||x|| (unit atoms, Cauchy-Schwarz) and by |a_i| for
         // the Gram terms, and the weights carry only their hi part; x4 margin.
-        // (K <= 5 only: for K = 8 the screen's code raises the register
-        // spills, and the image workload measured 2.2% faster without it)
-        constexpr bool kScreen = KK <= 5;
+        // (only the second pass runs more than one unit; at K = 8 the screen
+        // is built into that pass alone: 2.55 -> 2.18 ms per refine launch on
+        // the 21 x 21 image sizes, where windows hold many units)
+        constexpr bool kScreen = KK <= 5 || PASS == 2;
         float asum = 0.0f;
 #pragma unroll
         for (int i = 0; i < KK; ++i)
