@@ -314,9 +314,11 @@ __global__ void __launch_bounds__(kSThreads, 1)
               for (int u = 0; u < 16; ++u)
                 if (sub * 16 + u >= nv) f[u] = -1.0f;
             }
-            float h = -1.0f;
-#pragma unroll
-            for (int u = 0; u < 16; u += 2) h = fmax3(h, f[u], f[u + 1]);
+            // block maximum of the 16 values as a tree of depth 3
+            const float t0 = fmax3(f[0], f[1], f[2]), t1 = fmax3(f[3], f[4], f[5]);
+            const float t2 = fmax3(f[6], f[7], f[8]), t3 = fmax3(f[9], f[10], f[11]);
+            const float t4 = fmax3(f[12], f[13], f[14]);
+            const float h = fmax3(fmax3(t0, t1, t2), fmax3(t3, t4, f[15]), -1.0f);
 #pragma unroll
             for (int u = 0; u < 16; ++u) cmax[sub * 16 + u] = fmaxf(cmax[sub * 16 + u], f[u]);
             hm[sub] = h;
