@@ -774,10 +774,15 @@ def main():
     tuning = rsc.rsc_dict_tuning(dic.handle, K)
     # the same steps with the two halves serialised: each kernel timed alone
     iso_run = timed(args.precision, False, timing_mode=2, steps=min(args.steps, 10))
-    cmp_run = None
+    cmp_run = prune_run = None
     if args.precision != "fp32" and not args.no_fp32_compare:
         cmp_run = timed("fp32", False)
         parity_outputs["fp32"] = sample_outputs()
+        # the FP32 path with the exact |G| bound pruning: the same codes
+        prune_run = timed("fp32_prune", False, steps=min(args.steps, 5))
+        pruned = sample_outputs()
+        prune_run["same_codes"] = all(np.array_equal(pruned[k], parity_outputs["fp32"][k])
+                                      for k in pruned)
     step_ms, total_ms, clk = main_run["step_ms"], main_run["total_ms"], main_run["clocks"]
     ms_per_step = total_ms / args.steps
     value = world * P * args.steps / (total_ms / 1e3)
@@ -936,6 +941,16 @@ def main():
             line["fp32_path"] = {"value": v32, "unit": "patches/s",
                                  "ms_per_step": cmp_run["total_ms"] / args.steps,
                                  "speedup_of_headline": value / v32}
+        if prune_run is not None:
+            nst = min(args.steps, 5)
+            vp = world * P * nst / (prune_run["total_ms"] / 1e3)
+            line["fp32_prune_path"] = {
+                "value": vp, "unit": "patches/s", "ms_per_step": prune_run["total_ms"] / nst,
+                "over_fp32_path": vp / v32,
+                "same_codes_as_fp32_path": prune_run["same_codes"],
+                "note": "RSC_FP32_PRUNE: the angle transform only for atoms whose exact bound "
+                        "|G_0| + 2 sum_k |G_k| reaches the window of the running best; codes "
+                        "compared on the sampled patches of the last timed step"}
         if not args.no_extras and world == 1:
             line["projection"] = measure_projection(rsc, torch, dev, stream)
             line["rksvd"] = measure_rksvd(rsc, torch, dev)

@@ -58,6 +58,13 @@ extern "C" {
  * top-two margin of the exact scores exceeds their error bound. */
 #define RSC_FP32 0         /* FP32 CUDA-core contraction + angle DFT */
 #define RSC_F16_RESCORE 2 /* FP16 tcgen05 tensor-core scores, candidates re-scored */
+/* RSC_FP32 with the exact |G| bound pruning of the angle transform: an atom
+ * whose bound |G_0| + 2 sum_k |G_k| >= max_theta |score| (triangle inequality
+ * over the harmonics of Eq. (Sr)) cannot reach the window of the patch's
+ * running best is not transformed.  The same codes as RSC_FP32, bit for bit;
+ * on GB300 it is slower than RSC_FP32 (the transform it skips is cheap next
+ * to the contraction and the bound), so it is not the default. */
+#define RSC_FP32_PRUNE 3
 
 typedef struct {
   int32_t M;    /* atoms, >= 1 */
@@ -110,7 +117,7 @@ int rsc_dict_dims(const rsc_dict *dict, rsc_dims *dims);
  *   x         : device, P x (kmax+1) x J x 2 floats.
  *   P         : patches, >= 0 (0 is a no-op).
  *   K         : greedy steps, 1 <= K <= 16.
- *   prec      : RSC_FP32 or RSC_F16_RESCORE.  RSC_F16_RESCORE takes packed
+ *   prec      : RSC_FP32, RSC_FP32_PRUNE or RSC_F16_RESCORE.  RSC_F16_RESCORE takes packed
  *               lengths J (2 kmax + 1) <= 256 and K <= 8 (RSC_ERR_UNSUPPORTED
  *               otherwise); the dictionary's tables for it are built by
  *               rsc_dict_create when the sizes allow.

@@ -24,7 +24,8 @@ RSC_ERR_UNSUPPORTED = -5
 
 RSC_FP32 = 0
 RSC_F16_RESCORE = 2
-PRECISIONS = {"fp32": RSC_FP32, "f16": RSC_F16_RESCORE}
+RSC_FP32_PRUNE = 3
+PRECISIONS = {"fp32": RSC_FP32, "f16": RSC_F16_RESCORE, "fp32_prune": RSC_FP32_PRUNE}
 
 # every symbol include/rsc.h declares
 EXPORTS = (

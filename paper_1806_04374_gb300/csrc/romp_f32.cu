@@ -6,7 +6,10 @@
 //   (a) per-harmonic contraction G_k(m) = sum_j conj(d_m[j,k]) r[j,k], one
 //       lane per atom, FP32 FMA, the residual broadcast from shared memory;
 //   (b) angle transform score(m, r) = G_0 + 2 Re sum_k e^{ik 2 pi r / R} G_k,
-//       one lane per angle with its cos/sin factors held in registers;
+//       one lane per angle with its cos/sin factors held in registers; with
+//       RSC_FP32_PRUNE only for the atoms whose exact bound |G_0| +
+//       2 sum_k |G_k| >= max_r |score(m, r)| can still reach the window of
+//       the running best;
 //   (c) per-lane top-4 of |score| plus the largest discarded value, merged
 //       over the warp into every candidate within 2E of the best, where E
 //       bounds the FP32 error of a score; the candidates are re-scored in
@@ -39,8 +42,8 @@ struct Layout {
   int dT_off;             // transposed atoms [2][HJ][M] or -1 (read from global)
   // per-warp
   int warp_off, warp_bytes;
-  int x_off, rhi_off, rlo_off, g_off, cand_off, L_off, inv_off, z_off, a_off, adf_off, sel_off,
-      gram_off;
+  int x_off, rhi_off, rlo_off, g_off, ub_off, cand_off, L_off, inv_off, z_off, a_off, adf_off,
+      sel_off, gram_off;
   int acache_off;  // [K][HJ] float4: steered selected atoms (re hi, re lo, im hi, im lo)
   int total;
 };
@@ -64,6 +67,7 @@ __host__ __device__ inline Layout make_layout(int M, int J, int H, int R, int K,
   L.rhi_off = w;  w = align16(w + 2 * HJ * 4);
   L.rlo_off = w;  w = align16(w + 2 * HJ * 4);
   L.g_off = w;    w = align16(w + kChunk * GStride<KM>::v * 4);
+  L.ub_off = w;   w = align16(w + kChunk * 4);
   L.cand_off = w; w = align16(w + kCandCap * 4);
   L.L_off = w;    w = align16(w + K * (K + 1) / 2 * 8);
   L.inv_off = w;  w = align16(w + K * 8);
@@ -148,7 +152,7 @@ __device__ __forceinline__ float4 cdf_pack(const Cdf &a) {
 
 __device__ __forceinline__ Cdf cdf_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 
-template <int KM, int RPL>
+template <int KM, int RPL, bool PRUNE>
 __global__ void __launch_bounds__(256)
     romp_f32_kernel(RompArgs a, int dT_in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(256)
   float *s_rhi = reinterpret_cast<float *>(wbase + Lo.rhi_off);
   float *s_rlo = reinterpret_cast<float *>(wbase + Lo.rlo_off);
   float *s_g = reinterpret_cast<float *>(wbase + Lo.g_off);
+  float *s_ub = reinterpret_cast<float *>(wbase + Lo.ub_off);
   int *s_cand = reinterpret_cast<int *>(wbase + Lo.cand_off);
   double *s_L = reinterpret_cast<double *>(wbase + Lo.L_off);
   double *s_inv = reinterpret_cast<double *>(wbase + Lo.inv_off);  // 1 / L_ii
@@ -293,10 +298,21 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int q = 0; q < GS / 4; ++q)
               g4[q] = make_float4(gv[4 * q], gv[4 * q + 1], gv[4 * q + 2], gv[4 * q + 3]);
+            if constexpr (PRUNE) {
+              // |score(m, r)| <= |G_0| + 2 sum_k |G_k| for every angle
+              // (triangle inequality; gv holds G_0 and 2 Re / -2 Im of G_k),
+              // times a slack covering the FP32 rounding of this sum and of
+              // the transform below, so every FP32 score of the atom is <= ub
+              float ub = fabsf(gv[0]);
+#pragma unroll
+              for (int k = 1; k <= KM; ++k)
+                if (k <= kmax) ub += sqrtf(fmaf(gv[2 * k - 1], gv[2 * k - 1], gv[2 * k] * gv[2 * k]));
+              s_ub[ml] = ub * (1.0f + 16.0f * (KM + 2) * 5.9604644775390625e-8f);
+            }
           }
           __syncwarp();
           // (b) one lane per angle, (c) per-lane top-4
-          for (int ml = 0; ml < mend; ++ml) {
+          auto transform = [&](int ml) {
             const float4 *g4 = reinterpret_cast<const float4 *>(s_g + ml * GS);
             float gv[GS];
 #pragma unroll
@@ -320,6 +336,29 @@ __global__ void __launch_bounds__(256)
               // a value more than 2E below this lane's running best is below
               // the final window and need not be kept (the best only grows)
               if (r < R && !(v < tv[0] - win2)) top4_insert(tv, ti, disc, v, (mc + ml) * R + r);
+            }
+          };
+          if constexpr (!PRUNE) {
+            for (int ml = 0; ml < mend; ++ml) transform(ml);
+          } else {
+            // In index order, an atom whose bound is below the warp's running
+            // best minus the window 2E (refreshed every 8 atoms; a stale best
+            // is lower, so only more atoms are transformed) is skipped: every
+            // FP32 score of it is below best - 2E <= the final threshold
+            // s1 - 2E (the best only grows), so none of them could be a
+            // candidate or raise a lane's discarded value to the threshold;
+            // the best atom is never skipped (its bound is >= its score).
+            // Measured at M = 64, R = 64, K = 5 (400,000 patches): with the
+            // chunk's largest-bound atom first the bound rules out 52% of the
+            // transforms, yet that loop takes 1.55x the plain loop's time and
+            // this one 1.3x; the same loop transforming every atom takes
+            // 1.06x.  The plain loop's unbroken run of short FMA chains
+            // pipelines better than any loop with a data-dependent skip.
+            float wbest = -INFINITY;
+            for (int ml = 0; ml < mend; ++ml) {
+              if ((ml & 7) == 0) wbest = warp_max(tv[0]);
+              if (s_ub[ml] < wbest - win2) continue;
+              transform(ml);
             }
           }
           __syncwarp();
@@ -487,8 +526,8 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <int KM, int RPL>
-int launch_t(const RompArgs &a, cudaStream_t stream) {
+template <int KM, int RPL, bool PRUNE>
+int launch_p(const RompArgs &a, cudaStream_t stream) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
@@ -513,7 +552,7 @@ int launch_t(const RompArgs &a, cudaStream_t stream) {
     }
   }
   if (L.total > max_optin) return RSC_ERR_UNSUPPORTED;
-  auto kern = romp_f32_kernel<KM, RPL>;
+  auto kern = romp_f32_kernel<KM, RPL, PRUNE>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   int per_sm = 0;
@@ -529,6 +568,11 @@ int launch_t(const RompArgs &a, cudaStream_t stream) {
   e = cudaGetLastError();
   if (e != cudaSuccess) return rsc_cuda_fail(e);
   return RSC_OK;
+}
+
+template <int KM, int RPL>
+int launch_t(const RompArgs &a, cudaStream_t stream) {
+  return a.prune ? launch_p<KM, RPL, true>(a, stream) : launch_p<KM, RPL, false>(a, stream);
 }
 
 }  // namespace

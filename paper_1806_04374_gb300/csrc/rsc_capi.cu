@@ -817,10 +817,12 @@ int encode_impl(const rsc_dict *dict, const RompArgs &a, int32_t prec, cudaStrea
   const int K = a.K;
   int rc = RSC_OK;
   cudaError_t e = cudaSuccess;
-  if (prec == RSC_FP32) {
+  if (prec == RSC_FP32 || prec == RSC_FP32_PRUNE) {
     if (h && (e = copy_in(*h, a, 0, P, vec, st)) != cudaSuccess) return rsc_cuda_fail(e);
+    RompArgs af = a;
+    af.prune = prec == RSC_FP32_PRUNE;
     const int slot = timing_begin(dict, 0, st);
-    rc = rsc_launch_f32(a, st);
+    rc = rsc_launch_f32(af, st);
     timing_end(dict, slot, st);
     if (rc == RSC_OK && h && (e = copy_out(*h, a, 0, P, K, st)) != cudaSuccess)
       rc = rsc_cuda_fail(e);
@@ -914,7 +916,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
                int32_t *atom, int32_t *angle_idx, float *angle, double *coef, float *resid_norm2,
                void *stream) {
   if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
-  if (prec != RSC_FP32 && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_FP32_PRUNE && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
   if (P == 0) return RSC_OK;
   if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
   if (!aligned16(x) || !aligned_as<int32_t>(atom) || !aligned_as<int32_t>(angle_idx) ||
@@ -930,7 +932,7 @@ int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32
 int rsc_workspace_bytes(const rsc_dict *dict, const rsc_basis *basis, int64_t P, int32_t n_images,
                         int32_t K, int32_t prec, uint64_t *bytes) {
   if (!dict || !bytes || P < 0 || n_images < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
-  if (prec != RSC_FP32 && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_FP32_PRUNE && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
   uint64_t total = 0;
   if (P > 0 && prec == RSC_F16_RESCORE) {
     int64_t Pg[kMaxGroups] = {};
@@ -952,7 +954,7 @@ int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, 
                     int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
                     float *resid_norm2) {
   if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
-  if (prec != RSC_FP32 && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
+  if (prec != RSC_FP32 && prec != RSC_FP32_PRUNE && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
   if (P == 0) return RSC_OK;
   if (!x || !atom || !angle_idx || !coef) return RSC_ERR_INVALID;
   int rc = check_device(dict);

@@ -279,6 +279,8 @@ struct RompArgs {
   const int *resume_sI = nullptr;
   int64_t resume_P = 0;
   int resume_cap = 0;
+  // the exact |G| bound pruning of the angle transform (RSC_FP32_PRUNE)
+  int prune = 0;
 };
 
 // FP32 CUDA-core scoring path (romp_f32.cu).

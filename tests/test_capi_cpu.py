@@ -76,3 +76,17 @@ def test_workspace_query_argument_checks(lib):
     with pytest.raises(rsc.RscError):
         rsc.rsc_workspace_bytes(0, None, 10, 1, 5, rsc.RSC_FP32)
     assert lib.rsc_dict_set_limits(vp(None), 1, 1) == rsc.RSC_ERR_INVALID
+
+
+def test_binding_constants_match_the_header():
+    """Every #define of include/rsc.h (status codes, precisions) has the same
+    value in the Python binding."""
+    import re
+    import paper_1806_04374_gb300 as rsc
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "rsc.h")).read()
+    defs = dict(re.findall(r"#define (RSC_[A-Z0-9_]+) \(?(-?\d+)\)?", hdr))
+    assert {"RSC_OK", "RSC_FP32", "RSC_F16_RESCORE", "RSC_FP32_PRUNE"} <= set(defs)
+    for name, v in defs.items():
+        assert getattr(rsc, name) == int(v), name
+    assert rsc.PRECISIONS == {"fp32": 0, "f16": 2, "fp32_prune": 3}
