@@ -25,6 +25,11 @@ the coding runs in the library's kernels.
   request's codes are the same alone and in any batch.
 * Times.  Each request records when it was submitted, admitted, started and
   finished (host clock, seconds); ``latency_summary`` gives p50 / p99.
+* Failures.  A request that has not been admitted yet can be withdrawn
+  (``Request.cancel``; its ``result`` raises ``Cancelled``).  When a batched
+  call fails, each of its requests is coded again alone, so that only the
+  requests that fail by themselves report the error (``result`` raises it);
+  the worker goes on with the queue.
 """
 from __future__ import annotations
 
@@ -43,14 +48,19 @@ class AdmissionError(ValueError):
     """The request alone needs more device memory than the server's budget."""
 
 
+class Cancelled(RuntimeError):
+    """The request was withdrawn before it was admitted."""
+
+
 class Request:
     """One submitted image.  ``result()`` waits for and returns its codes:
     numpy arrays atom, angle_idx [W, K] int32, angle [W, K] float32, coef
     [W, K] float64 and resid_norm2 [W] float32, W = its windows in row-major
     order."""
 
-    def __init__(self, rid, image: np.ndarray, N: int):
+    def __init__(self, rid, image: np.ndarray, N: int, server=None):
         self.id = rid
+        self._server = server
         self.image = image
         self.h, self.w = image.shape
         self.windows = max(self.h - N + 1, 0) * max(self.w - N + 1, 0)
@@ -67,6 +77,11 @@ class Request:
 
     def wait(self, timeout=None) -> bool:
         return self._done.wait(timeout)
+
+    def cancel(self) -> bool:
+        """Withdraws the request if it is still waiting for admission; returns
+        whether it was withdrawn (False once a worker has taken it)."""
+        return self._server is not None and self._server._cancel(self)
 
     def result(self, timeout=None) -> dict:
         if not self._done.wait(timeout):
@@ -136,7 +151,7 @@ class Server:
             if rid is None:
                 rid = self._next_id
             self._next_id += 1
-        r = Request(rid, image, self.basis.N)
+        r = Request(rid, image, self.basis.N, self)
         r.need = self.need_bytes([r])
         if r.need > self.mem_budget:
             raise AdmissionError(f"request {rid} needs {r.need} bytes of device memory, "
@@ -145,6 +160,18 @@ class Server:
             self._queue.append(r)
             self._cv.notify_all()
         return r
+
+    def _cancel(self, r: Request) -> bool:
+        with self._cv:
+            try:
+                self._queue.remove(r)
+            except ValueError:
+                return False
+            r.error = Cancelled(f"request {r.id} withdrawn before admission")
+            r.t_done = time.perf_counter()
+            r._done.set()
+            self._cv.notify_all()
+        return True
 
     def close(self, wait: bool = True):
         with self._cv:
@@ -200,33 +227,49 @@ class Server:
             if got is None:
                 return
             batch, need = got
-            err, codes = None, None
-            try:
-                now = time.perf_counter()
-                for r in batch:
-                    r.t_start = now
-                with torch.cuda.stream(stream):
-                    imgs = [torch.from_numpy(r.image).pin_memory().to(self.device, non_blocking=True)
-                            for r in batch]
-                    out = _rsc.encode_images(self.dic, self.basis, imgs, self.K, self.precision,
-                                             stream=stream)
-                    codes = {k: v.cpu().numpy() for k, v in out.items()}
-                    del out, imgs
-            except Exception as e:  # noqa: BLE001 -- handed to the waiting callers
-                err = e
             now = time.perf_counter()
-            lo = 0
             for r in batch:
-                if err is None:
-                    r.codes = {k: v[lo:lo + r.windows] for k, v in codes.items()}
+                r.t_start = now
+            try:
+                results = self._code(batch, stream)
+            except Exception as e:  # noqa: BLE001 -- retried alone, then handed to the callers
+                if len(batch) == 1:
+                    results = [e]
                 else:
-                    r.error = err
-                lo += r.windows
+                    results = []
+                    for r in batch:
+                        try:
+                            results.append(self._code([r], stream)[0])
+                        except Exception as e1:  # noqa: BLE001
+                            results.append(e1)
+            now = time.perf_counter()
+            for r, res in zip(batch, results):
+                if isinstance(res, Exception):
+                    r.error = res
+                else:
+                    r.codes = res
                 r.t_done = now
                 r._done.set()
             with self._cv:
                 self.reserved -= need
                 self._cv.notify_all()
+
+    def _code(self, batch, stream) -> list:
+        """One rsc_encode_images call over `batch` on `stream`; returns each
+        request's codes (host numpy arrays, its windows in row-major order)."""
+        import torch
+        with torch.cuda.stream(stream):
+            imgs = [torch.from_numpy(r.image).pin_memory().to(self.device, non_blocking=True)
+                    for r in batch]
+            out = _rsc.encode_images(self.dic, self.basis, imgs, self.K, self.precision,
+                                     stream=stream)
+            codes = {k: v.cpu().numpy() for k, v in out.items()}
+            del out, imgs
+        res, lo = [], 0
+        for r in batch:
+            res.append({k: v[lo:lo + r.windows] for k, v in codes.items()})
+            lo += r.windows
+        return res
 
 
 def latency_summary(requests) -> dict:

@@ -85,3 +85,81 @@ def test_admission_by_device_memory(setup):
     # the codes are those of the images coded alone
     with serve.Server(dic, basis, K, "f16", slots=1) as srv:
         assert _equal(srv.submit(mid).result(timeout=60), cb)
+
+
+class _Gate:
+    """Wraps encode_images: calls wait until the test opens the gate, and a
+    call whose batch holds an image of shape `poison` raises (a failure made
+    on the host, before any device work)."""
+
+    def __init__(self, rsc, poison=None):
+        import threading
+        self.real, self.poison = rsc.encode_images, poison
+        self.open = threading.Event()
+        self.calls = []
+
+    def __call__(self, dic, basis, imgs, K, precision, **kw):
+        self.open.wait(60)
+        shapes = [tuple(im.shape) for im in imgs]
+        self.calls.append(shapes)
+        if self.poison in shapes:
+            raise RuntimeError("injected failure")
+        return self.real(dic, basis, imgs, K, precision, **kw)
+
+
+def test_cancel_before_admission(setup, monkeypatch):
+    from paper_1806_04374_gb300 import serve
+    rsc, dic, basis, images = setup
+    gate = _Gate(rsc)
+    monkeypatch.setattr(rsc, "encode_images", gate)
+    with serve.Server(dic, basis, K, "f16", slots=1, batch_windows=1) as srv:
+        ra = srv.submit(images[0])
+        for _ in range(600):  # the one worker has taken ra and waits at the gate
+            if ra.t_admit is not None:
+                break
+            import time
+            time.sleep(0.01)
+        assert ra.t_admit is not None
+        rb, rc = srv.submit(images[1]), srv.submit(images[2])
+        assert rb.cancel() and not rb.cancel()
+        assert not ra.cancel()  # already taken
+        gate.open.set()
+        ca, cc = ra.result(timeout=60), rc.result(timeout=60)
+        with pytest.raises(serve.Cancelled):
+            rb.result(timeout=60)
+    assert len(gate.calls) == 2  # rb was never coded
+    # the others' codes are those of a direct call
+    monkeypatch.undo()
+    for im, c in ((images[0], ca), (images[2], cc)):
+        import torch
+        d = rsc.encode_images(dic, basis, [torch.from_numpy(im).cuda()], K, "f16")
+        assert _equal({k: v.cpu().numpy() for k, v in d.items()}, c)
+
+
+def test_a_failing_request_fails_alone(setup, monkeypatch):
+    from paper_1806_04374_gb300 import serve
+    rsc, dic, basis, images = setup
+    bad = synth.make_line_image(37, 41, 0.01, 20180813)
+    with serve.Server(dic, basis, K, "f16", slots=1, batch_windows=1 << 20) as srv:
+        clean = [srv.submit(im).result(timeout=60) for im in images[:4]]
+    gate = _Gate(rsc, poison=bad.shape)
+    monkeypatch.setattr(rsc, "encode_images", gate)
+    with serve.Server(dic, basis, K, "f16", slots=1, batch_windows=1 << 20) as srv:
+        first = srv.submit(images[0])  # taken at once, held at the gate
+        for _ in range(600):
+            if first.t_admit is not None:
+                break
+            import time
+            time.sleep(0.01)
+        rest = [srv.submit(im) for im in (images[1], bad, images[2], images[3])]
+        gate.open.set()
+        assert _equal(first.result(timeout=60), clean[0])
+        with pytest.raises(RuntimeError, match="injected"):
+            rest[1].result(timeout=60)
+        for r, c in zip((rest[0], rest[2], rest[3]), clean[1:]):
+            assert _equal(r.result(timeout=60), c)
+        # the queued four went in one call, which failed; then one call each
+        assert max(len(c) for c in gate.calls) == 4
+        assert sum(1 for c in gate.calls if len(c) == 1) >= 4
+        # and the server goes on serving
+        assert _equal(srv.submit(images[1]).result(timeout=60), clean[1])
