@@ -773,6 +773,7 @@ extern "C" {
 
 int rsc_basis_create(int32_t N, int32_t J, int32_t kmax, double ring_width, double ring_spacing,
                      rsc_basis **out) {
+  RscRange nvtx_range("rsc_basis_create");
   if (!out) return RSC_ERR_INVALID;
   *out = nullptr;
   if (N < 1 || J < 1 || kmax < 0) return RSC_ERR_INVALID;
@@ -990,6 +991,7 @@ int rsc_basis_info(const rsc_basis *b, int32_t *npix, int32_t *n) {
 
 int rsc_project(const rsc_basis *b, const float *image, int32_t h, int32_t w, float *coef,
                 void *stream) {
+  RscRange nvtx_range("rsc_project");
   if (!b || h < 0 || w < 0) return RSC_ERR_INVALID;
   if (h < b->N || w < b->N) return RSC_OK;  // no complete window
   if (!image || !coef) return RSC_ERR_INVALID;
@@ -1017,6 +1019,7 @@ int rsc_encode_images(const rsc_dict *dict, const rsc_basis *b, const float *con
                       const int32_t *h, const int32_t *w, int32_t n_images, int32_t K,
                       int32_t prec, int32_t *atom, int32_t *angle_idx, float *angle,
                       double *coef, float *resid_norm2, void *stream) {
+  RscRange nvtx_range("rsc_encode_images");
   if (!dict || !b || n_images < 0 || (n_images > 0 && (!images || !h || !w)))
     return RSC_ERR_INVALID;
   if (b->J != dict->J || b->kmax != dict->kmax) return RSC_ERR_INVALID;
@@ -1064,6 +1067,7 @@ int rsc_classify_images(const rsc_dict *const *dicts, int32_t C, const rsc_basis
                         const float *const *images, const int32_t *h, const int32_t *w,
                         int32_t n_images, int32_t K, int32_t prec, int32_t *labels,
                         int32_t *hist, void *stream) {
+  RscRange nvtx_range("rsc_classify_images");
   if (!dicts || C < 1 || C > 4096 || !b || n_images < 0 || !hist ||
       (n_images > 0 && (!images || !h || !w)) || K < 1 || K > kMaxK)
     return RSC_ERR_INVALID;

@@ -638,6 +638,7 @@ int ksvd_finish(KsvdArgs &a, cudaStream_t st) {
 extern "C" int rsc_ksvd_update(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
                                const int32_t *atom, const int32_t *angle_idx, const double *coef,
                                float *new_coef, int32_t *n_used, void *stream) {
+  RscRange nvtx_range("rsc_ksvd_update");
   if (!x || !atom || !angle_idx || !coef || !new_coef) return RSC_ERR_INVALID;
   KsvdArgs a;
   int rc = ksvd_setup(dict, P, K, a);
@@ -684,6 +685,7 @@ extern "C" int rsc_ksvd_accumulate(const rsc_dict *dict, const float *x, int64_t
                                    const int32_t *atom, const int32_t *angle_idx,
                                    const double *coef, double *C, int32_t *count, float *top_err,
                                    int64_t *top_idx, float *top_vec, int32_t ntop, void *stream) {
+  RscRange nvtx_range("rsc_ksvd_accumulate");
   if (!x || !atom || !angle_idx || !coef || !C || !count) return RSC_ERR_INVALID;
   if (ntop < 0 || ntop > kTopMax || (ntop > 0 && (!top_err || !top_idx || !top_vec)))
     return RSC_ERR_INVALID;
@@ -706,6 +708,7 @@ extern "C" int rsc_ksvd_accumulate(const rsc_dict *dict, const float *x, int64_t
 extern "C" int rsc_ksvd_finish(const rsc_dict *dict, const double *C, const int32_t *count,
                                const int64_t *top_idx, const float *top_vec, int32_t ntop,
                                float *new_coef, int32_t *n_used, void *stream) {
+  RscRange nvtx_range("rsc_ksvd_finish");
   if (!dict || !C || !count || !new_coef) return RSC_ERR_INVALID;
   if (ntop < 0 || ntop > kTopMax || (ntop > 0 && (!top_idx || !top_vec))) return RSC_ERR_INVALID;
   int dev = -1;

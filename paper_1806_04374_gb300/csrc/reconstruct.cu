@@ -73,6 +73,7 @@ unsigned grid_for(int64_t total, int device) {
 extern "C" int rsc_reconstruct(const rsc_dict *dict, int64_t P, int32_t K, const int32_t *atom,
                                const int32_t *angle_idx, const double *coef, float *out,
                                void *stream) {
+  RscRange nvtx_range("rsc_reconstruct");
   if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
   if (P == 0) return RSC_OK;
   if (!atom || !angle_idx || !coef || !out) return RSC_ERR_INVALID;
@@ -92,6 +93,7 @@ extern "C" int rsc_reconstruct(const rsc_dict *dict, int64_t P, int32_t K, const
 
 extern "C" int rsc_synthesize(const rsc_basis *basis, const float *coef, int64_t P, float *pixels,
                               void *stream) {
+  RscRange nvtx_range("rsc_synthesize");
   if (!basis || P < 0) return RSC_ERR_INVALID;
   if (P == 0) return RSC_OK;
   if (!coef || !pixels) return RSC_ERR_INVALID;

@@ -634,6 +634,7 @@ const char *rsc_status_string(int s) {
 }
 
 int rsc_dict_create(const float *coef, rsc_dims dims, void *stream, rsc_dict **out) {
+  RscRange nvtx_range("rsc_dict_create");
   if (!out) return RSC_ERR_INVALID;
   *out = nullptr;
   if (!coef || !aligned16(coef)) return RSC_ERR_INVALID;
@@ -869,7 +870,10 @@ int encode_impl(const rsc_dict *dict, const RompArgs &a, int32_t prec, cudaStrea
   }
   int64_t off = 0;
   size_t soff = 0;
+  static const char *const kGroupRange[kMaxGroups] = {"rsc_encode group 0", "rsc_encode group 1",
+                                                      "rsc_encode group 2", "rsc_encode group 3"};
   for (int g = 0; g < G && rc == RSC_OK; ++g) {
+    RscRange nvtx_group(kGroupRange[g]);
     RompArgs ag = a;
     ag.x = a.x + off * vec;
     ag.P = Pg[g];
@@ -915,6 +919,7 @@ int encode_impl(const rsc_dict *dict, const RompArgs &a, int32_t prec, cudaStrea
 int rsc_encode(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
                int32_t *atom, int32_t *angle_idx, float *angle, double *coef, float *resid_norm2,
                void *stream) {
+  RscRange nvtx_range("rsc_encode");
   if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
   if (prec != RSC_FP32 && prec != RSC_FP32_PRUNE && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
   if (P == 0) return RSC_OK;
@@ -953,6 +958,7 @@ int rsc_workspace_bytes(const rsc_dict *dict, const rsc_basis *basis, int64_t P,
 int rsc_encode_host(const rsc_dict *dict, const float *x, int64_t P, int32_t K, int32_t prec,
                     int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
                     float *resid_norm2) {
+  RscRange nvtx_range("rsc_encode_host");
   if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
   if (prec != RSC_FP32 && prec != RSC_FP32_PRUNE && prec != RSC_F16_RESCORE) return RSC_ERR_INVALID;
   if (P == 0) return RSC_OK;

@@ -50,6 +50,7 @@ int scratch_for_current_device(int **out) {
 extern "C" int rsc_encode_noalloc(const rsc_dict *dict, const float *x, int64_t P, int32_t K,
                                   int32_t *atom, int32_t *angle_idx, float *angle, double *coef,
                                   float *resid_norm2, void *stream) {
+  RscRange nvtx_range("rsc_encode_noalloc");
   if (!dict || P < 0 || K < 1 || K > kMaxK) return RSC_ERR_INVALID;
   if (P > kNoAllocMaxPatches) return RSC_ERR_UNSUPPORTED;
   if (P == 0) return RSC_OK;
