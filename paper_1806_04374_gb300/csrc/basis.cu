@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "rsc_internal.h"
+#include "rsc_trace.h"
 #include "tc_ptx.cuh"
 
 #include <cuda_fp16.h>

@@ -29,6 +29,7 @@
 
 #include "df.cuh"
 #include "rsc_internal.h"
+#include "rsc_trace.h"
 
 namespace {
 

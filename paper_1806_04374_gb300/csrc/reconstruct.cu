@@ -10,6 +10,7 @@
 //   (patch, pixel), with the basis's real synthesis matrix (FP32, [n][npix],
 //   columns in the packed order: Re of k = 0, then sqrt2 Re and sqrt2 Im).
 #include "rsc_internal.h"
+#include "rsc_trace.h"
 
 namespace {
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "rsc_internal.h"
+#include "rsc_trace.h"
 
 namespace {
 

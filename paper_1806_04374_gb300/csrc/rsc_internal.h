@@ -2,7 +2,6 @@
 #pragma once
 
 #include <cuda.h>
-#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -289,16 +288,6 @@ int rsc_launch_f32(const RompArgs &a, cudaStream_t stream);
 
 // Records a CUDA error text for rsc_last_cuda_error and returns RSC_ERR_CUDA.
 int rsc_cuda_fail(cudaError_t e);
-
-// NVTX range over a scope: a tracing tool (Nsight Systems, ncu --nvtx) shows
-// the library's calls and the FP16 path's stream groups by name; without a
-// tool attached the calls return at once.
-struct RscRange {
-  explicit RscRange(const char *name) { nvtxRangePushA(name); }
-  ~RscRange() { nvtxRangePop(); }
-  RscRange(const RscRange &) = delete;
-  RscRange &operator=(const RscRange &) = delete;
-};
 
 // Per-call device scratch of the coders and the K-SVD update: stream-ordered
 // allocations from a memory pool per device that the library owns and that

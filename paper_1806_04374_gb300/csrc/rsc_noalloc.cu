@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "rsc_internal.h"
+#include "rsc_trace.h"
 
 namespace {
 
