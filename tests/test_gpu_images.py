@@ -157,3 +157,41 @@ def test_code_gpu_projection_at_full_margin(rsc, shape, precision):
     assert np.allclose(g1["coef"], g["coef"], rtol=0, atol=1e-12 * np.abs(g["coef"]).max())
     dic.close()
     b.close()
+
+
+def test_image_workload_full_size_sampled(rsc):
+    """The 21 x 21 image workload in the launch configuration the bench times
+    (its first 8 images, about 775,000 windows, one rsc_encode_images call,
+    the tuned groups and ring depth): 160 seeded windows checked against the
+    FP64 oracle run on the GPU's projected coefficients of those windows, at
+    the 1e-6 selection margin and the 1e-3 weight tolerance of the FP16 path."""
+    import torch
+    N, J, kmax, M, R, K = 21, 10, 12, 256, 128, 8
+    rng = np.random.default_rng(20180621)
+    sides = rng.integers(64, 513, size=512)[:8]
+    ims = [torch.from_numpy(synth.make_line_image(int(s), int(s), 0.01, 20180621 + i)).cuda()
+           for i, s in enumerate(sides)]
+    d = synth.make_dictionary(M, J, kmax, 20180622)
+    b = rsc.Basis(N, J, kmax)
+    dic = rsc.Dictionary(torch.from_numpy(d).cuda(), R)
+    out = rsc.encode_images(dic, b, ims, K, "f16")
+    torch.cuda.synchronize()
+    assert rsc.rsc_dict_check(dic.handle) == 0
+    P = out["atom"].shape[0]
+    assert P == sum((int(s) - N + 1) ** 2 for s in sides)
+    idx = np.sort(np.random.default_rng(20181220).choice(P, 160, replace=False))
+    # the sampled windows' coefficients, projected by the GPU image by image
+    xs, lo = [], 0
+    for t in ims:
+        c = rsc.project(b, t).reshape(-1, kmax + 1, J, 2)
+        sel = idx[(idx >= lo) & (idx < lo + c.shape[0])] - lo
+        xs.append(c[torch.from_numpy(sel).cuda()].cpu().numpy())
+        lo += c.shape[0]
+        del c
+    x = np.concatenate(xs)
+    g = {k: v[torch.from_numpy(idx).cuda()].cpu().numpy() for k, v in out.items()}
+    s = check(x, d, R, K, g, coef_tol=1e-3, margin=1e-6)
+    print("c2 full-size sample", P, s)
+    assert s["pinned_steps"] > 0.8 * x.shape[0] * K
+    dic.close()
+    b.close()
