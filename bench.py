@@ -527,45 +527,58 @@ def measure_rksvd(rsc, torch, dev, iters: int = 20) -> dict:
             "timing": "host clock around the whole loop (encode + update + sync per iteration)"}
 
 
-def run_c2(args) -> None:
+def measure_c2_full(rsc, torch, dev, n_images: int = 512, precision: str = "f16") -> dict:
     """The 21 x 21-patch image workload at full size: 512 images of side
     U{64..512} (square line textures, synth.make_line_image, 0.01 lines per
     pixel, standing in for the rendered texture images), every
     stride-1 window (about 4.5 x 10^7 patches) projected (N = 21, J = 10,
     kmax = 12, n = 250) and coded (M = 256, R = 128, K = 8) in one
-    rsc_encode_images call on the FP16 path.  Host clock around the call,
-    after a warm-up call on two images."""
+    rsc_encode_images call.  Host clock around the blocking call, after a
+    warm-up call on two images."""
+    N, J, kmax, M, R, K = 21, 10, 12, 256, 128, 8
+    rng = np.random.default_rng(20180621)
+    sides = rng.integers(64, 513, size=512)[:n_images]
+    imgs = [torch.from_numpy(synth.make_line_image(int(s_), int(s_), 0.01, 20180621 + i)).to(dev)
+            for i, s_ in enumerate(sides)]
+    basis = rsc.Basis(N, J, kmax)
+    dic = rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180622)).to(dev), R)
+    out = rsc.encode_images(dic, basis, imgs[:2], K, precision)
+    del out
+    torch.cuda.synchronize(dev)
+    rsc.rsc_dict_fallback_count(dic.handle)
+    t0 = time.perf_counter()
+    out = rsc.encode_images(dic, basis, imgs, K, precision)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    P = int(out["atom"].shape[0])
+    steps = float((out["atom"] >= 0).sum().item()) / P
+    res = {"value": P / dt, "unit": "patches/s", "s": dt, "patches": P, "images": len(sides),
+           "mean_steps_taken": steps, "handoffs": rsc.rsc_dict_fallback_count(dic.handle),
+           "precision": precision,
+           "config": f"{len(sides)} images, side U{{64..512}}, N=21 (349 px), J=10, "
+                     "kmax=12 (n=250), M=256, R=128, K=8; projection + coding in one "
+                     "rsc_encode_images call, host clock"}
+    del out, imgs
+    dic.close()
+    basis.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_c2(args) -> None:
+    """``bench.py --c2``: the full-size image workload alone, as one JSON line."""
     import torch
     import paper_1806_04374_gb300 as rsc
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     rsc.load_library()
-    N, J, kmax, M, R, K = 21, 10, 12, 256, 128, 8
-    rng = np.random.default_rng(20180621)
-    sides = rng.integers(64, 513, size=512)[:args.c2_images]
-    imgs = [torch.from_numpy(synth.make_line_image(int(s_), int(s_), 0.01, 20180621 + i)).to(dev)
-            for i, s_ in enumerate(sides)]
-    basis = rsc.Basis(N, J, kmax)
-    dic = rsc.Dictionary(torch.from_numpy(synth.make_dictionary(M, J, kmax, 20180622)).to(dev), R)
-    out = rsc.encode_images(dic, basis, imgs[:2], K, args.precision)
-    del out
-    torch.cuda.synchronize(dev)
-    rsc.rsc_dict_fallback_count(dic.handle)
-    t0 = time.perf_counter()
-    out = rsc.encode_images(dic, basis, imgs, K, args.precision)
-    torch.cuda.synchronize(dev)
-    dt = time.perf_counter() - t0
-    P = int(out["atom"].shape[0])
-    steps = float((out["atom"] >= 0).sum().item()) / P
+    r = measure_c2_full(rsc, torch, dev, args.c2_images, args.precision)
     print(json.dumps({
-        "metric": "image workload patches/s (projection + coding, one call)", "value": P / dt,
+        "metric": "image workload patches/s (projection + coding, one call)", "value": r["value"],
         "unit": "patches/s", "n_gpus": 1, "dtype": "f16" if args.precision == "f16" else "f32",
-        "data": "synthetic", "s": dt, "patches": P, "mean_steps_taken": steps,
-        "handoffs": rsc.rsc_dict_fallback_count(dic.handle),
-        "config": {"workload": f"{len(sides)} images, side U{{64..512}}, N=21 (349 px), J=10, "
-                               "kmax=12 (n=250), M=256, R=128, K=8"}}))
-    dic.close()
-    basis.close()
+        "data": "synthetic", "s": r["s"], "patches": r["patches"],
+        "mean_steps_taken": r["mean_steps_taken"], "handoffs": r["handoffs"],
+        "config": {"workload": r["config"]}}))
 
 
 SERVE_DIMS = dict(N=11, J=6, kmax=8, M=128, R=64, K=5)
@@ -955,6 +968,7 @@ def main():
             line["projection"] = measure_projection(rsc, torch, dev, stream)
             line["rksvd"] = measure_rksvd(rsc, torch, dev)
             line["images_c2_sizes"] = measure_images_c2(rsc, torch, dev)
+            line["images_c2"] = measure_c2_full(rsc, torch, dev)
             line["roundtrip"] = measure_roundtrip(rsc, torch, dev, stream, dic, out)
             line["classify"] = measure_classify(rsc, torch, dev)
             line["serving"] = measure_serving(rsc, torch, dev, rates=[200.0, 50.0], seconds=3.0,
