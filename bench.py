@@ -390,10 +390,18 @@ def measure_projection(rsc, torch, dev, stream, reps: int = 5) -> dict:
     nout = (kmax + 1) * J * 2
     flops = 2.0 * basis.npix * nout * P
     basis.close()
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    # algorithmic bytes per launch: the image read once, one packed
+    # coefficient vector written per window
+    algo = 2048 * 2048 * 4 + P * nout * 4
     return {"windows": P, "ms_per_call": ms, "windows_per_s": P / (ms / 1e3),
             "achieved_tflops": flops / (ms / 1e3) / 1e12,
             "path": "tcgen05, operands split into fp16 hi + lo (3 products)",
             "write_gbs": P * nout * 4 / (ms / 1e3) / 1e9,
+            "roofline": {"kernel": "project_tc_kernel", "bound": "hbm",
+                         "achieved": algo / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": algo / (ms / 1e3) / 1e9 / hbm, "bytes_per_launch": algo,
+                         "peak_note": "measured copy bandwidth"},
             "config": "one 2048x2048 image, N=11 (97 px), J=6, kmax=8, stride 1"}
 
 
@@ -421,9 +429,26 @@ def measure_roundtrip(rsc, torch, dev, stream, dic, codes, reps: int = 5) -> dic
         stream.synchronize()
     ms_rec = ev[0].elapsed_time(ev[1]) / reps
     ms_syn = ev[1].elapsed_time(ev[2]) / reps
+    npix = basis.npix
     basis.close()
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    K = int(codes["atom"].shape[1])
+    nco = 9 * 6 * 2 * 4  # one patch's half-spectrum coefficients (float32)
+    # algorithmic bytes: reconstruct reads the codes (atom, angle, FP64 weight)
+    # and writes the coefficients; synthesize reads those and writes the pixels
+    b_rec = P * (K * (4 + 4 + 8) + nco)
+    b_syn = P * (nco + npix * 4)
     return {"patches": P, "reconstruct_ms": ms_rec, "reconstruct_patches_per_s": P / (ms_rec / 1e3),
             "synthesize_ms": ms_syn, "synthesize_patches_per_s": P / (ms_syn / 1e3),
+            "roofline": {
+                "reconstruct": {"bound": "hbm", "achieved": b_rec / (ms_rec / 1e3) / 1e9,
+                                "peak": hbm, "unit": "GB/s",
+                                "frac": b_rec / (ms_rec / 1e3) / 1e9 / hbm},
+                "synthesize": {"bound": "hbm", "achieved": b_syn / (ms_syn / 1e3) / 1e9,
+                               "peak": hbm, "unit": "GB/s",
+                               "frac": b_syn / (ms_syn / 1e3) / 1e9 / hbm},
+                "peak_note": "measured copy bandwidth; algorithmic bytes (codes or coefficients "
+                             "in, coefficients or pixels out)"},
             "config": "omp_1m codes (M=64, R=64, K=5); synthesis on the 11x11 basis (97 px, n=102)"}
 
 
@@ -951,9 +976,23 @@ def main():
                                                         value)
         if cmp_run is not None:
             v32 = world * P * args.steps / (cmp_run["total_ms"] / 1e3)
+            # the FP32 kernel codes all K steps in one launch with the direct
+            # angle transform: its own flops, (a) + M R (4 kmax + 1) per step
+            alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+            f32_flops = wl.K * (fl["a"] + fl["b_direct"]) * P
+            f32_s = cmp_run["total_ms"] / args.steps / 1e3
             line["fp32_path"] = {"value": v32, "unit": "patches/s",
                                  "ms_per_step": cmp_run["total_ms"] / args.steps,
-                                 "speedup_of_headline": value / v32}
+                                 "speedup_of_headline": value / v32,
+                                 "roofline": {
+                                     "kernel": "romp_f32_kernel", "bound": "alu",
+                                     "achieved": f32_flops / f32_s / 1e12, "peak": alu_peak,
+                                     "unit": "TFLOP/s", "frac": f32_flops / f32_s / 1e12 / alu_peak,
+                                     "flops_per_patch": wl.K * (fl["a"] + fl["b_direct"]),
+                                     "flops_convention": "(a) 2J(1+4kmax)M + direct (b) M R (4kmax+1) "
+                                                         "per patch-step, x K; one launch per step",
+                                     "peak_note": f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x "
+                                                  f"2 x {sm_max:.0f} MHz"}}
         if prune_run is not None:
             nst = min(args.steps, 5)
             vp = world * P * nst / (prune_run["total_ms"] / 1e3)
