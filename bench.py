@@ -58,6 +58,18 @@ def mma_flops_per_patch(wl) -> int:
     return wl.K * 2 * up(n) * wl.M * wl.R
 
 
+def kernel_launch_count(slots, K: int, precision: str) -> int:
+    """Kernels launched, from the library's per-phase event slots: a scoring
+    slot and a hand-off slot are one kernel each; on the FP16 path each group
+    has one refine-phase slot around the init kernel and K around the
+    refine's two passes (two kernels each)."""
+    score, handoff, refine = (int(v) for v in slots)
+    if precision != "f16":
+        return score + handoff + refine
+    inits = refine // (K + 1)
+    return score + handoff + inits + 2 * (refine - inits)
+
+
 def algorithmic_bytes_per_patch(wl) -> int:
     n_floats = (wl.kmax + 1) * wl.J * 2
     return 4 * n_floats + wl.K * (4 + 4 + 4 + 8) + 4
@@ -929,7 +941,8 @@ def main():
                     "timing": "host clock around each blocking rsc_encode_host call (pinned "
                               "host buffers, H2D of x and D2H of every output inside); median "
                               "call"},
-            "gpu_launches": int(sum(main_run["kernel_launches"])),
+            "gpu_launches": kernel_launch_count(main_run["kernel_launches"], wl.K,
+                                                args.precision),
             "handoffs": main_run["handoffs"],
             "kernel_ms_per_step": {"scoring": main_run["kernel_ms"][0] / args.steps,
                                    "fp32_handoff": main_run["kernel_ms"][1] / args.steps,

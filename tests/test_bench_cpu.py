@@ -1,7 +1,7 @@
-"""Host logic of bench.py (CPU only): the oracle-parity counts that the
-benchmark line carries for its timed outputs are zero for the oracle's own
-results and count a planted wrong pick, a wrong weight and a wrong residual
-norm."""
+"""Host logic of bench.py (CPU only): the kernel count the line reports, and
+the oracle-parity counts that the benchmark line carries for its timed
+outputs (zero for the oracle's own results; a planted wrong pick, a wrong
+weight and a wrong residual norm are counted)."""
 import numpy as np
 
 import bench
@@ -38,3 +38,12 @@ def test_oracle_parity_counts_planted_errors():
     gpu2["resid_norm2"] = gpu2["resid_norm2"] * 1.5 + 1.0
     r2 = bench.oracle_parity(x, d, wl, gpu2, free, 1e-5)
     assert r2["rn2_violations"] == x.shape[0]
+
+
+def test_kernel_launch_count_from_event_slots():
+    # one call of 3 stream groups at K = 5: per group 5 scoring slots, one
+    # hand-off slot, and 6 refine-phase slots (the init kernel, then 5 slots
+    # of two refine passes): 5 + 1 + 1 + 10 = 17 kernels a group
+    assert bench.kernel_launch_count([15, 3, 18], 5, "f16") == 51
+    # the FP32 path: one kernel a call, timed in the scoring phase
+    assert bench.kernel_launch_count([4, 0, 0], 5, "fp32") == 4
