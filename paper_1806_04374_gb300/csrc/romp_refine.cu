@@ -34,9 +34,9 @@ struct StateIdx {
   static constexpr int nL = KK * (KK + 1) / 2;
   // doubles: L, inv, z, a
   static constexpr int dL = 0, dInv = nL, dZ = nL + KK, dA = nL + 2 * KK, nD = nL + 3 * KK;
-  // floats: ahi, alo, xnorm, rnorm, dr
+  // floats: ahi, alo, xnorm, rnorm, dr, ||x||^2 in double-float (hi, lo)
   static constexpr int fHi = 0, fLo = KK, fX = 2 * KK, fR = 2 * KK + 1, fDr = 2 * KK + 2,
-                       nF = 2 * KK + 3;
+                       fX2h = 2 * KK + 3, fX2l = 2 * KK + 4, nF = 2 * KK + 5;
   // ints: m, r, t, e (exponent of the current row's scale)
   static constexpr int iM = 0, iR = KK, iT = 2 * KK, iE = 2 * KK + 1, nI = 2 * KK + 2;
 };
@@ -249,6 +249,8 @@ __global__ void __launch_bounds__(128) romp_init_kernel(const RefineArgs a) {
     a.sI[I::iT * a.P + p] = 0;
     a.sI[I::iE * a.P + p] = e;
     a.sF[I::fX * a.P + p] = xnorm;
+    a.sF[I::fX2h * a.P + p] = acc.hi;
+    a.sF[I::fX2l * a.P + p] = acc.lo;
     a.sF[I::fR * a.P + p] = rn;
     a.sF[I::fDr * a.P + p] = 2.0f * kU32 * xnorm;
     a.win[p] = score_window(rn, 2.0f * kU32 * xnorm, e, a.L);
@@ -520,8 +522,18 @@ __global__ void __launch_bounds__(128, KK > 5 ? 4 : 5) romp_refine_kernel(const 
             dr = 2.0f * (t + 6) * kU32 * (xnorm + 1.5f * asum);
             if (t >= a.K) {
               outcome = 1;
-              // final residual norm in FP32 (the fp16 row is not needed any more)
-              rnorm = sqrtf(residual_q<KK>(nullptr, a.L, 1.0f, xp, a.d, HJ, t, S, tw, qtab));
+              // final residual norm from the least-squares solution: with
+              // L z = b (b_i = <A_i, x>, the factor of the Gram of the
+              // selected steered atoms), ||x - sum_i a_i A_i||^2 =
+              // ||x||^2 - z^T z, in FP64 from ||x||^2 in double-float (no
+              // residual is formed: the fp16 row is not needed any more)
+              double zz = 0.0;
+#pragma unroll
+              for (int i = 0; i < KK; ++i)
+                if (i < t) zz = fma(S.z[i], S.z[i], zz);
+              const double x2 = (double)a.sF[StateIdx<KK>::fX2h * a.P + p] +
+                                (double)a.sF[StateIdx<KK>::fX2l * a.P + p];
+              rnorm = (float)sqrt(fmax(x2 - zz, 0.0));
             } else {
               // the previous residual's norm bounds the new one (least squares
               // over a larger support)

@@ -274,3 +274,24 @@ def test_f16_and_fp32_paths_agree(rsc):
     assert rel < 1e-9, rel
     print("identical patches", same.sum(), "of", same.size, "max rel coef diff", rel,
           "f16 handed to fp32:", g16["fallbacks"])
+
+
+def test_final_residual_norm_from_the_factor(rsc):
+    """On the FP16 path a patch that takes all K steps reports
+    ||x||^2 - z^T z (L z = b, the least-squares factor; ||x||^2 in
+    double-float): within the float32 rounding of ||r|| and of its square
+    (4 ulps) of the forced-path oracle's FP64 residual norm^2, far inside the
+    1e-5 ||x||^2 of the general rule (the FP32 residual's own norm is off by
+    up to ~3e-7 ||x||^2)."""
+    d, x, _, wl = synth.workload_inputs("omp_1m", P=4096)
+    g = run_gpu(rsc, x, d, wl.R, wl.K, "f16")
+    forced = oracle.romp(x, d, wl.R, wl.K, forced_atom=g["atom"], forced_angle=g["angle_idx"])
+    xd = x.astype(np.float64)
+    xn2 = 2 * np.einsum("phjc,phjc->p", xd, xd) - np.einsum("pjc,pjc->p", xd[:, 0], xd[:, 0])
+    full = g["atom"][:, -1] >= 0
+    assert full.sum() > 0.99 * x.shape[0]
+    gn = g["resid_norm2"].astype(np.float64)
+    ref = forced["rn2"]
+    err = np.abs(gn - ref)[full]
+    bound = (2.0 ** -21 * ref + 1e-12 * xn2)[full]
+    assert np.all(err <= bound), (err.max(), (err / xn2[full]).max())
