@@ -19,7 +19,9 @@
 //     best row first, the others (K <= 5) only when their FP32 score plus its
 //     error bound reaches the exact best;
 //   * adds the Cholesky row of the winner (Gram entries and right-hand side
-//     in double-float, factor and solve in FP64) and writes the new residual.
+//     in double-float, factor and solve in FP64) and writes the new residual
+//     row; after the last step the reported residual norm comes from the
+//     factor instead (||x||^2 - z^T z, L z = b).
 // Per-patch state lives in HBM as structure-of-arrays (coalesced over
 // threads); stopped and finished patches write their outputs.
 #include "rsc_internal.h"
