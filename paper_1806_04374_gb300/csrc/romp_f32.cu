@@ -162,6 +162,10 @@ __global__ void __launch_bounds__(256)
   const int warps = blockDim.x >> 5;
   const Layout Lo = make_layout<KM>(M, J, H, R, K, warps, dT_in_smem != 0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // hand-off mode launches the whole persistent grid for a list whose length
+  // only the device knows (a few patches): a block with no patch of the list
+  // leaves before loading its tables (the whole block, before any barrier)
+  if (a.redo_list && (int64_t)blockIdx.x * warps >= (int64_t)*a.redo_count) return;
 
   // ---- block setup: twiddles (padded stride) and transposed atoms
   float *s_tw = reinterpret_cast<float *>(smem + Lo.tw_off);
