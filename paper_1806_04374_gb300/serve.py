@@ -103,7 +103,6 @@ class Server:
     def __init__(self, dic: "_rsc.Dictionary", basis: "_rsc.Basis", K: int,
                  precision: str = "f16", mem_budget: int = 8 << 30, slots: int = 3,
                  batch_windows: int = 1 << 20):
-        import torch
         if basis.J != dic.J or basis.kmax != dic.kmax:
             raise ValueError("basis and dictionary differ in J or kmax")
         if slots < 1 or mem_budget <= 0 or batch_windows < 1:
@@ -113,7 +112,6 @@ class Server:
         self.prec = _rsc.PRECISIONS[precision]
         self.mem_budget = int(mem_budget)
         self.batch_windows = int(batch_windows)
-        self.device = torch.device("cuda", torch.cuda.current_device())
         self.reserved = 0
         self.peak_reserved = 0
         self.calls = 0
@@ -121,11 +119,23 @@ class Server:
         self._cv = threading.Condition()
         self._closed = False
         self._next_id = 0
-        self._streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self._streams = self._make_streams(slots)
         self._workers = [threading.Thread(target=self._work, args=(s,), daemon=True)
                          for s in self._streams]
         for t in self._workers:
             t.start()
+
+    # ------------------------------------------------------------- device
+    def _make_streams(self, slots: int) -> list:
+        """The current CUDA device and one stream per slot."""
+        import torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        return [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+
+    def _bind(self):
+        """Makes the server's device current in a worker thread."""
+        import torch
+        torch.cuda.set_device(self.device)
 
     # ------------------------------------------------------------- memory
     def need_bytes(self, requests) -> int:
@@ -219,8 +229,7 @@ class Server:
         return batch, need
 
     def _work(self, stream):
-        import torch
-        torch.cuda.set_device(self.device)
+        self._bind()
         while True:
             with self._cv:
                 got = self._take()
