@@ -929,6 +929,11 @@ def main():
                 "kernel_ms": launch_s * 1e3,
                 "flops_per_launch": flops_per_launch,
                 "peak_note": peak_note,
+                "limiter": ("measured: the MMA issue rate that two TMEM accumulator buffers "
+                            "allow (100-134 cycles per MMA against 64 streamed) balanced with "
+                            "the epilogue over all M R / 2 pair values; tensor pipe 25% busy"
+                            if args.precision == "f16" else
+                            "measured: issue-bound on the FP32 and ALU pipes"),
             },
             "hbm": {"algorithmic_bytes_per_patch": algorithmic_bytes_per_patch(wl),
                     "achieved_gbs": algorithmic_bytes_per_patch(wl) * P / launch_s / 1e9,
